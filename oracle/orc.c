@@ -1,0 +1,975 @@
+/*
+ * orc.c -- plain, slow FP64 CPU oracle for one coupled time step of the
+ * hybrid low-Mach lattice Boltzmann / finite-difference solver of
+ * Hosseini & Thevenin, "Towards pore-scale simulation of combustion in
+ * porous media using a low-Mach hybrid lattice Boltzmann/finite difference
+ * solver" (arXiv 2304.05657).
+ *
+ * TEST INFRASTRUCTURE ONLY.  The tests, the package smoke check and the
+ * CPU-baseline leg of bench.py load this file's shared object; the CUDA
+ * library never does, and this file includes no header of it.  Every
+ * constant here (lattice, weights, stencil coefficients) is written out
+ * again on purpose.
+ *
+ * Equation numbers follow the paper's order of display:
+ *   Eq. 1 species balance, Eq. 2 diffusion velocity with correction,
+ *   Eq. 5 hydrodynamic-pressure closure, Eq. 6 Lambda, Eq. 7 energy,
+ *   Eq. 8 LB equation, Eq. 9 source Xi, Eq. 10 f^eq, Eq. 12 g^eq,
+ *   Eq. 13 moments (P_h, rho u), Eq. 14 post-collision g*, Eq. 15 MRT
+ *   relaxation, Eq. 18 omega_s, Eq. 19 pre-conditioning, Eq. 21 central
+ *   moments, Eq. 22 forward cumulants, Eq. 23 relaxation of cumulants,
+ *   Eq. 24 backward cumulants, Eq. 26 corrected convection (Sec. II.D),
+ *   Eq. 28 half-way bounce-back, Eq. 31 inlet, Eq. 32 outlet,
+ *   Eq. 34 ghost node (Sec. III.B).
+ *
+ * Where the paper is silent or garbled, this file takes the following
+ * readings (each also stated where it is used):
+ *   - order of one step: pull-stream with boundary rules; u from the pulled
+ *     populations; FD right-hand side from state n and u^n; Lambda^n from
+ *     the non-convective part of that right-hand side; collision with
+ *     rho^n, grad rho^n, Lambda^n, P_h^n.  The stored populations are
+ *     post-collision.
+ *   - omega_s = 1 / (nu/(cs^2 dt) + 1/2): Eq. 18 prints tau, not omega.
+ *   - relaxation (Eq. 15, 23): K*_j = Keq_j + (1 - omega_j)(K_j - Keq_j),
+ *     Keq from the same transform applied to g^eq/(rho cs^2) about the same
+ *     u; orders 0 and 1 are carried unchanged.  Second order: deviatoric
+ *     parts at omega_s, trace at omega_bulk; orders >= 3 at omega_hi.
+ *   - cumulant formulas: the index typos of Eq. 22 are fixed by permutation
+ *     symmetry (Pi_xx Pi_yy in K_xxyy, Pi_zz Pi_xyy in K_xyyzz, Pi_zz Pi_xxyy
+ *     in K_xxyyzz) and the backward map is the exact algebraic inverse of
+ *     the forward one, not Eq. 24 as printed.
+ *   - outlet (Eq. 32): g_i(x,t+1) = (cs - u.n) g*_i(x-n,t)
+ *     + (1 - cs + u.n) g*_i(x,t) in lattice units, u.n from the first
+ *     moment of g*(x) divided by rho(x) of the current scalar state.
+ *   - inlet (Eq. 31) applied to g: g_i = g*_ibar + 2 w_i rho_in u_in.c_i.
+ *   - constant-pressure outlet (the outlet of the validation cases,
+ *     Sec. IV.A and IV.C): anti-bounce-back,
+ *     g_i = -g*_ibar + 2 [w_i P_out + w_i rho ((c_i.u)^2/(2 cs^2) - u.u/2)]
+ *     with P_out = 0 and rho, u of the boundary cell (u from g*), i.e. twice
+ *     the even part of g^eq (Eq. 12) at the outlet pressure.  Eq. 32 alone
+ *     leaves the pressure level free to drift in this pressure-based scheme.
+ *   - transport: constant kinematic nu, alpha = nu/Pr, D_k = alpha/Le_k;
+ *     fluxes in expanded form with 4th-order central first and second
+ *     derivatives; equal constant c_p for all species.
+ *   - reaction: single-step global, rate per unit mass
+ *     q = A dt max(Y_F,0) max(Y_O,0) exp(-Ta/T).
+ *   - EOS: rho = (T_in/T)(W/W_in), so rho = 1 at the inlet state.
+ *   - ghosts per axis line; the ghost at distance j from the wall mirrors
+ *     the fluid point at distance j-1 on the other side; if that point is
+ *     not fluid the centre cell is used.  Density at ghost points is
+ *     reconstructed directly (Dirichlet rule on rho with rho_B = EOS(T_B,Y)),
+ *     following the paper's note on ghost-node properties.
+ *   - convection: WENO3 (Jiang-Shu, r = 2) upwinded on the sign of the
+ *     local velocity component; centred 2nd order on an axis when a point
+ *     of the +-2 stencil on that axis is not a fluid cell of the domain.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_MAXSP 8
+
+enum { ORC_PERIODIC = 0, ORC_WALL_ADIABATIC = 1, ORC_WALL_ISOTHERMAL = 2,
+       ORC_INLET = 3, ORC_OUTLET = 4, ORC_OUTLET_PRESSURE = 5 };
+/* classification of a point next to a fluid cell */
+enum { PT_FLUID = 0, PT_SOLID = 16 };
+
+typedef struct {
+    int dim, nx, ny, nz;
+    int bc[6];                 /* faces -x,+x,-y,+y,-z,+z */
+    double T_wall[6];
+    int n_species;
+    double W[ORC_MAXSP];       /* molar masses */
+    double nu_stoich[ORC_MAXSP];
+    double Le[ORC_MAXSP];
+    int fuel, oxid;
+    double A, Ta, Q, cp, dt;   /* A [1/s], Ta [K], Q [J/kg fuel], cp [J/kg/K], dt [s] */
+    double nu, Pr, omega_bulk, omega_hi;  /* omega_bulk <= 0 means omega_s */
+    double u_in, T_in, Y_in[ORC_MAXSP];
+    double T_solid;
+    int solid_isothermal;
+    int poiseuille_inlet;
+    double weno_eps;           /* species; temperature uses weno_eps * T_in^2 */
+} orc_setup;
+
+typedef struct {
+    orc_setup s;
+    int Q, nsp;
+    long N;
+    int c[27][3];
+    double w[27];
+    int opp[27];
+    double *g, *T, *Y;         /* state: g post-collision [Q][N], T [N], Y [nsp][N] */
+    double *gn, *Tn, *Yn;      /* next state */
+    unsigned char *solid;
+    double cs2, cs, omega_s, omega_b, alpha, D[ORC_MAXSP], A_lat;
+    double invW_in, rho_in;
+    long steps;
+} orc_sim;
+
+/* one point of an FD line: primitive and derived values */
+typedef struct {
+    double T, Y[ORC_MAXSP], invW, X[ORC_MAXSP], rho;
+} orc_pt;
+
+/* ------------------------------------------------------------------ */
+/* lattice                                                              */
+/* ------------------------------------------------------------------ */
+
+/* D2Q9 / D3Q27 as tensor products of D1Q3 {-1,0,1} with weights
+ * {1/6, 2/3, 1/6}; population index i = (cx+1) + 3(cy+1) + 9(cz+1). */
+static void lattice_init(orc_sim *S)
+{
+    const double w1[3] = {1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0};
+    int i = 0;
+    S->Q = (S->s.dim == 2) ? 9 : 27;
+    for (int cz = -1; cz <= 1; ++cz) {
+        if (S->s.dim == 2 && cz != 0) continue;
+        for (int cy = -1; cy <= 1; ++cy)
+            for (int cx = -1; cx <= 1; ++cx) {
+                int idx = (cx + 1) + 3 * (cy + 1) + (S->s.dim == 3 ? 9 * (cz + 1) : 0);
+                S->c[idx][0] = cx;
+                S->c[idx][1] = cy;
+                S->c[idx][2] = cz;
+                S->w[idx] = w1[cx + 1] * w1[cy + 1] * (S->s.dim == 3 ? w1[cz + 1] : 1.0);
+                ++i;
+            }
+    }
+    for (int a = 0; a < S->Q; ++a)
+        for (int b = 0; b < S->Q; ++b)
+            if (S->c[a][0] == -S->c[b][0] && S->c[a][1] == -S->c[b][1] &&
+                S->c[a][2] == -S->c[b][2])
+                S->opp[a] = b;
+    (void)i;
+}
+
+/* ------------------------------------------------------------------ */
+/* thermochemistry                                                      */
+/* ------------------------------------------------------------------ */
+
+static double inv_molar_mass(const orc_sim *S, const double *Y)
+{
+    double s = 0.0;
+    for (int k = 0; k < S->nsp; ++k) s += Y[k] / S->s.W[k];
+    return s;
+}
+
+/* ideal-gas EOS at constant P_0 (Sec. II.A), scaled so that rho(T_in, Y_in) = 1 */
+static double eos_rho(const orc_sim *S, double T, double invW)
+{
+    return (S->s.T_in / T) * (S->invW_in / invW);
+}
+
+/* single-step rate per unit mass of fuel consumed, per time step */
+static double rate_q(const orc_sim *S, double T, const double *Y)
+{
+    double yf = Y[S->s.fuel] > 0.0 ? Y[S->s.fuel] : 0.0;
+    double yo = Y[S->s.oxid] > 0.0 ? Y[S->s.oxid] : 0.0;
+    return S->A_lat * yf * yo * exp(-S->s.Ta / T);
+}
+
+/* mass yield of species k per unit mass of fuel consumed: nu_k W_k / (-nu_F W_F) */
+static double yield(const orc_sim *S, int k)
+{
+    return S->s.nu_stoich[k] * S->s.W[k] / (-S->s.nu_stoich[S->s.fuel] * S->s.W[S->s.fuel]);
+}
+
+/* ------------------------------------------------------------------ */
+/* geometry helpers                                                     */
+/* ------------------------------------------------------------------ */
+
+static int extent(const orc_sim *S, int a)
+{
+    return a == 0 ? S->s.nx : (a == 1 ? S->s.ny : S->s.nz);
+}
+
+static long cell_index(const orc_sim *S, const int p[3])
+{
+    return (long)p[0] + (long)S->s.nx * ((long)p[1] + (long)S->s.ny * (long)p[2]);
+}
+
+/* Classify position p (may lie outside the box along one axis).  Returns
+ * PT_FLUID with *idx set (periodic axes wrapped), PT_SOLID for a solid cell,
+ * or the boundary type of the face that is crossed, with *face set. */
+static int classify(const orc_sim *S, const int pin[3], long *idx, int *face)
+{
+    int p[3] = {pin[0], pin[1], pin[2]};
+    int wall = -1;
+    for (int a = 0; a < S->s.dim; ++a) {
+        int n = extent(S, a);
+        int f = -1;
+        if (p[a] < 0) f = 2 * a;
+        else if (p[a] >= n) f = 2 * a + 1;
+        if (f < 0) continue;
+        if (S->s.bc[f] == ORC_PERIODIC) {
+            p[a] = ((p[a] % n) + n) % n;
+        } else if (wall < 0) {
+            wall = f;
+        }
+    }
+    if (wall >= 0) {
+        *face = wall;
+        return S->s.bc[wall];
+    }
+    *idx = cell_index(S, p);
+    if (S->solid[*idx]) return PT_SOLID;
+    return PT_FLUID;
+}
+
+/* ------------------------------------------------------------------ */
+/* FD line points and ghosts (Sec. III.B, Eq. 34)                        */
+/* ------------------------------------------------------------------ */
+
+static void fluid_pt(const orc_sim *S, long idx, orc_pt *pt)
+{
+    pt->T = S->T[idx];
+    for (int k = 0; k < S->nsp; ++k) pt->Y[k] = S->Y[(long)k * S->N + idx];
+    pt->invW = inv_molar_mass(S, pt->Y);
+    for (int k = 0; k < S->nsp; ++k) pt->X[k] = pt->Y[k] / (S->s.W[k] * pt->invW);
+    pt->rho = eos_rho(S, pt->T, pt->invW);
+}
+
+/* ghost value from its mirror point m: phi_G = 2 phi_B - phi_I (Dirichlet)
+ * or phi_G = phi_I (Neumann). type is PT_SOLID or a face boundary type. */
+static void ghost_pt(const orc_sim *S, int type, int face, const orc_pt *m, orc_pt *g)
+{
+    int dirichlet_T = 0, dirichlet_Y = 0;
+    double TB = 0.0;
+    const double *YB = m->Y;
+    if (type == PT_SOLID) {
+        if (S->s.solid_isothermal) { dirichlet_T = 1; TB = S->s.T_solid; }
+    } else if (type == ORC_WALL_ISOTHERMAL) {
+        dirichlet_T = 1; TB = S->s.T_wall[face];
+    } else if (type == ORC_INLET) {
+        dirichlet_T = 1; TB = S->s.T_in;
+        dirichlet_Y = 1; YB = S->s.Y_in;
+    }
+    g->T = dirichlet_T ? 2.0 * TB - m->T : m->T;
+    for (int k = 0; k < S->nsp; ++k)
+        g->Y[k] = dirichlet_Y ? 2.0 * S->s.Y_in[k] - m->Y[k] : m->Y[k];
+    g->invW = inv_molar_mass(S, g->Y);
+    for (int k = 0; k < S->nsp; ++k) g->X[k] = g->Y[k] / (S->s.W[k] * g->invW);
+    if (dirichlet_T) {
+        double rhoB = eos_rho(S, TB, inv_molar_mass(S, YB));
+        g->rho = 2.0 * rhoB - m->rho;
+    } else {
+        g->rho = m->rho;
+    }
+}
+
+/* Build the 5-point line (offsets -2..2) through cell p along axis a.
+ * Returns 1 when a point of the line is not a fluid cell of the domain. */
+static int build_line(const orc_sim *S, const int p[3], long cidx, int a, orc_pt line[5])
+{
+    int near = 0;
+    fluid_pt(S, cidx, &line[2]);
+    for (int side = -1; side <= 1; side += 2) {
+        int w = 0, wtype = 0, wface = -1;
+        for (int j = 1; j <= 2; ++j) {
+            int q[3] = {p[0], p[1], p[2]};
+            long idx;
+            int face = -1;
+            q[a] += side * j;
+            int t = classify(S, q, &idx, &face);
+            if (t == PT_FLUID) {
+                fluid_pt(S, idx, &line[2 + side * j]);
+            } else {
+                w = j; wtype = t; wface = face;
+                break;
+            }
+        }
+        if (!w) continue;
+        near = 1;
+        for (int j = w; j <= 2; ++j) {
+            int m = 2 * w - 1 - j;  /* mirror offset on this side (may be -1) */
+            orc_pt mpt;
+            if (m >= 0) {
+                mpt = line[2 + side * m];
+            } else {
+                int q[3] = {p[0], p[1], p[2]};
+                long idx;
+                int face = -1;
+                q[a] -= side;  /* one step on the opposite side */
+                if (classify(S, q, &idx, &face) == PT_FLUID) fluid_pt(S, idx, &mpt);
+                else mpt = line[2];
+            }
+            ghost_pt(S, wtype, wface, &mpt, &line[2 + side * j]);
+        }
+    }
+    return near;
+}
+
+/* ------------------------------------------------------------------ */
+/* FD operators (Sec. II.D)                                              */
+/* ------------------------------------------------------------------ */
+
+/* 4th-order central first derivative, unit spacing */
+double orc_d1(const double v[5])
+{
+    return (v[0] - 8.0 * v[1] + 8.0 * v[3] - v[4]) / 12.0;
+}
+
+/* 4th-order central second derivative, unit spacing */
+double orc_d2(const double v[5])
+{
+    return (-v[0] + 16.0 * v[1] - 30.0 * v[2] + 16.0 * v[3] - v[4]) / 12.0;
+}
+
+/* centred 2nd-order first derivative */
+double orc_c2(const double v[5])
+{
+    return 0.5 * (v[3] - v[1]);
+}
+
+/* WENO3 face value (Jiang-Shu, r = 2).  a: far upwind, b: upwind cell,
+ * c: downwind cell of the face. */
+static double weno3_face(double a, double b, double c, double eps)
+{
+    double q0 = -0.5 * a + 1.5 * b;
+    double q1 = 0.5 * b + 0.5 * c;
+    double b0 = (b - a) * (b - a);
+    double b1 = (c - b) * (c - b);
+    double a0 = (1.0 / 3.0) / ((eps + b0) * (eps + b0));
+    double a1 = (2.0 / 3.0) / ((eps + b1) * (eps + b1));
+    return (a0 * q0 + a1 * q1) / (a0 + a1);
+}
+
+/* WENO3 approximation of d(phi)/dx at the centre of v[0..4], upwinded
+ * for the sign of the advecting velocity u (u = 0 takes the u > 0 branch). */
+double orc_weno3(const double v[5], double u, double eps)
+{
+    double fp, fm;
+    if (u >= 0.0) {
+        fp = weno3_face(v[1], v[2], v[3], eps);
+        fm = weno3_face(v[0], v[1], v[2], eps);
+    } else {
+        fp = weno3_face(v[4], v[3], v[2], eps);
+        fm = weno3_face(v[3], v[2], v[1], eps);
+    }
+    return fp - fm;
+}
+
+/* ------------------------------------------------------------------ */
+/* central moments and cumulants (Sec. II.C, Eq. 21, 22, 24)              */
+/* ------------------------------------------------------------------ */
+
+static double ipow(double x, int p)
+{
+    double r = 1.0;
+    for (int k = 0; k < p; ++k) r *= x;
+    return r;
+}
+
+/* moment index j = p + 3q + 9r, exponents p, q, r in {0,1,2} */
+static void moment_exponents(int j, int *p, int *q, int *r)
+{
+    *p = j % 3;
+    *q = (j / 3) % 3;
+    *r = j / 9;
+}
+
+/* Eq. 21: Pi_j = sum_i (c_ix-u_x)^p (c_iy-u_y)^q (c_iz-u_z)^r f_i */
+static void central_moments(const orc_sim *S, const double *f, const double u[3], double *Pi)
+{
+    for (int j = 0; j < S->Q; ++j) {
+        int p, q, r;
+        moment_exponents(j, &p, &q, &r);
+        double s = 0.0;
+        for (int i = 0; i < S->Q; ++i)
+            s += ipow(S->c[i][0] - u[0], p) * ipow(S->c[i][1] - u[1], q) *
+                 ipow(S->c[i][2] - u[2], r) * f[i];
+        Pi[j] = s;
+    }
+}
+
+/* Inverse of Eq. 21: solve the Q x Q linear system by Gaussian elimination
+ * with partial pivoting. */
+static void central_moments_inverse(const orc_sim *S, const double *Pi, const double u[3], double *f)
+{
+    int Q = S->Q;
+    double M[27][28];
+    for (int j = 0; j < Q; ++j) {
+        int p, q, r;
+        moment_exponents(j, &p, &q, &r);
+        for (int i = 0; i < Q; ++i)
+            M[j][i] = ipow(S->c[i][0] - u[0], p) * ipow(S->c[i][1] - u[1], q) *
+                      ipow(S->c[i][2] - u[2], r);
+        M[j][Q] = Pi[j];
+    }
+    for (int col = 0; col < Q; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < Q; ++r)
+            if (fabs(M[r][col]) > fabs(M[piv][col])) piv = r;
+        if (piv != col)
+            for (int k = 0; k <= Q; ++k) {
+                double t = M[col][k]; M[col][k] = M[piv][k]; M[piv][k] = t;
+            }
+        for (int r = col + 1; r < Q; ++r) {
+            double fac = M[r][col] / M[col][col];
+            for (int k = col; k <= Q; ++k) M[r][k] -= fac * M[col][k];
+        }
+    }
+    for (int r = Q - 1; r >= 0; --r) {
+        double s = M[r][Q];
+        for (int k = r + 1; k < Q; ++k) s -= M[r][k] * f[k];
+        f[r] = s / M[r][r];
+    }
+}
+
+#define MI(p, q, r) ((p) + 3 * (q) + 9 * (r))
+
+/* Eq. 22, with the index typos fixed by permutation symmetry.  Orders <= 3
+ * are the central moments themselves. */
+void orc_cumulants(int dim, const double *Pi, double *K)
+{
+    int Q = dim == 2 ? 9 : 27;
+    for (int j = 0; j < Q; ++j) K[j] = Pi[j];
+#define M_(p, q, r) Pi[MI(p, q, r)]
+    if (dim == 2) {
+        K[MI(2, 2, 0)] = M_(2, 2, 0) - M_(2, 0, 0) * M_(0, 2, 0) - 2.0 * M_(1, 1, 0) * M_(1, 1, 0);
+        return;
+    }
+    /* fourth order: xxyy class */
+    K[MI(2, 2, 0)] = M_(2, 2, 0) - M_(2, 0, 0) * M_(0, 2, 0) - 2.0 * M_(1, 1, 0) * M_(1, 1, 0);
+    K[MI(2, 0, 2)] = M_(2, 0, 2) - M_(2, 0, 0) * M_(0, 0, 2) - 2.0 * M_(1, 0, 1) * M_(1, 0, 1);
+    K[MI(0, 2, 2)] = M_(0, 2, 2) - M_(0, 2, 0) * M_(0, 0, 2) - 2.0 * M_(0, 1, 1) * M_(0, 1, 1);
+    /* fourth order: xxyz class */
+    K[MI(2, 1, 1)] = M_(2, 1, 1) - M_(2, 0, 0) * M_(0, 1, 1) - 2.0 * M_(1, 1, 0) * M_(1, 0, 1);
+    K[MI(1, 2, 1)] = M_(1, 2, 1) - M_(0, 2, 0) * M_(1, 0, 1) - 2.0 * M_(1, 1, 0) * M_(0, 1, 1);
+    K[MI(1, 1, 2)] = M_(1, 1, 2) - M_(0, 0, 2) * M_(1, 1, 0) - 2.0 * M_(1, 0, 1) * M_(0, 1, 1);
+    /* fifth order: xyyzz class */
+    K[MI(1, 2, 2)] = M_(1, 2, 2) - M_(0, 0, 2) * M_(1, 2, 0) - M_(0, 2, 0) * M_(1, 0, 2)
+                   - 4.0 * M_(0, 1, 1) * M_(1, 1, 1) - 2.0 * M_(1, 0, 1) * M_(0, 2, 1)
+                   - 2.0 * M_(1, 1, 0) * M_(0, 1, 2);
+    K[MI(2, 1, 2)] = M_(2, 1, 2) - M_(0, 0, 2) * M_(2, 1, 0) - M_(2, 0, 0) * M_(0, 1, 2)
+                   - 4.0 * M_(1, 0, 1) * M_(1, 1, 1) - 2.0 * M_(0, 1, 1) * M_(2, 0, 1)
+                   - 2.0 * M_(1, 1, 0) * M_(1, 0, 2);
+    K[MI(2, 2, 1)] = M_(2, 2, 1) - M_(2, 0, 0) * M_(0, 2, 1) - M_(0, 2, 0) * M_(2, 0, 1)
+                   - 4.0 * M_(1, 1, 0) * M_(1, 1, 1) - 2.0 * M_(1, 0, 1) * M_(1, 2, 0)
+                   - 2.0 * M_(0, 1, 1) * M_(2, 1, 0);
+    /* sixth order */
+    K[MI(2, 2, 2)] = M_(2, 2, 2)
+        - M_(2, 0, 0) * M_(0, 2, 2) - M_(0, 2, 0) * M_(2, 0, 2) - M_(0, 0, 2) * M_(2, 2, 0)
+        - 4.0 * M_(1, 1, 0) * M_(1, 1, 2) - 4.0 * M_(1, 0, 1) * M_(1, 2, 1)
+        - 4.0 * M_(0, 1, 1) * M_(2, 1, 1)
+        - 4.0 * M_(1, 1, 1) * M_(1, 1, 1)
+        - 2.0 * M_(2, 1, 0) * M_(0, 1, 2) - 2.0 * M_(2, 0, 1) * M_(0, 2, 1)
+        - 2.0 * M_(1, 2, 0) * M_(1, 0, 2)
+        + 2.0 * M_(2, 0, 0) * M_(0, 2, 0) * M_(0, 0, 2)
+        + 4.0 * M_(2, 0, 0) * M_(0, 1, 1) * M_(0, 1, 1)
+        + 4.0 * M_(0, 2, 0) * M_(1, 0, 1) * M_(1, 0, 1)
+        + 4.0 * M_(0, 0, 2) * M_(1, 1, 0) * M_(1, 1, 0)
+        + 16.0 * M_(1, 1, 0) * M_(1, 0, 1) * M_(0, 1, 1);
+#undef M_
+}
+
+/* Exact inverse of orc_cumulants (stands in for Eq. 24): central moments of
+ * order <= 3 equal the cumulants; higher orders are rebuilt from the
+ * cumulant and the already rebuilt lower-order central moments. */
+void orc_cumulants_inverse(int dim, const double *K, double *Pi)
+{
+    int Q = dim == 2 ? 9 : 27;
+    for (int j = 0; j < Q; ++j) Pi[j] = K[j];
+#define M_(p, q, r) Pi[MI(p, q, r)]
+    if (dim == 2) {
+        Pi[MI(2, 2, 0)] = K[MI(2, 2, 0)] + M_(2, 0, 0) * M_(0, 2, 0) + 2.0 * M_(1, 1, 0) * M_(1, 1, 0);
+        return;
+    }
+    Pi[MI(2, 2, 0)] = K[MI(2, 2, 0)] + M_(2, 0, 0) * M_(0, 2, 0) + 2.0 * M_(1, 1, 0) * M_(1, 1, 0);
+    Pi[MI(2, 0, 2)] = K[MI(2, 0, 2)] + M_(2, 0, 0) * M_(0, 0, 2) + 2.0 * M_(1, 0, 1) * M_(1, 0, 1);
+    Pi[MI(0, 2, 2)] = K[MI(0, 2, 2)] + M_(0, 2, 0) * M_(0, 0, 2) + 2.0 * M_(0, 1, 1) * M_(0, 1, 1);
+    Pi[MI(2, 1, 1)] = K[MI(2, 1, 1)] + M_(2, 0, 0) * M_(0, 1, 1) + 2.0 * M_(1, 1, 0) * M_(1, 0, 1);
+    Pi[MI(1, 2, 1)] = K[MI(1, 2, 1)] + M_(0, 2, 0) * M_(1, 0, 1) + 2.0 * M_(1, 1, 0) * M_(0, 1, 1);
+    Pi[MI(1, 1, 2)] = K[MI(1, 1, 2)] + M_(0, 0, 2) * M_(1, 1, 0) + 2.0 * M_(1, 0, 1) * M_(0, 1, 1);
+    Pi[MI(1, 2, 2)] = K[MI(1, 2, 2)] + M_(0, 0, 2) * M_(1, 2, 0) + M_(0, 2, 0) * M_(1, 0, 2)
+                    + 4.0 * M_(0, 1, 1) * M_(1, 1, 1) + 2.0 * M_(1, 0, 1) * M_(0, 2, 1)
+                    + 2.0 * M_(1, 1, 0) * M_(0, 1, 2);
+    Pi[MI(2, 1, 2)] = K[MI(2, 1, 2)] + M_(0, 0, 2) * M_(2, 1, 0) + M_(2, 0, 0) * M_(0, 1, 2)
+                    + 4.0 * M_(1, 0, 1) * M_(1, 1, 1) + 2.0 * M_(0, 1, 1) * M_(2, 0, 1)
+                    + 2.0 * M_(1, 1, 0) * M_(1, 0, 2);
+    Pi[MI(2, 2, 1)] = K[MI(2, 2, 1)] + M_(2, 0, 0) * M_(0, 2, 1) + M_(0, 2, 0) * M_(2, 0, 1)
+                    + 4.0 * M_(1, 1, 0) * M_(1, 1, 1) + 2.0 * M_(1, 0, 1) * M_(1, 2, 0)
+                    + 2.0 * M_(0, 1, 1) * M_(2, 1, 0);
+    Pi[MI(2, 2, 2)] = K[MI(2, 2, 2)]
+        + M_(2, 0, 0) * M_(0, 2, 2) + M_(0, 2, 0) * M_(2, 0, 2) + M_(0, 0, 2) * M_(2, 2, 0)
+        + 4.0 * M_(1, 1, 0) * M_(1, 1, 2) + 4.0 * M_(1, 0, 1) * M_(1, 2, 1)
+        + 4.0 * M_(0, 1, 1) * M_(2, 1, 1)
+        + 4.0 * M_(1, 1, 1) * M_(1, 1, 1)
+        + 2.0 * M_(2, 1, 0) * M_(0, 1, 2) + 2.0 * M_(2, 0, 1) * M_(0, 2, 1)
+        + 2.0 * M_(1, 2, 0) * M_(1, 0, 2)
+        - 2.0 * M_(2, 0, 0) * M_(0, 2, 0) * M_(0, 0, 2)
+        - 4.0 * M_(2, 0, 0) * M_(0, 1, 1) * M_(0, 1, 1)
+        - 4.0 * M_(0, 2, 0) * M_(1, 0, 1) * M_(1, 0, 1)
+        - 4.0 * M_(0, 0, 2) * M_(1, 1, 0) * M_(1, 1, 0)
+        - 16.0 * M_(1, 1, 0) * M_(1, 0, 1) * M_(0, 1, 1);
+#undef M_
+}
+
+/* ------------------------------------------------------------------ */
+/* collision (Sec. II.B-C)                                               */
+/* ------------------------------------------------------------------ */
+
+static int moment_order(int j)
+{
+    int p, q, r;
+    moment_exponents(j, &p, &q, &r);
+    return p + q + r;
+}
+
+/* One cell: pre-collision populations g (after streaming), density rho,
+ * velocity u, density gradient grad_rho, expansion source Lambda.
+ * Writes post-collision g* (Eq. 14).  Optionally returns P_h and Xi. */
+static void collide(const orc_sim *S, const double *g, double rho, const double u[3],
+                    const double grad_rho[3], double Lam, double *gstar,
+                    double *P_h_out, double *Xi_out)
+{
+    int Q = S->Q;
+    double cs2 = S->cs2;
+    double sum_g = 0.0;
+    for (int i = 0; i < Q; ++i) sum_g += g[i];
+    double P_h = sum_g + 0.5 * rho * cs2 * Lam;                       /* Eq. 13a */
+    double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    double Xi[27], fp[27], fpeq[27];
+    for (int i = 0; i < Q; ++i) {
+        double cu = S->c[i][0] * u[0] + S->c[i][1] * u[1] + S->c[i][2] * u[2];
+        double feq = S->w[i] * rho * (1.0 + cu / cs2 + cu * cu / (2.0 * cs2 * cs2) - uu / (2.0 * cs2)); /* Eq. 10 */
+        double cmu_grad = (S->c[i][0] - u[0]) * grad_rho[0] + (S->c[i][1] - u[1]) * grad_rho[1] +
+                          (S->c[i][2] - u[2]) * grad_rho[2];
+        Xi[i] = cs2 * (feq / rho - S->w[i]) * cmu_grad + S->w[i] * rho * cs2 * Lam;  /* Eq. 9 */
+        double geq = S->w[i] * (P_h - rho * cs2) + cs2 * feq;                      /* Eq. 12 */
+        fp[i] = g[i] / (rho * cs2) + Xi[i] / (2.0 * rho * cs2);                     /* Eq. 19 */
+        fpeq[i] = geq / (rho * cs2);
+    }
+    double Pi[27], Pieq[27], K[27], Keq[27], Ks[27], Pis[27], fps[27];
+    central_moments(S, fp, u, Pi);
+    central_moments(S, fpeq, u, Pieq);
+    orc_cumulants(S->s.dim, Pi, K);
+    orc_cumulants(S->s.dim, Pieq, Keq);
+    /* Eq. 15/23 read as relaxation toward the equilibrium cumulants */
+    for (int j = 0; j < Q; ++j) {
+        int o = moment_order(j);
+        if (o <= 1) Ks[j] = K[j];
+        else if (o >= 3) Ks[j] = Keq[j] + (1.0 - S->s.omega_hi) * (K[j] - Keq[j]);
+        else Ks[j] = 0.0; /* second order handled below */
+    }
+    double ws = S->omega_s, wb = S->omega_b;
+    if (S->s.dim == 2) {
+        int ixx = MI(2, 0, 0), iyy = MI(0, 2, 0), ixy = MI(1, 1, 0);
+        double tr = K[ixx] + K[iyy], treq = Keq[ixx] + Keq[iyy];
+        double dv = K[ixx] - K[iyy], dveq = Keq[ixx] - Keq[iyy];
+        double trs = treq + (1.0 - wb) * (tr - treq);
+        double dvs = dveq + (1.0 - ws) * (dv - dveq);
+        Ks[ixx] = 0.5 * (trs + dvs);
+        Ks[iyy] = 0.5 * (trs - dvs);
+        Ks[ixy] = Keq[ixy] + (1.0 - ws) * (K[ixy] - Keq[ixy]);
+    } else {
+        int ixx = MI(2, 0, 0), iyy = MI(0, 2, 0), izz = MI(0, 0, 2);
+        double tr = K[ixx] + K[iyy] + K[izz], treq = Keq[ixx] + Keq[iyy] + Keq[izz];
+        double d1 = K[ixx] - K[iyy], d1eq = Keq[ixx] - Keq[iyy];
+        double d2 = K[ixx] - K[izz], d2eq = Keq[ixx] - Keq[izz];
+        double trs = treq + (1.0 - wb) * (tr - treq);
+        double d1s = d1eq + (1.0 - ws) * (d1 - d1eq);
+        double d2s = d2eq + (1.0 - ws) * (d2 - d2eq);
+        Ks[ixx] = (trs + d1s + d2s) / 3.0;
+        Ks[iyy] = Ks[ixx] - d1s;
+        Ks[izz] = Ks[ixx] - d2s;
+        int off[3] = {MI(1, 1, 0), MI(1, 0, 1), MI(0, 1, 1)};
+        for (int t = 0; t < 3; ++t)
+            Ks[off[t]] = Keq[off[t]] + (1.0 - ws) * (K[off[t]] - Keq[off[t]]);
+    }
+    orc_cumulants_inverse(S->s.dim, Ks, Pis);
+    central_moments_inverse(S, Pis, u, fps);
+    for (int i = 0; i < Q; ++i) gstar[i] = rho * cs2 * fps[i] + 0.5 * Xi[i];   /* Eq. 14 */
+    if (P_h_out) *P_h_out = P_h;
+    if (Xi_out)
+        for (int i = 0; i < Q; ++i) Xi_out[i] = Xi[i];
+}
+
+/* ------------------------------------------------------------------ */
+/* streaming with boundary rules (Eq. 8, 28, 31, 32)                     */
+/* ------------------------------------------------------------------ */
+
+/* inlet velocity vector for an inlet on face f at position p */
+static void inlet_velocity(const orc_sim *S, int f, const int p[3], double uin[3])
+{
+    int a = f / 2;
+    double sgn = (f % 2 == 0) ? 1.0 : -1.0;  /* inward normal */
+    double mag = S->s.u_in;
+    if (S->s.poiseuille_inlet && S->s.dim == 2 && a == 0) {
+        double ny = S->s.ny, y = p[1] + 0.5;
+        mag = 6.0 * S->s.u_in * y * (ny - y) / (ny * ny);
+    }
+    uin[0] = uin[1] = uin[2] = 0.0;
+    uin[a] = sgn * mag;
+}
+
+/* pulled population i at cell p (post-streaming, time n+1) */
+static double pull(const orc_sim *S, int i, const int p[3], long cidx)
+{
+    int src[3] = {p[0] - S->c[i][0], p[1] - S->c[i][1], p[2] - S->c[i][2]};
+    int wall = 0, inlet = -1, outlet = -1;
+    for (int a = 0; a < S->s.dim; ++a) {
+        int n = extent(S, a), f = -1;
+        if (src[a] < 0) f = 2 * a;
+        else if (src[a] >= n) f = 2 * a + 1;
+        if (f < 0) continue;
+        switch (S->s.bc[f]) {
+        case ORC_PERIODIC: src[a] = ((src[a] % n) + n) % n; break;
+        case ORC_INLET: if (inlet < 0) inlet = f; break;
+        case ORC_OUTLET:
+        case ORC_OUTLET_PRESSURE: if (outlet < 0) outlet = f; break;
+        default: wall = 1; break;
+        }
+    }
+    const double *g = S->g;
+    long N = S->N;
+    int ib = S->opp[i];
+    if (wall) return g[(long)ib * N + cidx];                              /* Eq. 28 */
+    if (inlet >= 0) {                                                     /* Eq. 31 */
+        double uin[3];
+        inlet_velocity(S, inlet, p, uin);
+        double cu = S->c[i][0] * uin[0] + S->c[i][1] * uin[1] + S->c[i][2] * uin[2];
+        return g[(long)ib * N + cidx] + (S->w[i] + S->w[ib]) * S->rho_in * cu;
+    }
+    if (outlet >= 0 && S->s.bc[outlet] == ORC_OUTLET_PRESSURE) {         /* constant P_h */
+        double T = S->T[cidx], Y[ORC_MAXSP], u[3] = {0.0, 0.0, 0.0};
+        for (int k = 0; k < S->nsp; ++k) Y[k] = S->Y[(long)k * N + cidx];
+        double rho = eos_rho(S, T, inv_molar_mass(S, Y));
+        for (int a = 0; a < S->s.dim; ++a) {
+            double m = 0.0;
+            for (int j = 0; j < S->Q; ++j) m += S->c[j][a] * g[(long)j * N + cidx];
+            u[a] = m / (rho * S->cs2);
+        }
+        double cu = S->c[i][0] * u[0] + S->c[i][1] * u[1] + S->c[i][2] * u[2];
+        double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        double geq_even = S->w[i] * (0.0 - rho * S->cs2) +
+                          S->cs2 * S->w[i] * rho * (1.0 + cu * cu / (2.0 * S->cs2 * S->cs2) - uu / (2.0 * S->cs2));
+        return -g[(long)ib * N + cidx] + 2.0 * geq_even;
+    }
+    if (outlet >= 0) {                                                    /* Eq. 32 */
+        int a = outlet / 2;
+        int nsign = (outlet % 2 == 1) ? 1 : -1;  /* outward normal along axis a */
+        double T = S->T[cidx], Y[ORC_MAXSP];
+        for (int k = 0; k < S->nsp; ++k) Y[k] = S->Y[(long)k * N + cidx];
+        double rho = eos_rho(S, T, inv_molar_mass(S, Y));
+        double mom = 0.0;
+        for (int j = 0; j < S->Q; ++j) mom += S->c[j][a] * nsign * g[(long)j * N + cidx];
+        double un = mom / (rho * S->cs2);
+        int q[3] = {p[0], p[1], p[2]};
+        q[a] -= nsign;
+        double inner = g[(long)i * N + cidx];
+        if (q[a] >= 0 && q[a] < extent(S, a)) {
+            long qi = cell_index(S, q);
+            if (!S->solid[qi]) inner = g[(long)i * N + qi];
+        }
+        return (S->cs - un) * inner + (1.0 - S->cs + un) * g[(long)i * N + cidx];
+    }
+    long sidx = cell_index(S, src);
+    if (S->solid[sidx]) return g[(long)ib * N + cidx];                     /* Eq. 28 */
+    return g[(long)i * N + sidx];                                          /* Eq. 8 */
+}
+
+/* ------------------------------------------------------------------ */
+/* one cell of the coupled step                                          */
+/* ------------------------------------------------------------------ */
+
+/* Per-cell quantities, also returned to the tests by orc_cell_terms. */
+typedef struct {
+    double rho, u[3], grad_rho[3];
+    double conv_T, diff_T, reac_T;
+    double conv_Y[ORC_MAXSP], diff_Y[ORC_MAXSP], reac_Y[ORC_MAXSP];
+    double Lambda, P_h;
+} orc_terms;
+
+static void cell_update(const orc_sim *S, const int p[3], long cidx, double *gin,
+                        orc_terms *tm, double *T_new, double *Y_new, double *gstar)
+{
+    int nsp = S->nsp, dim = S->s.dim;
+    /* a1: pull-stream with boundary rules */
+    for (int i = 0; i < S->Q; ++i) gin[i] = pull(S, i, p, cidx);
+
+    /* a2: density from the EOS, velocity from Eq. 13b */
+    orc_pt c0;
+    fluid_pt(S, cidx, &c0);
+    double rho = c0.rho;
+    double u[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < dim; ++a) {
+        double m = 0.0;
+        for (int i = 0; i < S->Q; ++i) m += S->c[i][a] * gin[i];
+        u[a] = m / (rho * S->cs2);
+    }
+
+    /* a3-a5: per-axis FD lines */
+    double conv_T = 0.0, diff_T = 0.0;
+    double conv_Y[ORC_MAXSP] = {0}, diff_Y[ORC_MAXSP] = {0};
+    double grad_rho[3] = {0.0, 0.0, 0.0};
+    double epsY = S->s.weno_eps, epsT = S->s.weno_eps * S->s.T_in * S->s.T_in;
+    for (int a = 0; a < dim; ++a) {
+        orc_pt line[5];
+        int near = build_line(S, p, cidx, a, line);
+        double v[5];
+        /* density gradient, 4th order (used by diffusion and by Xi) */
+        for (int j = 0; j < 5; ++j) v[j] = line[j].rho;
+        double drho = orc_d1(v);
+        grad_rho[a] = drho;
+        /* temperature: convection (no correction) and diffusion, Eq. 7 */
+        for (int j = 0; j < 5; ++j) v[j] = line[j].T;
+        conv_T += u[a] * (near ? orc_c2(v) : orc_weno3(v, u[a], epsT));
+        diff_T += S->alpha * (orc_d2(v) + drho * orc_d1(v) / rho);
+        /* species convection with the correction of Eq. 26 */
+        double L[ORC_MAXSP], sumL = 0.0;
+        for (int k = 0; k < nsp; ++k) {
+            for (int j = 0; j < 5; ++j) v[j] = line[j].Y[k];
+            L[k] = near ? orc_c2(v) : orc_weno3(v, u[a], epsY);
+            sumL += L[k];
+        }
+        for (int k = 0; k < nsp; ++k) conv_Y[k] += u[a] * (L[k] - c0.Y[k] * sumL);
+        /* species diffusion, Eq. 1-2 with constant D_k, expanded form */
+        double vW[5];
+        for (int j = 0; j < 5; ++j) vW[j] = line[j].invW;
+        double dinvW = orc_d1(vW);
+        double m[ORC_MAXSP], dm[ORC_MAXSP], dY[ORC_MAXSP], Msum = 0.0, dMsum = 0.0;
+        for (int k = 0; k < nsp; ++k) {
+            double ak = S->D[k] * S->s.W[k];
+            for (int j = 0; j < 5; ++j) v[j] = line[j].X[k];
+            double dX = orc_d1(v), d2X = orc_d2(v);
+            m[k] = ak * c0.invW * dX;
+            dm[k] = ak * (c0.invW * d2X + dinvW * dX);
+            for (int j = 0; j < 5; ++j) v[j] = line[j].Y[k];
+            dY[k] = orc_d1(v);
+            Msum += m[k];
+            dMsum += dm[k];
+        }
+        for (int k = 0; k < nsp; ++k)
+            diff_Y[k] += dm[k] - dY[k] * Msum - c0.Y[k] * dMsum +
+                         (m[k] - c0.Y[k] * Msum) * drho / rho;
+    }
+
+    /* a6: reaction */
+    double q = rate_q(S, c0.T, c0.Y);
+    double reac_T = S->s.Q / S->s.cp * q;
+    double reac_Y[ORC_MAXSP];
+    for (int k = 0; k < nsp; ++k) reac_Y[k] = yield(S, k) * q;
+
+    /* a7: explicit Euler and Lambda (Eq. 6, from the non-convective rates) */
+    *T_new = c0.T + (-conv_T + diff_T + reac_T);
+    double Lam = (diff_T + reac_T) / c0.T;
+    double W = 1.0 / c0.invW;
+    for (int k = 0; k < nsp; ++k) {
+        Y_new[k] = c0.Y[k] + (-conv_Y[k] + diff_Y[k] + reac_Y[k]);
+        Lam += W / S->s.W[k] * (diff_Y[k] + reac_Y[k]);
+    }
+
+    /* a8-a9: source, pre-conditioning and cumulant collision */
+    double P_h;
+    collide(S, gin, rho, u, grad_rho, Lam, gstar, &P_h, NULL);
+
+    if (tm) {
+        tm->rho = rho;
+        for (int a = 0; a < 3; ++a) { tm->u[a] = u[a]; tm->grad_rho[a] = grad_rho[a]; }
+        tm->conv_T = conv_T; tm->diff_T = diff_T; tm->reac_T = reac_T;
+        for (int k = 0; k < nsp; ++k) {
+            tm->conv_Y[k] = conv_Y[k]; tm->diff_Y[k] = diff_Y[k]; tm->reac_Y[k] = reac_Y[k];
+        }
+        tm->Lambda = Lam;
+        tm->P_h = P_h;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* public oracle interface (ctypes)                                      */
+/* ------------------------------------------------------------------ */
+
+orc_sim *orc_new(const orc_setup *s, const unsigned char *solid)
+{
+    orc_sim *S = (orc_sim *)calloc(1, sizeof(orc_sim));
+    if (!S) return NULL;
+    S->s = *s;
+    if (S->s.dim == 2) S->s.nz = 1;
+    S->nsp = s->n_species;
+    S->N = (long)S->s.nx * S->s.ny * S->s.nz;
+    lattice_init(S);
+    S->cs2 = 1.0 / 3.0;
+    S->cs = sqrt(S->cs2);
+    S->omega_s = 1.0 / (s->nu / S->cs2 + 0.5);   /* Eq. 18 read as 1/tau */
+    S->omega_b = s->omega_bulk > 0.0 ? s->omega_bulk : S->omega_s;
+    S->alpha = s->nu / s->Pr;
+    for (int k = 0; k < S->nsp; ++k) S->D[k] = S->alpha / s->Le[k];
+    S->A_lat = s->A * s->dt;
+    S->invW_in = inv_molar_mass(S, s->Y_in);
+    S->rho_in = eos_rho(S, s->T_in, S->invW_in);
+    long N = S->N;
+    S->g = (double *)calloc((size_t)S->Q * N, sizeof(double));
+    S->gn = (double *)calloc((size_t)S->Q * N, sizeof(double));
+    S->T = (double *)calloc((size_t)N, sizeof(double));
+    S->Tn = (double *)calloc((size_t)N, sizeof(double));
+    S->Y = (double *)calloc((size_t)S->nsp * N, sizeof(double));
+    S->Yn = (double *)calloc((size_t)S->nsp * N, sizeof(double));
+    S->solid = (unsigned char *)calloc((size_t)N, 1);
+    if (!S->g || !S->gn || !S->T || !S->Tn || !S->Y || !S->Yn || !S->solid) return NULL;
+    if (solid) memcpy(S->solid, solid, (size_t)N);
+    return S;
+}
+
+void orc_free(orc_sim *S)
+{
+    if (!S) return;
+    free(S->g); free(S->gn); free(S->T); free(S->Tn); free(S->Y); free(S->Yn); free(S->solid);
+    free(S);
+}
+
+long orc_ncells(const orc_sim *S) { return S->N; }
+int orc_q(const orc_sim *S) { return S->Q; }
+double orc_omega_s(const orc_sim *S) { return S->omega_s; }
+
+/* T [N], Y [nsp][N], g [Q][N] (g may be NULL: zero populations) */
+void orc_set_state(orc_sim *S, const double *T, const double *Y, const double *g)
+{
+    long N = S->N;
+    memcpy(S->T, T, sizeof(double) * (size_t)N);
+    memcpy(S->Y, Y, sizeof(double) * (size_t)S->nsp * N);
+    if (g) memcpy(S->g, g, sizeof(double) * (size_t)S->Q * N);
+    else memset(S->g, 0, sizeof(double) * (size_t)S->Q * N);
+    S->steps = 0;
+}
+
+void orc_get_state(const orc_sim *S, double *T, double *Y, double *g)
+{
+    long N = S->N;
+    if (T) memcpy(T, S->T, sizeof(double) * (size_t)N);
+    if (Y) memcpy(Y, S->Y, sizeof(double) * (size_t)S->nsp * N);
+    if (g) memcpy(g, S->g, sizeof(double) * (size_t)S->Q * N);
+}
+
+/* Advance n coupled steps.  Solid cells keep their state. */
+void orc_step(orc_sim *S, int n)
+{
+    long N = S->N;
+    double gin[27], gst[27], Yn[ORC_MAXSP], Tn;
+    for (int it = 0; it < n; ++it) {
+        memcpy(S->gn, S->g, sizeof(double) * (size_t)S->Q * N);
+        memcpy(S->Tn, S->T, sizeof(double) * (size_t)N);
+        memcpy(S->Yn, S->Y, sizeof(double) * (size_t)S->nsp * N);
+        for (int z = 0; z < S->s.nz; ++z)
+            for (int y = 0; y < S->s.ny; ++y)
+                for (int x = 0; x < S->s.nx; ++x) {
+                    int p[3] = {x, y, z};
+                    long c = cell_index(S, p);
+                    if (S->solid[c]) continue;
+                    cell_update(S, p, c, gin, NULL, &Tn, Yn, gst);
+                    S->Tn[c] = Tn;
+                    for (int k = 0; k < S->nsp; ++k) S->Yn[(long)k * N + c] = Yn[k];
+                    for (int i = 0; i < S->Q; ++i) S->gn[(long)i * N + c] = gst[i];
+                }
+        double *t;
+        t = S->g; S->g = S->gn; S->gn = t;
+        t = S->T; S->T = S->Tn; S->Tn = t;
+        t = S->Y; S->Y = S->Yn; S->Yn = t;
+        S->steps++;
+    }
+}
+
+/* Per-cell terms of the next step at cell (x,y,z), without advancing.
+ * out layout: rho, u[3], grad_rho[3], conv_T, diff_T, reac_T, Lambda, P_h,
+ * then conv_Y[nsp], diff_Y[nsp], reac_Y[nsp], then g_in[Q], g*[Q],
+ * T_new, Y_new[nsp]. */
+void orc_cell_terms(const orc_sim *S, int x, int y, int z, double *out)
+{
+    int p[3] = {x, y, z};
+    long c = cell_index(S, p);
+    orc_terms tm;
+    double gin[27], gst[27], Yn[ORC_MAXSP], Tn;
+    memset(&tm, 0, sizeof tm);
+    cell_update(S, p, c, gin, &tm, &Tn, Yn, gst);
+    int o = 0, nsp = S->nsp;
+    out[o++] = tm.rho;
+    for (int a = 0; a < 3; ++a) out[o++] = tm.u[a];
+    for (int a = 0; a < 3; ++a) out[o++] = tm.grad_rho[a];
+    out[o++] = tm.conv_T; out[o++] = tm.diff_T; out[o++] = tm.reac_T;
+    out[o++] = tm.Lambda; out[o++] = tm.P_h;
+    for (int k = 0; k < nsp; ++k) out[o++] = tm.conv_Y[k];
+    for (int k = 0; k < nsp; ++k) out[o++] = tm.diff_Y[k];
+    for (int k = 0; k < nsp; ++k) out[o++] = tm.reac_Y[k];
+    for (int i = 0; i < S->Q; ++i) out[o++] = gin[i];
+    for (int i = 0; i < S->Q; ++i) out[o++] = gst[i];
+    out[o++] = Tn;
+    for (int k = 0; k < nsp; ++k) out[o++] = Yn[k];
+}
+
+/* Single-cell collision for the tests: g (pre-collision), rho, u, grad_rho,
+ * Lambda -> g*, Xi, P_h.  Uses the sim's lattice and relaxation rates. */
+void orc_collide_cell(const orc_sim *S, const double *g, double rho, const double *u,
+                      const double *grad_rho, double Lam, double *gstar, double *Xi, double *P_h)
+{
+    double uu[3] = {u[0], u[1], u[2]}, gr[3] = {grad_rho[0], grad_rho[1], grad_rho[2]};
+    collide(S, g, rho, uu, gr, Lam, gstar, P_h, Xi);
+}
+
+/* Central moments (Eq. 21) and their inverse, for the tests. */
+void orc_central_moments(const orc_sim *S, const double *f, const double *u, double *Pi)
+{
+    double uu[3] = {u[0], u[1], u[2]};
+    central_moments(S, f, uu, Pi);
+}
+
+void orc_central_moments_inverse(const orc_sim *S, const double *Pi, const double *u, double *f)
+{
+    double uu[3] = {u[0], u[1], u[2]};
+    central_moments_inverse(S, Pi, uu, f);
+}
+
+/* Diagnostics over fluid cells (a11):
+ * out[0] x_f = sum Y_F / (Y_F,in * fluid cells in the x = 0 section) [cells]
+ * out[1] mass = sum rho
+ * out[2] heat release = sum rho (Q/cp) q   [K per step, rho-weighted]
+ * out[3] fuel consumption = sum rho q
+ * out[4] max T
+ * out[5] x of the maximum heat release on the centre line y = ny/2, z = nz/2
+ *        (smallest x on ties; -1 when no fluid cell there)
+ * out[6] number of fluid cells with a non-finite state value
+ * out[7] number of fluid cells */
+void orc_diagnostics(const orc_sim *S, double *out)
+{
+    long N = S->N;
+    int nsp = S->nsp;
+    double sumYF = 0.0, mass = 0.0, hrr = 0.0, fuel = 0.0, Tmax = -INFINITY;
+    double nonfinite = 0.0, nfluid = 0.0, section = 0.0;
+    double best = -INFINITY;
+    int bestx = -1;
+    int yc = S->s.ny / 2, zc = S->s.nz / 2;
+    for (int z = 0; z < S->s.nz; ++z)
+        for (int y = 0; y < S->s.ny; ++y)
+            for (int x = 0; x < S->s.nx; ++x) {
+                int p[3] = {x, y, z};
+                long c = cell_index(S, p);
+                if (S->solid[c]) continue;
+                nfluid += 1.0;
+                if (x == 0) section += 1.0;
+                double Y[ORC_MAXSP];
+                int bad = !isfinite(S->T[c]);
+                for (int k = 0; k < nsp; ++k) {
+                    Y[k] = S->Y[(long)k * N + c];
+                    bad |= !isfinite(Y[k]);
+                }
+                for (int i = 0; i < S->Q; ++i) bad |= !isfinite(S->g[(long)i * N + c]);
+                if (bad) { nonfinite += 1.0; continue; }
+                double T = S->T[c];
+                double rho = eos_rho(S, T, inv_molar_mass(S, Y));
+                double q = rate_q(S, T, Y);
+                double h = rho * S->s.Q / S->s.cp * q;
+                sumYF += Y[S->s.fuel];
+                mass += rho;
+                hrr += h;
+                fuel += rho * q;
+                if (T > Tmax) Tmax = T;
+                if (y == yc && z == zc && h > best) { best = h; bestx = x; }
+            }
+    out[0] = section > 0.0 ? sumYF / (S->s.Y_in[S->s.fuel] * section) : 0.0;
+    out[1] = mass;
+    out[2] = hrr;
+    out[3] = fuel;
+    out[4] = Tmax;
+    out[5] = (double)bestx;
+    out[6] = nonfinite;
+    out[7] = nfluid;
+}
