@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Throughput of the coupled LB/FD step on GB300.
+
+One bench step = one coupled time step (pull-stream, FD scalar update,
+cumulant collision: the whole hot path, one fused kernel launch) over the
+whole batch.  Default workload: 16 2-D D2Q9 channels of widths 16..196 and
+length 1024 with isothermal walls, packed into one masked domain, mixed
+precision (FP32, FP64 Arrhenius above 1000 K).
+
+Timing: W warm-up steps, then K timed steps; before every timed step a
+256 MiB buffer is written to flush the L2 (the state is 104 MiB per
+buffer), and each step is bracketed by CUDA events on the launch stream.
+Under torchrun each rank runs its own replica (the channels are independent
+problems: weak scaling, no collective on the data path).
+
+--impl reference times the FP64 oracle (the plain CPU restatement of the
+method) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2304_05657_gb300 import inputs  # noqa: E402
+
+METRIC = "coupled MLUPS & HBM GB/s (% roofline); adjoint grad-steps/s vs plain FP64 GPU"
+FLUSH_BYTES = 256 << 20
+
+
+def workload(name: str, precision: str):
+    """(cfg, solid, T, Y, description) of a named workload."""
+    if name == "batched16x1024":
+        cfg, solid, T, Y, seg = inputs.batched_channels()
+        desc = "16 D2Q9 channels, widths 16..196 (step 12), length 1024, isothermal 300 K walls, 1 solid row between"
+    elif name == "channel256x32":
+        cfg, solid, T, Y = inputs.channel(nx=256, ny=32)
+        T, Y = inputs.ignition_fields(cfg, solid, 0, 20, burnt=False)
+        desc = "D2Q9 channel 256x32, adiabatic walls"
+    elif name == "burner2048x512":
+        cfg, solid, T, Y = inputs.cylinder_burner()
+        desc = "D2Q9 2048x512 staggered cylinders d=40 pitch 64, 373 K"
+    elif name == "porous512x256x256":
+        cfg, solid, T, Y = inputs.sphere_packing()
+        desc = "D3Q27 512x256x256 overlapping spheres r in [8,16], porosity 0.80"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    cfg["precision"] = precision
+    return cfg, solid, T, Y, desc
+
+
+def sample_workload(name: str, precision: str, length: int = 96):
+    """A bounded slice of the workload for the CPU oracle (same physics and
+    geometry rules, fewer cells)."""
+    if name == "batched16x1024":
+        cfg, solid, T, Y, seg = inputs.batched_channels(length=length)
+        return cfg, solid, T, Y, f"the 16 channels cut to length {length} ({1711 * length} cells)"
+    if name == "channel256x32":
+        cfg, solid, T, Y = inputs.channel(nx=256, ny=32)
+        T, Y = inputs.ignition_fields(cfg, solid, 0, 20, burnt=False)
+        return cfg, solid, T, Y, "the full 256x32 channel"
+    if name == "burner2048x512":
+        cfg, solid, T, Y = inputs.cylinder_burner(nx=256, ny=128, x_range=(64, 192))
+        return cfg, solid, T, Y, "a 256x128 crop of the burner geometry"
+    cfg, solid, T, Y = inputs.sphere_packing(nx=32, ny=16, nz=16, x_range=(4, 28), r_range=(2.0, 4.0))
+    return cfg, solid, T, Y, "a 32x16x16 sphere packing"
+
+
+def bytes_per_cell(cfg) -> int:
+    Q = 9 if cfg["dim"] == 2 else 27
+    e = 8 if cfg["precision"] == "fp64" else 4
+    return (Q + 1 + 5) * e * 2 + 1  # read + write every state value, read the mask byte
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: str, path: str):
+        self.path = path
+        self.proc = None
+        try:
+            self.f = open(path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits", "-lms", "20",
+                 "-i", gpu_index], stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.1)
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    """The oracle (FP64, single thread, plain C) on a bounded sample."""
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    # about 60 s of oracle work in total: cells per step scale as 1/(K+W)
+    length = int(max(4, min(1024, 60 * 4.0e5 / ((args.steps + args.warmup) * 1711))))
+    cfg, solid, T, Y, sdesc = sample_workload(args.workload, "fp64", length)
+    fluid = int((solid == 0).sum())
+    sim = oracle.Sim(cfg, solid)
+    sim.set_state(T, Y)
+    for _ in range(args.warmup):
+        sim.step(1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        sim.step(1)
+        times.append(time.perf_counter() - t0)
+    sec = float(np.sum(times))
+    value = fluid * args.steps / sec / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": args.workload, "sample": sdesc, "fluid_cells": fluid},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sdesc},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(args, precision):
+    """Oracle timing on a bounded sample (rank 0, N = 1 only), plus the
+    accuracy of the CUDA path on the same sample."""
+    import oracle
+
+    from paper_2304_05657_gb300 import lbfd
+
+    oracle.build()
+    cfg, solid, T, Y, sdesc = sample_workload(args.workload, "fp64")
+    fluid = int((solid == 0).sum())
+    sim = oracle.Sim(cfg, solid)
+    sim.set_state(T, Y)
+    steps = args.baseline_steps
+    t0 = time.perf_counter()
+    sim.step(steps)
+    sec = time.perf_counter() - t0
+    To, Yo, go = sim.get_state()
+    gpu = lbfd.Solver(dict(cfg, precision=precision), solid)
+    gpu.set_state(T, Y)
+    gpu.step(steps)
+    Tg, Yg, gg = gpu.get_state()
+    gpu.close()
+    err_T = float(np.linalg.norm(Tg - To) / np.linalg.norm(To))
+    errs = [float(np.linalg.norm(Yg[k] - Yo[k]) / np.linalg.norm(Yo[k])) for k in range(5)
+            if np.linalg.norm(Yo[k]) > 0]
+    err_Y = max(errs) if errs else float("nan")
+    return {"value": fluid * steps / sec / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{sdesc}, {steps} steps from the workload's initial state",
+            "gpu_rel_l2_vs_oracle": {"T": err_T, "Y_max": err_Y, "steps": steps}}
+
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2304_05657_gb300 import build as libbuild
+    from paper_2304_05657_gb300 import lbfd
+
+    if rank == 0:
+        libbuild.build()
+    if world > 1:
+        torch.distributed.barrier()
+    precision = args.precision
+    cfg, solid, T, Y, desc = workload(args.workload, precision)
+    stream = torch.cuda.current_stream()
+    s = lbfd.Solver(cfg, solid, stream=stream)
+    s.init_fields(T, Y)
+    fluid = int((solid == 0).sum())
+    ncell = solid.size
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def one_step(ev0=None, ev1=None):
+        flush.zero_()
+        if ev0 is not None:
+            ev0.record(stream)
+        s.step(1)
+        if ev1 is not None:
+            ev1.record(stream)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local if world > 1 else 0]
+    sampler = ClockSampler(gpu_index, os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
+                           if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/lbfd_clocks_{rank}.csv")
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    for i in range(args.steps):
+        one_step(ev0[i], ev1[i])
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    step_ms = np.array([a.elapsed_time(b) for a, b in zip(ev0, ev1)])
+    total_ms = float(step_ms.sum())
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    diag = s.diagnostics()
+
+    # end to end through the C ABI with pinned host buffers
+    nbytes = s.state_bytes()
+    host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    s.get_state_raw(host.data_ptr(), nbytes)
+    e2e_steps = min(args.steps, args.e2e_steps)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s.set_state_raw(host.data_ptr(), nbytes)
+        s.step(1)
+        s.get_state_raw(host.data_ptr(), nbytes)
+    torch.cuda.synchronize()
+    e2e_sec = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_sec], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_sec = float(t.item())
+
+    value = fluid * world * args.steps / (total_ms * 1e-3) / 1e6
+    e2e_value = fluid * world * e2e_steps / e2e_sec / 1e6
+    bpc = bytes_per_cell(cfg)
+    alg_bytes = fluid * bpc + (ncell - fluid) * 1
+    mean_s = float(step_ms.mean()) * 1e-3
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / mean_s / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if precision == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "description": desc, "cells": ncell, "fluid_cells": fluid,
+                   "precision": precision, "l2": "flushed before every timed step (256 MiB write)",
+                   "state_bytes_per_buffer": nbytes, "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                     "algorithmic_bytes_per_cell": bpc, "kernel": "step_kernel",
+                     "mean_launch_ms": mean_s * 1e3},
+        "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                "steps": e2e_steps, "api": "lbfd_set_state_raw + lbfd_step + lbfd_get_state_raw (pinned)"},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        "wall_ms_per_step_with_flush": 1e3 * t_wall / args.steps,
+        "diagnostics_after": {k: diag[k] for k in ("x_f", "T_max", "n_nonfinite")},
+    }
+    if rank == 0 and world == 1 and not args.no_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, precision)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    s.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="batched16x1024",
+                    choices=["batched16x1024", "channel256x32", "burner2048x512", "porous512x256x256"])
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--baseline-steps", type=int, default=40)
+    ap.add_argument("--no-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

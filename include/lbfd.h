@@ -1,0 +1,204 @@
+/*
+ * lbfd.h -- C ABI of the GB300 (sm_103a) library for the coupled time step
+ * of the hybrid low-Mach lattice Boltzmann / finite-difference solver of
+ * Hosseini & Thevenin, arXiv 2304.05657.
+ *
+ * One step advances, for every fluid cell, the pressure-based lattice
+ * Boltzmann populations g_i (Sec. II.B, Eq. 8-13) with the cumulant
+ * collision (Sec. II.C, Eq. 14-24) and the finite-difference temperature and
+ * species fields (Sec. II.A Eq. 1-7, Sec. II.D Eq. 26) with a single-step
+ * Arrhenius source, with half-way bounce-back walls, velocity inlet and
+ * convective outlet (Sec. III.A, Eq. 28, 31, 32) and ghost-node scalar
+ * boundaries (Sec. III.B, Eq. 34).  All of a step runs in CUDA kernels of
+ * this library; there is no CPU fallback: when no CUDA device is present
+ * lbfd_create returns LBFD_ECUDA.
+ *
+ * Conventions shared by every entry point
+ *   - Return value: LBFD_OK (0) or one of the LBFD_E* codes below;
+ *     lbfd_strerror() gives a static message.  A CUDA failure is reported
+ *     as LBFD_ECUDA and its text is kept in lbfd_last_error().
+ *   - Units are lattice units (dr = dt = 1, cs^2 = 1/3) except the
+ *     thermochemistry in lbfd_mechanism, which is SI; the step length
+ *     lbfd_params.dt [s] maps the pre-exponential factor to A*dt per step.
+ *   - Cell index: c = x + nx*(y + ny*z), x fastest.  Populations are
+ *     numbered i = (cx+1) + 3(cy+1) [+ 9(cz+1) in 3-D] with c_i in {-1,0,1}.
+ *   - Every host array passed in is copied before the call returns; the
+ *     library never keeps a caller pointer.  Output arrays are owned by the
+ *     caller.  The handle owns all device memory it allocates.
+ *   - Calls on one handle are not thread-safe; distinct handles are
+ *     independent.
+ */
+#ifndef LBFD_H
+#define LBFD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define LBFD_OK 0
+#define LBFD_EINVAL 1     /* bad argument (null pointer, size, enum value) */
+#define LBFD_ENOMEM 2     /* device or host allocation failed */
+#define LBFD_ECUDA 3      /* a CUDA call failed (see lbfd_last_error) */
+#define LBFD_ENONFINITE 4 /* a fluid cell holds a non-finite value */
+#define LBFD_ETIMEOUT 5   /* a bounded device wait gave up */
+#define LBFD_EUNSTABLE 6  /* parameters violate a stability limit */
+#define LBFD_ENOTSUP 7    /* valid request this build does not support */
+
+/* boundary type of each domain face (Sec. III) */
+#define LBFD_BC_PERIODIC 0
+#define LBFD_BC_WALL_ADIABATIC 1   /* half-way bounce-back, Neumann T and Y */
+#define LBFD_BC_WALL_ISOTHERMAL 2  /* half-way bounce-back, Dirichlet T = T_wall */
+#define LBFD_BC_INLET 3            /* Eq. 31 velocity inlet, Dirichlet T_in, Y_in */
+#define LBFD_BC_OUTLET 4           /* Eq. 32 convective outlet, zero-gradient T, Y */
+#define LBFD_BC_OUTLET_PRESSURE 5  /* constant P_h = 0 outlet (Sec. IV.A, IV.C) by anti-bounce-back:
+                                      g_i = -g*_ibar + 2 (even part of g^eq at P_h = 0, rho and u of
+                                      the cell); zero-gradient T, Y */
+
+/* arithmetic of the step */
+#define LBFD_FP64 0  /* FP64 storage and arithmetic */
+#define LBFD_MIXED 1 /* FP32 storage and arithmetic; FP64 Arrhenius above T_fp64 */
+
+/* number of species the kernels are built for */
+#define LBFD_NSP 5
+
+/* fields for lbfd_read_field */
+#define LBFD_FIELD_T 0
+#define LBFD_FIELD_Y0 1    /* Y_k is LBFD_FIELD_Y0 + k */
+#define LBFD_FIELD_UX 6    /* sum_i c_i g*_i / (rho cs^2), rho of the stored T, Y */
+#define LBFD_FIELD_UY 7
+#define LBFD_FIELD_UZ 8
+#define LBFD_FIELD_PH 9    /* sum_i g*_i */
+#define LBFD_FIELD_RHO 10  /* EOS density of the stored T, Y */
+#define LBFD_FIELD_HRR 11  /* rho (Q/cp) A dt Y_F Y_O exp(-Ta/T) [K per step] */
+#define LBFD_FIELD_G0 16   /* stored (post-collision) population i is G0 + i */
+
+/* diagnostics vector of lbfd_diagnostics */
+#define LBFD_DIAG_XF 0        /* sum Y_F / (Y_F,in * fluid cells at x = 0) [cells] */
+#define LBFD_DIAG_MASS 1      /* sum rho over fluid cells */
+#define LBFD_DIAG_HRR 2       /* sum of LBFD_FIELD_HRR over fluid cells */
+#define LBFD_DIAG_FUEL 3      /* sum rho A dt Y_F Y_O exp(-Ta/T) (fuel consumed per step) */
+#define LBFD_DIAG_TMAX 4      /* maximum T over fluid cells */
+#define LBFD_DIAG_XHRR 5      /* x of the largest HRR on the line y = ny/2, z = nz/2 */
+#define LBFD_DIAG_NONFINITE 6 /* fluid cells holding a non-finite value */
+#define LBFD_DIAG_NFLUID 7    /* number of fluid cells */
+#define LBFD_NDIAG 8
+
+typedef struct lbfd_handle lbfd_handle;
+
+/* Grid and face boundary types.  dim = 2 (D2Q9, nz ignored) or 3 (D3Q27).
+ * bc[] and T_wall[] are per face in the order -x, +x, -y, +y, -z, +z;
+ * T_wall is read for LBFD_BC_WALL_ISOTHERMAL faces only [K]. */
+typedef struct lbfd_grid {
+    int dim, nx, ny, nz;
+    int bc[6];
+    double T_wall[6];
+} lbfd_grid;
+
+/* Single-step global mechanism Fuel + ... -> products (the stand-in for the
+ * Cantera kinetics of Sec. II.D).  Rate per unit mass of fuel:
+ * q = A max(Y_F,0) max(Y_O,0) exp(-Ta/T); species k gains
+ * nu_k W_k / (-nu_F W_F) q, temperature gains (Q/cp) q.
+ * W [g/mol], nu_stoich < 0 for reactants, A [1/s], Ta [K], Q [J/kg fuel],
+ * cp [J/kg/K] equal for all species, Le_k constant Lewis numbers. */
+typedef struct lbfd_mechanism {
+    int n_species;
+    double W[8];
+    double nu_stoich[8];
+    int fuel, oxidiser;
+    double A, Ta, Q, cp;
+    double Le[8];
+} lbfd_mechanism;
+
+/* Physical and numerical parameters.
+ * nu: kinematic viscosity (lattice); omega_s = 1/(nu/cs^2 + 1/2) (Eq. 18).
+ * Pr: alpha = nu/Pr;  D_k = alpha/Le_k.
+ * omega_bulk: rate of the second-order trace (<= 0: omega_s).
+ * omega_hi: rate of cumulants of order >= 3 (Eq. 23).
+ * u_in, T_in [K], Y_in: inlet state; (T_in, Y_in) is the EOS reference
+ *   (rho = 1 there).
+ * T_solid [K], solid_isothermal: thermal condition of solid-mask cells.
+ * dx [m], dt [s]: physical size of a cell and of a step.
+ * T_fp64 [K]: LBFD_MIXED evaluates the Arrhenius source in FP64 where T > T_fp64.
+ * weno_eps: WENO3 epsilon for species (temperature: weno_eps*T_in^2).
+ * precision: LBFD_FP64 or LBFD_MIXED.
+ * poiseuille_inlet: 2-D -x/+x inlet with parabolic profile of mean u_in. */
+typedef struct lbfd_params {
+    double nu, Pr, omega_bulk, omega_hi;
+    double u_in, T_in, Y_in[8];
+    double T_solid;
+    int solid_isothermal;
+    double dx, dt;
+    double T_fp64;
+    double weno_eps;
+    int precision;
+    int poiseuille_inlet;
+} lbfd_params;
+
+/* Create a solver.  solid_mask: nx*ny*nz bytes on the host, nonzero = solid
+ * (copied).  Allocates the double-buffered state on the current CUDA device
+ * and initialises every cell to T = T_in, Y = Y_in, g = 0.
+ * Errors: EINVAL (null pointer, sizes, bc values, n_species != LBFD_NSP is
+ * ENOTSUP), EUNSTABLE (omega outside (0,2), |u_in| >= cs, explicit Euler
+ * diffusion limit alpha*sum_axes(64/12) >= 2), ENOMEM, ECUDA. */
+int lbfd_create(const lbfd_grid* grid, const uint8_t* solid_mask,
+                const lbfd_mechanism* mech, const lbfd_params* params,
+                lbfd_handle** out);
+
+/* Release the handle and its device memory (NULL is accepted). */
+int lbfd_destroy(lbfd_handle* h);
+
+/* Run subsequent work on this CUDA stream (a cudaStream_t passed as void*;
+ * NULL selects the legacy default stream).  The caller keeps ownership. */
+int lbfd_set_stream(lbfd_handle* h, void* cuda_stream);
+
+/* Set the scalar fields from host FP64 arrays T[N] and Y[nsp][N] and reset
+ * the populations to g = 0 (the rest state, P_h = 0, u = 0).  Synchronous. */
+int lbfd_init_fields(lbfd_handle* h, const double* T, const double* Y);
+
+/* Set the full state from host FP64 arrays (g: [Q][N] post-collision
+ * populations; NULL keeps them at 0).  Synchronous. */
+int lbfd_set_state(lbfd_handle* h, const double* T, const double* Y, const double* g);
+
+/* Advance n coupled steps (Sec. II), asynchronously on the handle's stream.
+ * Each step is one launch of the fused kernel. */
+int lbfd_step(lbfd_handle* h, int n);
+
+/* Copy one field (LBFD_FIELD_*) of all N cells to host FP64 out[N].
+ * Synchronises the handle's stream. */
+int lbfd_read_field(lbfd_handle* h, int field, double* out);
+
+/* Reductions over fluid cells in FP64 (warp shuffles + atomics), out[LBFD_NDIAG]
+ * as listed above.  Synchronises; returns LBFD_ENONFINITE (after filling out)
+ * when a fluid cell holds a non-finite value. */
+int lbfd_diagnostics(lbfd_handle* h, double* out);
+
+/* Flame position x_f [m] (LBFD_DIAG_XF times dx), fluid mass sum rho and
+ * total heat release (LBFD_DIAG_HRR).  Any pointer may be NULL. */
+int lbfd_flame_position(lbfd_handle* h, double* x_f, double* mass, double* heat_release);
+
+/* Raw state in storage precision (4 or 8 bytes per value):
+ * layout g[Q][N], T[N], Y[nsp][N], contiguous; lbfd_state_bytes gives the size.
+ * The host buffer may be pageable or pinned; the copy is ordered on the
+ * handle's stream and the call synchronises it. */
+size_t lbfd_state_bytes(const lbfd_handle* h);
+int lbfd_get_state_raw(lbfd_handle* h, void* host_dst, size_t bytes);
+int lbfd_set_state_raw(lbfd_handle* h, const void* host_src, size_t bytes);
+
+/* Counters and sizes. */
+long long lbfd_steps_done(const lbfd_handle* h);
+long long lbfd_num_cells(const lbfd_handle* h);
+int lbfd_num_populations(const lbfd_handle* h);
+
+const char* lbfd_strerror(int status);
+/* text of the last CUDA failure on this thread ("" when none) */
+const char* lbfd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBFD_H */

@@ -1,0 +1,426 @@
+// lbfd_api.cu -- host side of the C ABI declared in include/lbfd.h.
+//
+// The handle owns a double-buffered device state (populations and scalar
+// fields in SoA planes), the solid mask, a small reduction scratch and a
+// read-out buffer.  All arithmetic of a step runs in the kernels of
+// lbfd_step.cu; this file validates, converts parameters to lattice units,
+// moves data and launches.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/lbfd.h"
+#include "lbfd_internal.h"
+
+using lbfd::StateView;
+using lbfd::StepParams;
+
+struct lbfd_handle {
+    lbfd_grid grid;
+    lbfd_mechanism mech;
+    lbfd_params prm;
+    int dim, Q, precision;
+    long long ncell, stride;
+    size_t esz;           // bytes per stored value
+    size_t planes;        // Q + 1 + NSP
+    void* buf[2];         // device state buffers
+    int cur;
+    uint8_t* solid;       // device mask
+    double* red;          // device reduction scratch
+    double* tmp;          // device read-out buffer (ncell doubles)
+    cudaStream_t stream;
+    long long steps;
+    StepParams<double> Pd;
+    StepParams<float> Pf;
+};
+
+namespace {
+
+thread_local char g_last_error[512] = "";
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    snprintf(g_last_error, sizeof g_last_error, "%s: %s", what, cudaGetErrorString(e));
+    return LBFD_ECUDA;
+}
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);        \
+    } while (0)
+
+StateView view(const lbfd_handle* h, int which)
+{
+    char* base = (char*)h->buf[which];
+    const size_t plane = (size_t)h->stride * h->esz;
+    StateView v;
+    v.g = base;
+    v.T = base + plane * h->Q;
+    v.Y = base + plane * (h->Q + 1);
+    return v;
+}
+
+template <typename R>
+void fill_params(const lbfd_handle* h, StepParams<R>& P)
+{
+    const lbfd_grid& G = h->grid;
+    const lbfd_mechanism& M = h->mech;
+    const lbfd_params& p = h->prm;
+    memset(&P, 0, sizeof P);
+    P.dim = G.dim;
+    P.nx = G.nx;
+    P.ny = G.ny;
+    P.nz = G.dim == 3 ? G.nz : 1;
+    P.ncell = h->ncell;
+    P.N = h->stride;
+    for (int f = 0; f < 6; ++f) {
+        P.bc[f] = (f < 2 * G.dim) ? G.bc[f] : LBFD_BC_PERIODIC;
+        P.T_wall[f] = (R)G.T_wall[f];
+    }
+    const double cs2 = 1.0 / 3.0;
+    const double alpha = p.nu / p.Pr;
+    double invW_in = 0.0;
+    for (int k = 0; k < lbfd::NSP; ++k) invW_in += p.Y_in[k] / M.W[k];
+    const double yF = -M.nu_stoich[M.fuel] * M.W[M.fuel];
+    for (int k = 0; k < lbfd::NSP; ++k) {
+        P.inv_Wk[k] = (R)(1.0 / M.W[k]);
+        P.yield[k] = (R)(M.nu_stoich[k] * M.W[k] / yF);
+        P.a_diff[k] = (R)(alpha / M.Le[k] * M.W[k]);
+        P.Y_in[k] = (R)p.Y_in[k];
+    }
+    P.fuel = M.fuel;
+    P.oxid = M.oxidiser;
+    P.A_lat = (R)(M.A * p.dt);
+    P.Ta = (R)M.Ta;
+    P.Q_cp = (R)(M.Q / M.cp);
+    P.A_lat_d = M.A * p.dt;
+    P.Ta_d = M.Ta;
+    P.T_fp64 = (R)p.T_fp64;
+    const double omega_s = 1.0 / (p.nu / cs2 + 0.5);  // Eq. 18 read as 1/tau
+    P.omega_s = (R)omega_s;
+    P.omega_b = (R)(p.omega_bulk > 0.0 ? p.omega_bulk : omega_s);
+    P.omega_hi = (R)p.omega_hi;
+    P.alpha = (R)alpha;
+    P.u_in = (R)p.u_in;
+    P.T_in = (R)p.T_in;
+    P.invW_in = (R)invW_in;
+    P.rho_in = (R)1.0;  // EOS reference state (T_in, Y_in)
+    P.T_solid = (R)p.T_solid;
+    P.solid_isothermal = p.solid_isothermal;
+    P.poiseuille = p.poiseuille_inlet;
+    P.epsY = (R)p.weno_eps;
+    P.epsT = (R)(p.weno_eps * p.T_in * p.T_in);
+    P.cs = (R)sqrt(cs2);
+}
+
+int validate(const lbfd_grid* G, const lbfd_mechanism* M, const lbfd_params* p)
+{
+    if (G->dim != 2 && G->dim != 3) return LBFD_EINVAL;
+    if (G->nx < 1 || G->ny < 1 || (G->dim == 3 && G->nz < 1)) return LBFD_EINVAL;
+    if ((long long)G->nx * G->ny * (G->dim == 3 ? G->nz : 1) > (1ll << 40)) return LBFD_EINVAL;
+    for (int f = 0; f < 2 * G->dim; ++f) {
+        if (G->bc[f] < LBFD_BC_PERIODIC || G->bc[f] > LBFD_BC_OUTLET_PRESSURE) return LBFD_EINVAL;
+        const int o = f ^ 1;  // periodic faces come in pairs
+        if ((G->bc[f] == LBFD_BC_PERIODIC) != (G->bc[o] == LBFD_BC_PERIODIC)) return LBFD_EINVAL;
+        if (G->bc[f] == LBFD_BC_WALL_ISOTHERMAL && !(G->T_wall[f] > 0.0)) return LBFD_EINVAL;
+    }
+    if (M->n_species != lbfd::NSP) return LBFD_ENOTSUP;
+    if (M->fuel < 0 || M->fuel >= lbfd::NSP || M->oxidiser < 0 || M->oxidiser >= lbfd::NSP ||
+        M->fuel == M->oxidiser)
+        return LBFD_EINVAL;
+    if (!(M->nu_stoich[M->fuel] < 0.0)) return LBFD_EINVAL;
+    for (int k = 0; k < lbfd::NSP; ++k)
+        if (!(M->W[k] > 0.0) || !(M->Le[k] > 0.0)) return LBFD_EINVAL;
+    if (!(M->A >= 0.0) || !(M->Ta >= 0.0) || !(M->cp > 0.0) || !std::isfinite(M->Q)) return LBFD_EINVAL;
+    if (!(p->T_in > 0.0) || !(p->dt > 0.0) || !(p->Pr > 0.0) || !(p->weno_eps > 0.0)) return LBFD_EINVAL;
+    if (p->precision != LBFD_FP64 && p->precision != LBFD_MIXED) return LBFD_EINVAL;
+    double ysum = 0.0;
+    for (int k = 0; k < lbfd::NSP; ++k) ysum += p->Y_in[k];
+    if (fabs(ysum - 1.0) > 1e-6) return LBFD_EINVAL;
+    // stability limits
+    if (!(p->nu > 0.0)) return LBFD_EUNSTABLE;
+    const double omega_s = 1.0 / (3.0 * p->nu + 0.5);
+    if (!(omega_s > 0.0 && omega_s < 2.0)) return LBFD_EUNSTABLE;
+    if (p->omega_bulk > 0.0 && !(p->omega_bulk < 2.0)) return LBFD_EUNSTABLE;
+    if (!(p->omega_hi > 0.0 && p->omega_hi < 2.0)) return LBFD_EUNSTABLE;
+    if (!(fabs(p->u_in) < sqrt(1.0 / 3.0))) return LBFD_EUNSTABLE;
+    double dmax = p->nu / p->Pr;
+    for (int k = 0; k < lbfd::NSP; ++k) dmax = fmax(dmax, p->nu / p->Pr / M->Le[k]);
+    // explicit Euler with the 4th-order Laplacian: |eigenvalue| <= dim * 64/12
+    if (!(dmax * G->dim * 64.0 / 12.0 < 2.0)) return LBFD_EUNSTABLE;
+    return LBFD_OK;
+}
+
+void free_handle(lbfd_handle* h)
+{
+    if (!h) return;
+    for (int b = 0; b < 2; ++b)
+        if (h->buf[b]) cudaFree(h->buf[b]);
+    if (h->solid) cudaFree(h->solid);
+    if (h->red) cudaFree(h->red);
+    if (h->tmp) cudaFree(h->tmp);
+    delete h;
+}
+
+// host values (double, dense planes) -> storage precision -> device buffer `which`
+int upload_planes(lbfd_handle* h, int which, int first_plane, int nplanes, const double* src)
+{
+    const size_t n = (size_t)h->ncell;
+    std::vector<char> stage(n * h->esz * nplanes);
+    if (h->precision == LBFD_FP64) {
+        memcpy(stage.data(), src, n * sizeof(double) * nplanes);
+    } else {
+        float* d = (float*)stage.data();
+        for (size_t i = 0; i < n * nplanes; ++i) d[i] = (float)src[i];
+    }
+    char* dst = (char*)h->buf[which] + (size_t)first_plane * h->stride * h->esz;
+    CK(cudaMemcpy2DAsync(dst, (size_t)h->stride * h->esz, stage.data(), n * h->esz, n * h->esz, nplanes,
+                         cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LBFD_OK;
+}
+
+int sync_other_buffer(lbfd_handle* h)
+{
+    const size_t bytes = h->planes * (size_t)h->stride * h->esz;
+    CK(cudaMemcpyAsync(h->buf[h->cur ^ 1], h->buf[h->cur], bytes, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LBFD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbfd_strerror(int s)
+{
+    switch (s) {
+    case LBFD_OK: return "ok";
+    case LBFD_EINVAL: return "invalid argument";
+    case LBFD_ENOMEM: return "out of memory";
+    case LBFD_ECUDA: return "CUDA error";
+    case LBFD_ENONFINITE: return "non-finite value in a fluid cell";
+    case LBFD_ETIMEOUT: return "bounded device wait timed out";
+    case LBFD_EUNSTABLE: return "parameters violate a stability limit";
+    case LBFD_ENOTSUP: return "not supported by this build";
+    default: return "unknown status";
+    }
+}
+
+const char* lbfd_last_error(void) { return g_last_error; }
+
+int lbfd_create(const lbfd_grid* grid, const uint8_t* solid_mask, const lbfd_mechanism* mech,
+                const lbfd_params* params, lbfd_handle** out)
+{
+    if (!grid || !mech || !params || !out) return LBFD_EINVAL;
+    *out = nullptr;
+    int st = validate(grid, mech, params);
+    if (st != LBFD_OK) return st;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev < 1) {
+        snprintf(g_last_error, sizeof g_last_error, "no CUDA device: %s",
+                 e == cudaSuccess ? "device count is 0" : cudaGetErrorString(e));
+        return LBFD_ECUDA;
+    }
+    lbfd_handle* h = new (std::nothrow) lbfd_handle();
+    if (!h) return LBFD_ENOMEM;
+    h->grid = *grid;
+    if (grid->dim == 2) h->grid.nz = 1;
+    h->mech = *mech;
+    h->prm = *params;
+    h->dim = grid->dim;
+    h->Q = grid->dim == 2 ? 9 : 27;
+    h->precision = params->precision;
+    h->ncell = (long long)h->grid.nx * h->grid.ny * h->grid.nz;
+    h->stride = (h->ncell + 63) / 64 * 64;  // 256-byte aligned FP32 planes
+    h->esz = h->precision == LBFD_FP64 ? 8 : 4;
+    h->planes = (size_t)h->Q + 1 + lbfd::NSP;
+    h->stream = nullptr;
+    const size_t bytes = h->planes * (size_t)h->stride * h->esz;
+    for (int b = 0; b < 2; ++b) {
+        e = cudaMalloc(&h->buf[b], bytes);
+        if (e != cudaSuccess) {
+            free_handle(h);
+            cuda_fail(e, "cudaMalloc(state)");
+            return LBFD_ENOMEM;
+        }
+    }
+    if ((e = cudaMalloc(&h->solid, (size_t)h->ncell)) != cudaSuccess ||
+        (e = cudaMalloc(&h->red, lbfd::RED_WORDS * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&h->tmp, (size_t)h->ncell * sizeof(double))) != cudaSuccess) {
+        free_handle(h);
+        cuda_fail(e, "cudaMalloc");
+        return LBFD_ENOMEM;
+    }
+    fill_params(h, h->Pd);
+    fill_params(h, h->Pf);
+    // mask
+    std::vector<uint8_t> m((size_t)h->ncell, 0);
+    if (solid_mask)
+        for (long long c = 0; c < h->ncell; ++c) m[c] = solid_mask[c] ? 1 : 0;
+    if ((e = cudaMemcpy(h->solid, m.data(), (size_t)h->ncell, cudaMemcpyHostToDevice)) != cudaSuccess) {
+        free_handle(h);
+        return cuda_fail(e, "cudaMemcpy(mask)");
+    }
+    // initial state: T_in, Y_in, g = 0
+    h->cur = 0;
+    if ((e = cudaMemset(h->buf[0], 0, bytes)) != cudaSuccess) {
+        free_handle(h);
+        return cuda_fail(e, "cudaMemset");
+    }
+    std::vector<double> TY((size_t)h->ncell * (1 + lbfd::NSP));
+    for (long long c = 0; c < h->ncell; ++c) TY[c] = params->T_in;
+    for (int k = 0; k < lbfd::NSP; ++k)
+        for (long long c = 0; c < h->ncell; ++c) TY[(size_t)(k + 1) * h->ncell + c] = params->Y_in[k];
+    st = upload_planes(h, 0, h->Q, 1 + lbfd::NSP, TY.data());
+    if (st == LBFD_OK) st = sync_other_buffer(h);
+    if (st != LBFD_OK) {
+        free_handle(h);
+        return st;
+    }
+    *out = h;
+    return LBFD_OK;
+}
+
+int lbfd_destroy(lbfd_handle* h)
+{
+    if (!h) return LBFD_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    free_handle(h);
+    return LBFD_OK;
+}
+
+int lbfd_set_stream(lbfd_handle* h, void* s)
+{
+    if (!h) return LBFD_EINVAL;
+    h->stream = (cudaStream_t)s;
+    return LBFD_OK;
+}
+
+int lbfd_set_state(lbfd_handle* h, const double* T, const double* Y, const double* g)
+{
+    if (!h || !T || !Y) return LBFD_EINVAL;
+    const size_t n = (size_t)h->ncell;
+    std::vector<double> all(n * h->planes, 0.0);
+    if (g) memcpy(all.data(), g, n * h->Q * sizeof(double));
+    memcpy(all.data() + n * h->Q, T, n * sizeof(double));
+    memcpy(all.data() + n * (h->Q + 1), Y, n * lbfd::NSP * sizeof(double));
+    int st = upload_planes(h, h->cur, 0, (int)h->planes, all.data());
+    if (st != LBFD_OK) return st;
+    return sync_other_buffer(h);
+}
+
+int lbfd_init_fields(lbfd_handle* h, const double* T, const double* Y)
+{
+    return lbfd_set_state(h, T, Y, nullptr);
+}
+
+int lbfd_step(lbfd_handle* h, int n)
+{
+    if (!h || n < 0) return LBFD_EINVAL;
+    for (int it = 0; it < n; ++it) {
+        cudaError_t e = lbfd::launch_step(h->dim, h->precision, h->Pd, h->Pf, view(h, h->cur), view(h, h->cur ^ 1),
+                                          h->solid, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
+        h->cur ^= 1;
+        h->steps++;
+    }
+    return LBFD_OK;
+}
+
+int lbfd_read_field(lbfd_handle* h, int field, double* out)
+{
+    if (!h || !out) return LBFD_EINVAL;
+    const bool ok = (field >= 0 && field <= LBFD_FIELD_HRR) ||
+                    (field >= LBFD_FIELD_G0 && field < LBFD_FIELD_G0 + h->Q);
+    if (!ok) return LBFD_EINVAL;
+    CK(lbfd::launch_field(h->dim, h->precision, h->Pd, view(h, h->cur), h->solid, field, h->tmp, h->stream));
+    CK(cudaMemcpyAsync(out, h->tmp, (size_t)h->ncell * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LBFD_OK;
+}
+
+int lbfd_diagnostics(lbfd_handle* h, double* out)
+{
+    if (!h || !out) return LBFD_EINVAL;
+    double r[lbfd::RED_WORDS];
+    CK(lbfd::launch_diagnostics(h->dim, h->precision, h->Pd, view(h, h->cur), h->solid, h->red, h->stream));
+    CK(cudaMemcpyAsync(r, h->red, sizeof r, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    unsigned long long u[lbfd::RED_WORDS];
+    memcpy(u, r, sizeof r);
+    const double section = (double)u[7];
+    const double yf_in = h->prm.Y_in[h->mech.fuel];
+    out[LBFD_DIAG_XF] = section > 0.0 ? r[0] / (yf_in * section) : 0.0;
+    out[LBFD_DIAG_MASS] = r[1];
+    out[LBFD_DIAG_HRR] = r[2];
+    out[LBFD_DIAG_FUEL] = r[3];
+    {
+        const unsigned long long k = u[4];
+        double t;
+        if (k == 0ull) {
+            t = -INFINITY;
+        } else {
+            const unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+            memcpy(&t, &b, sizeof t);
+        }
+        out[LBFD_DIAG_TMAX] = t;
+    }
+    out[LBFD_DIAG_XHRR] = r[9];
+    out[LBFD_DIAG_NONFINITE] = (double)u[5];
+    out[LBFD_DIAG_NFLUID] = (double)u[6];
+    return u[5] ? LBFD_ENONFINITE : LBFD_OK;
+}
+
+int lbfd_flame_position(lbfd_handle* h, double* x_f, double* mass, double* heat_release)
+{
+    double d[LBFD_NDIAG];
+    int st = lbfd_diagnostics(h, d);
+    if (st != LBFD_OK && st != LBFD_ENONFINITE) return st;
+    if (x_f) *x_f = d[LBFD_DIAG_XF] * h->prm.dx;
+    if (mass) *mass = d[LBFD_DIAG_MASS];
+    if (heat_release) *heat_release = d[LBFD_DIAG_HRR];
+    return st;
+}
+
+size_t lbfd_state_bytes(const lbfd_handle* h)
+{
+    return h ? h->planes * (size_t)h->ncell * h->esz : 0;
+}
+
+int lbfd_get_state_raw(lbfd_handle* h, void* dst, size_t bytes)
+{
+    if (!h || !dst || bytes != lbfd_state_bytes(h)) return LBFD_EINVAL;
+    const size_t w = (size_t)h->ncell * h->esz;
+    CK(cudaMemcpy2DAsync(dst, w, h->buf[h->cur], (size_t)h->stride * h->esz, w, h->planes, cudaMemcpyDeviceToHost,
+                         h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LBFD_OK;
+}
+
+int lbfd_set_state_raw(lbfd_handle* h, const void* src, size_t bytes)
+{
+    if (!h || !src || bytes != lbfd_state_bytes(h)) return LBFD_EINVAL;
+    const size_t w = (size_t)h->ncell * h->esz;
+    CK(cudaMemcpy2DAsync(h->buf[h->cur], (size_t)h->stride * h->esz, src, w, w, h->planes, cudaMemcpyHostToDevice,
+                         h->stream));
+    // the other buffer too: the step never rewrites solid cells
+    const size_t all = h->planes * (size_t)h->stride * h->esz;
+    CK(cudaMemcpyAsync(h->buf[h->cur ^ 1], h->buf[h->cur], all, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LBFD_OK;
+}
+
+long long lbfd_steps_done(const lbfd_handle* h) { return h ? h->steps : -1; }
+long long lbfd_num_cells(const lbfd_handle* h) { return h ? h->ncell : -1; }
+int lbfd_num_populations(const lbfd_handle* h) { return h ? h->Q : -1; }
+
+}  // extern "C"

@@ -1,0 +1,371 @@
+// lbfd_device.cuh -- device-side building blocks of the fused coupled step:
+// lattice constants, boundary classification, pull streaming with boundary
+// rules, FD line gathering with ghost nodes, FD operators, and the cumulant
+// collision.  Written for sm_103a; templated on the compute type R (double
+// for the FP64 form, float for the mixed form).
+//
+// Method: Hosseini & Thevenin, arXiv 2304.05657, Sec. II-III.
+#pragma once
+#include <cstdint>
+
+#include "lbfd_params.h"
+
+namespace lbfd {
+
+enum { BC_PERIODIC = 0, BC_WALL_ADIABATIC = 1, BC_WALL_ISOTHERMAL = 2, BC_INLET = 3, BC_OUTLET = 4,
+       BC_OUTLET_PRESSURE = 5 };
+enum { PT_FLUID = 0, PT_SOLID = 16 };
+// ghost modes of an FD line point
+enum { G_DIRECT = 0, G_NEUMANN = 1, G_DIRICHLET_T = 2, G_INLET = 3 };
+
+// ---------------------------------------------------------------------------
+// lattice: D1Q3 tensor products, i = (cx+1) + 3(cy+1) + 9(cz+1)
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int cx_of(int i) { return i % 3 - 1; }
+__host__ __device__ constexpr int cy_of(int i) { return (i / 3) % 3 - 1; }
+__host__ __device__ constexpr int cz_of(int i) { return i / 9 - 1; }
+template <typename R>
+__host__ __device__ constexpr R w1(int c) { return c == 0 ? R(2) / R(3) : R(1) / R(6); }
+template <int DIM, typename R>
+__host__ __device__ constexpr R weight(int i)
+{
+    return DIM == 2 ? w1<R>(cx_of(i)) * w1<R>(cy_of(i))
+                    : w1<R>(cx_of(i)) * w1<R>(cy_of(i)) * w1<R>(cz_of(i));
+}
+template <int DIM>
+__host__ __device__ constexpr int ccomp(int i, int a)
+{
+    return a == 0 ? cx_of(i) : (a == 1 ? cy_of(i) : (DIM == 3 ? cz_of(i) : 0));
+}
+template <int DIM>
+__host__ __device__ constexpr int opposite(int i) { return (DIM == 2 ? 8 : 26) - i; }
+
+// ---------------------------------------------------------------------------
+// geometry
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ int extent(const StepParams<R>& P, int a)
+{
+    return a == 0 ? P.nx : (a == 1 ? P.ny : P.nz);
+}
+
+template <typename R>
+__device__ __forceinline__ long long cell_of(const StepParams<R>& P, int x, int y, int z)
+{
+    return (long long)x + (long long)P.nx * ((long long)y + (long long)P.ny * z);
+}
+
+// Classify a point that differs from a fluid cell along one or more axes.
+// Periodic axes wrap; a crossed non-periodic face returns its bc type.
+template <int DIM, typename R>
+__device__ __forceinline__ int classify(const StepParams<R>& P, int q[3], const uint8_t* __restrict__ solid,
+                                        long long* idx, int* face)
+{
+    int wall = -1;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        int n = extent(P, a);
+        int f = -1;
+        if (q[a] < 0) f = 2 * a;
+        else if (q[a] >= n) f = 2 * a + 1;
+        if (f < 0) continue;
+        if (P.bc[f] == BC_PERIODIC) q[a] = ((q[a] % n) + n) % n;  // extents may be < 3
+        else if (wall < 0) wall = f;
+    }
+    if (wall >= 0) {
+        *face = wall;
+        return P.bc[wall];
+    }
+    *idx = cell_of(P, q[0], q[1], DIM == 3 ? q[2] : 0);
+    return solid[*idx] ? PT_SOLID : PT_FLUID;
+}
+
+// ---------------------------------------------------------------------------
+// thermochemistry
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R inv_molar_mass(const StepParams<R>& P, const R* Y)
+{
+    R s = R(0);
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) s += Y[k] * P.inv_Wk[k];
+    return s;
+}
+
+// EOS at constant P_0 (Sec. II.A) with rho(T_in, Y_in) = 1
+template <typename R>
+__device__ __forceinline__ R eos(const StepParams<R>& P, R T, R invW)
+{
+    return P.T_in * P.invW_in / (T * invW);
+}
+
+// Single-step rate per unit mass of fuel, per step.  The mixed form
+// evaluates it in FP64 where T > T_fp64.
+template <typename R>
+__device__ __forceinline__ R arrhenius(const StepParams<R>& P, R T, R yf, R yo)
+{
+    yf = yf > R(0) ? yf : R(0);
+    yo = yo > R(0) ? yo : R(0);
+    if (sizeof(R) == 4 && T > P.T_fp64) {
+        double q = P.A_lat_d * (double)yf * (double)yo * exp(-P.Ta_d / (double)T);
+        return (R)q;
+    }
+    if (sizeof(R) == 4) return P.A_lat * yf * yo * (R)expf(-(float)(P.Ta / T));
+    return P.A_lat * yf * yo * (R)exp(-(double)(P.Ta / T));
+}
+
+// ---------------------------------------------------------------------------
+// FD operators (Sec. II.D), unit spacing, v[0..4] = phi_{i-2..i+2}
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R fd_d1(const R* v)  // 4th-order central first derivative
+{
+    return (v[0] - v[4] + R(8) * (v[3] - v[1])) * (R(1) / R(12));
+}
+template <typename R>
+__device__ __forceinline__ R fd_d2(const R* v)  // 4th-order central second derivative
+{
+    return (R(16) * (v[1] + v[3]) - (v[0] + v[4]) - R(30) * v[2]) * (R(1) / R(12));
+}
+template <typename R>
+__device__ __forceinline__ R fd_c2(const R* v)  // centred 2nd order
+{
+    return R(0.5) * (v[3] - v[1]);
+}
+
+// WENO3 face value: a far upwind, b upwind cell, c downwind cell
+template <typename R>
+__device__ __forceinline__ R weno3_face(R a, R b, R c, R eps)
+{
+    R q0 = R(1.5) * b - R(0.5) * a;
+    R q1 = R(0.5) * (b + c);
+    R e0 = eps + (b - a) * (b - a);
+    R e1 = eps + (c - b) * (c - b);
+    // alpha_0 = (1/3)/e0^2, alpha_1 = (2/3)/e1^2; the common factor is dropped
+    R a0 = e1 * e1;
+    R a1 = R(2) * e0 * e0;
+    return (a0 * q0 + a1 * q1) / (a0 + a1);
+}
+template <typename R>
+__device__ __forceinline__ R weno3_deriv(const R* v, R u, R eps)
+{
+    if (u >= R(0)) return weno3_face(v[1], v[2], v[3], eps) - weno3_face(v[0], v[1], v[2], eps);
+    return weno3_face(v[4], v[3], v[2], eps) - weno3_face(v[3], v[2], v[1], eps);
+}
+
+// ---------------------------------------------------------------------------
+// central moments (Eq. 21) by axis-wise D1Q3 transforms, and cumulants
+// (Eq. 22) with their exact inverse.  Moment index p + 3q + 9r.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void cm3_forward(R& f0, R& f1, R& f2, R u)
+{
+    R r0 = f0 + f1 + f2;
+    R r1 = f2 - f0;
+    R r2 = f2 + f0;
+    f0 = r0;
+    f1 = r1 - u * r0;
+    f2 = r2 - R(2) * u * r1 + u * u * r0;
+}
+template <typename R>
+__device__ __forceinline__ void cm3_inverse(R& m0, R& m1, R& m2, R u)
+{
+    R r0 = m0;
+    R r1 = m1 + u * m0;
+    R r2 = m2 + R(2) * u * m1 + u * u * m0;
+    m0 = R(0.5) * (r2 - r1);
+    m1 = r0 - r2;
+    m2 = R(0.5) * (r2 + r1);
+}
+
+template <int DIM, typename R>
+__device__ __forceinline__ void central_forward(R* f, const R* u)
+{
+    constexpr int NZ = DIM == 3 ? 3 : 1;
+#pragma unroll
+    for (int c = 0; c < NZ; ++c)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) cm3_forward(f[3 * b + 9 * c], f[1 + 3 * b + 9 * c], f[2 + 3 * b + 9 * c], u[0]);
+#pragma unroll
+    for (int c = 0; c < NZ; ++c)
+#pragma unroll
+        for (int p = 0; p < 3; ++p) cm3_forward(f[p + 9 * c], f[p + 3 + 9 * c], f[p + 6 + 9 * c], u[1]);
+    if (DIM == 3) {
+#pragma unroll
+        for (int j = 0; j < 9; ++j) cm3_forward(f[j], f[j + 9], f[j + 18], u[2]);
+    }
+}
+
+template <int DIM, typename R>
+__device__ __forceinline__ void central_inverse(R* m, const R* u)
+{
+    constexpr int NZ = DIM == 3 ? 3 : 1;
+    if (DIM == 3) {
+#pragma unroll
+        for (int j = 0; j < 9; ++j) cm3_inverse(m[j], m[j + 9], m[j + 18], u[2]);
+    }
+#pragma unroll
+    for (int c = 0; c < NZ; ++c)
+#pragma unroll
+        for (int p = 0; p < 3; ++p) cm3_inverse(m[p + 9 * c], m[p + 3 + 9 * c], m[p + 6 + 9 * c], u[1]);
+#pragma unroll
+    for (int c = 0; c < NZ; ++c)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) cm3_inverse(m[3 * b + 9 * c], m[1 + 3 * b + 9 * c], m[2 + 3 * b + 9 * c], u[0]);
+}
+
+#define LBFD_M(p, q, r) ((p) + 3 * (q) + 9 * (r))
+
+// In place: central moments -> cumulants (orders >= 4 change).
+template <int DIM, typename R>
+__device__ __forceinline__ void to_cumulants(R* m)
+{
+#define C_(p, q, r) m[LBFD_M(p, q, r)]
+    if (DIM == 2) {
+        C_(2, 2, 0) -= C_(2, 0, 0) * C_(0, 2, 0) + R(2) * C_(1, 1, 0) * C_(1, 1, 0);
+        return;
+    }
+    // sixth order first: it reads the order-4 central moments
+    R k222 = C_(2, 2, 2)
+        - (C_(2, 0, 0) * C_(0, 2, 2) + C_(0, 2, 0) * C_(2, 0, 2) + C_(0, 0, 2) * C_(2, 2, 0))
+        - R(4) * (C_(1, 1, 0) * C_(1, 1, 2) + C_(1, 0, 1) * C_(1, 2, 1) + C_(0, 1, 1) * C_(2, 1, 1))
+        - R(4) * C_(1, 1, 1) * C_(1, 1, 1)
+        - R(2) * (C_(2, 1, 0) * C_(0, 1, 2) + C_(2, 0, 1) * C_(0, 2, 1) + C_(1, 2, 0) * C_(1, 0, 2))
+        + R(2) * C_(2, 0, 0) * C_(0, 2, 0) * C_(0, 0, 2)
+        + R(4) * (C_(2, 0, 0) * C_(0, 1, 1) * C_(0, 1, 1) + C_(0, 2, 0) * C_(1, 0, 1) * C_(1, 0, 1)
+                  + C_(0, 0, 2) * C_(1, 1, 0) * C_(1, 1, 0))
+        + R(16) * C_(1, 1, 0) * C_(1, 0, 1) * C_(0, 1, 1);
+    R k122 = C_(1, 2, 2) - C_(0, 0, 2) * C_(1, 2, 0) - C_(0, 2, 0) * C_(1, 0, 2)
+        - R(4) * C_(0, 1, 1) * C_(1, 1, 1) - R(2) * (C_(1, 0, 1) * C_(0, 2, 1) + C_(1, 1, 0) * C_(0, 1, 2));
+    R k212 = C_(2, 1, 2) - C_(0, 0, 2) * C_(2, 1, 0) - C_(2, 0, 0) * C_(0, 1, 2)
+        - R(4) * C_(1, 0, 1) * C_(1, 1, 1) - R(2) * (C_(0, 1, 1) * C_(2, 0, 1) + C_(1, 1, 0) * C_(1, 0, 2));
+    R k221 = C_(2, 2, 1) - C_(2, 0, 0) * C_(0, 2, 1) - C_(0, 2, 0) * C_(2, 0, 1)
+        - R(4) * C_(1, 1, 0) * C_(1, 1, 1) - R(2) * (C_(1, 0, 1) * C_(1, 2, 0) + C_(0, 1, 1) * C_(2, 1, 0));
+    C_(2, 2, 2) = k222;
+    C_(1, 2, 2) = k122;
+    C_(2, 1, 2) = k212;
+    C_(2, 2, 1) = k221;
+    C_(2, 2, 0) -= C_(2, 0, 0) * C_(0, 2, 0) + R(2) * C_(1, 1, 0) * C_(1, 1, 0);
+    C_(2, 0, 2) -= C_(2, 0, 0) * C_(0, 0, 2) + R(2) * C_(1, 0, 1) * C_(1, 0, 1);
+    C_(0, 2, 2) -= C_(0, 2, 0) * C_(0, 0, 2) + R(2) * C_(0, 1, 1) * C_(0, 1, 1);
+    C_(2, 1, 1) -= C_(2, 0, 0) * C_(0, 1, 1) + R(2) * C_(1, 1, 0) * C_(1, 0, 1);
+    C_(1, 2, 1) -= C_(0, 2, 0) * C_(1, 0, 1) + R(2) * C_(1, 1, 0) * C_(0, 1, 1);
+    C_(1, 1, 2) -= C_(0, 0, 2) * C_(1, 1, 0) + R(2) * C_(1, 0, 1) * C_(0, 1, 1);
+#undef C_
+}
+
+// In place: cumulants -> central moments (exact inverse of to_cumulants).
+template <int DIM, typename R>
+__device__ __forceinline__ void from_cumulants(R* m)
+{
+#define C_(p, q, r) m[LBFD_M(p, q, r)]
+    if (DIM == 2) {
+        C_(2, 2, 0) += C_(2, 0, 0) * C_(0, 2, 0) + R(2) * C_(1, 1, 0) * C_(1, 1, 0);
+        return;
+    }
+    C_(2, 2, 0) += C_(2, 0, 0) * C_(0, 2, 0) + R(2) * C_(1, 1, 0) * C_(1, 1, 0);
+    C_(2, 0, 2) += C_(2, 0, 0) * C_(0, 0, 2) + R(2) * C_(1, 0, 1) * C_(1, 0, 1);
+    C_(0, 2, 2) += C_(0, 2, 0) * C_(0, 0, 2) + R(2) * C_(0, 1, 1) * C_(0, 1, 1);
+    C_(2, 1, 1) += C_(2, 0, 0) * C_(0, 1, 1) + R(2) * C_(1, 1, 0) * C_(1, 0, 1);
+    C_(1, 2, 1) += C_(0, 2, 0) * C_(1, 0, 1) + R(2) * C_(1, 1, 0) * C_(0, 1, 1);
+    C_(1, 1, 2) += C_(0, 0, 2) * C_(1, 1, 0) + R(2) * C_(1, 0, 1) * C_(0, 1, 1);
+    C_(1, 2, 2) += C_(0, 0, 2) * C_(1, 2, 0) + C_(0, 2, 0) * C_(1, 0, 2)
+        + R(4) * C_(0, 1, 1) * C_(1, 1, 1) + R(2) * (C_(1, 0, 1) * C_(0, 2, 1) + C_(1, 1, 0) * C_(0, 1, 2));
+    C_(2, 1, 2) += C_(0, 0, 2) * C_(2, 1, 0) + C_(2, 0, 0) * C_(0, 1, 2)
+        + R(4) * C_(1, 0, 1) * C_(1, 1, 1) + R(2) * (C_(0, 1, 1) * C_(2, 0, 1) + C_(1, 1, 0) * C_(1, 0, 2));
+    C_(2, 2, 1) += C_(2, 0, 0) * C_(0, 2, 1) + C_(0, 2, 0) * C_(2, 0, 1)
+        + R(4) * C_(1, 1, 0) * C_(1, 1, 1) + R(2) * (C_(1, 0, 1) * C_(1, 2, 0) + C_(0, 1, 1) * C_(2, 1, 0));
+    C_(2, 2, 2) += (C_(2, 0, 0) * C_(0, 2, 2) + C_(0, 2, 0) * C_(2, 0, 2) + C_(0, 0, 2) * C_(2, 2, 0))
+        + R(4) * (C_(1, 1, 0) * C_(1, 1, 2) + C_(1, 0, 1) * C_(1, 2, 1) + C_(0, 1, 1) * C_(2, 1, 1))
+        + R(4) * C_(1, 1, 1) * C_(1, 1, 1)
+        + R(2) * (C_(2, 1, 0) * C_(0, 1, 2) + C_(2, 0, 1) * C_(0, 2, 1) + C_(1, 2, 0) * C_(1, 0, 2))
+        - R(2) * C_(2, 0, 0) * C_(0, 2, 0) * C_(0, 0, 2)
+        - R(4) * (C_(2, 0, 0) * C_(0, 1, 1) * C_(0, 1, 1) + C_(0, 2, 0) * C_(1, 0, 1) * C_(1, 0, 1)
+                  + C_(0, 0, 2) * C_(1, 1, 0) * C_(1, 1, 0))
+        - R(16) * C_(1, 1, 0) * C_(1, 0, 1) * C_(0, 1, 1);
+#undef C_
+}
+
+__host__ __device__ constexpr int moment_order(int j) { return j % 3 + (j / 3) % 3 + j / 9; }
+
+// ---------------------------------------------------------------------------
+// Collision of one cell (Eq. 9, 10, 12-15, 19, 21-24): g (post-streaming)
+// is replaced by g*.  Relaxation toward the cumulants of g^eq/(rho cs^2);
+// orders 0-1 carried, second order split into trace (omega_b) and
+// deviatoric/off-diagonal (omega_s), orders >= 3 at omega_hi.
+// ---------------------------------------------------------------------------
+template <int DIM, typename R>
+__device__ __forceinline__ void collide(const StepParams<R>& P, R* g, R rho, const R* u, const R* grad_rho,
+                                        R Lam)
+{
+    constexpr int Q = DIM == 2 ? 9 : 27;
+    const R cs2 = R(1) / R(3);
+    R sum_g = R(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) sum_g += g[i];
+    const R rcs2 = rho * cs2;
+    const R P_h = sum_g + R(0.5) * rcs2 * Lam;  // Eq. 13a
+    const R uu = u[0] * u[0] + u[1] * u[1] + (DIM == 3 ? u[2] * u[2] : R(0));
+    const R inv_rcs2 = R(1) / rcs2;
+    R xi[Q], fe[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const R wi = weight<DIM, R>(i);
+        R cu = R(0), cg = R(0);
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            const int c = ccomp<DIM>(i, a);
+            cu += R(c) * u[a];
+            cg += (R(c) - u[a]) * grad_rho[a];
+        }
+        // f^eq / rho, Eq. 10
+        const R feq_r = wi * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
+        xi[i] = cs2 * (feq_r - wi) * cg + wi * rcs2 * Lam;  // Eq. 9
+        // g^eq / (rho cs2) = w (P_h/(rho cs2) - 1) + f^eq/rho, Eq. 12
+        fe[i] = wi * (P_h * inv_rcs2 - R(1)) + feq_r;
+        g[i] = (g[i] + R(0.5) * xi[i]) * inv_rcs2;  // Eq. 19
+    }
+    central_forward<DIM>(g, u);
+    central_forward<DIM>(fe, u);
+    to_cumulants<DIM>(g);
+    to_cumulants<DIM>(fe);
+    // relaxation
+    const R ws = P.omega_s, wb = P.omega_b, wh = P.omega_hi;
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        const int o = moment_order(j);
+        if (o >= 3) g[j] = fe[j] + (R(1) - wh) * (g[j] - fe[j]);
+    }
+    if (DIM == 2) {
+        const int ixx = LBFD_M(2, 0, 0), iyy = LBFD_M(0, 2, 0), ixy = LBFD_M(1, 1, 0);
+        const R tr = g[ixx] + g[iyy], tre = fe[ixx] + fe[iyy];
+        const R dv = g[ixx] - g[iyy], dve = fe[ixx] - fe[iyy];
+        const R trs = tre + (R(1) - wb) * (tr - tre);
+        const R dvs = dve + (R(1) - ws) * (dv - dve);
+        g[ixx] = R(0.5) * (trs + dvs);
+        g[iyy] = R(0.5) * (trs - dvs);
+        g[ixy] = fe[ixy] + (R(1) - ws) * (g[ixy] - fe[ixy]);
+    } else {
+        const int ixx = LBFD_M(2, 0, 0), iyy = LBFD_M(0, 2, 0), izz = LBFD_M(0, 0, 2);
+        const R tr = g[ixx] + g[iyy] + g[izz], tre = fe[ixx] + fe[iyy] + fe[izz];
+        const R d1 = g[ixx] - g[iyy], d1e = fe[ixx] - fe[iyy];
+        const R d2 = g[ixx] - g[izz], d2e = fe[ixx] - fe[izz];
+        const R trs = tre + (R(1) - wb) * (tr - tre);
+        const R d1s = d1e + (R(1) - ws) * (d1 - d1e);
+        const R d2s = d2e + (R(1) - ws) * (d2 - d2e);
+        const R xx = (trs + d1s + d2s) * (R(1) / R(3));
+        g[ixx] = xx;
+        g[iyy] = xx - d1s;
+        g[izz] = xx - d2s;
+        const int o1 = LBFD_M(1, 1, 0), o2 = LBFD_M(1, 0, 1), o3 = LBFD_M(0, 1, 1);
+        g[o1] = fe[o1] + (R(1) - ws) * (g[o1] - fe[o1]);
+        g[o2] = fe[o2] + (R(1) - ws) * (g[o2] - fe[o2]);
+        g[o3] = fe[o3] + (R(1) - ws) * (g[o3] - fe[o3]);
+    }
+    from_cumulants<DIM>(g);
+    central_inverse<DIM>(g, u);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) g[i] = rcs2 * g[i] + R(0.5) * xi[i];  // Eq. 14
+}
+
+}  // namespace lbfd

@@ -1,0 +1,37 @@
+// lbfd_internal.h -- launch interface between the C-ABI host code and the
+// kernel translation units.  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "lbfd_params.h"
+
+namespace lbfd {
+
+// Device views of one state buffer: populations g[Q][stride], T[stride],
+// Y[NSP][stride], all in storage precision.
+struct StateView {
+    void* g;
+    void* T;
+    void* Y;
+};
+
+// Launch one fused coupled step: state `in` -> state `out`.
+// precision: 0 = FP64 (S = R = double), 1 = mixed (S = R = float).
+cudaError_t launch_step(int dim, int precision, const StepParams<double>& Pd, const StepParams<float>& Pf,
+                        StateView in, StateView out, const uint8_t* solid, cudaStream_t stream);
+
+// Diagnostics reduction into the device scratch `red` (LBFD_NDIAG + extra
+// words, zeroed by the launcher); FP64 accumulation.
+cudaError_t launch_diagnostics(int dim, int precision, const StepParams<double>& Pd, StateView st,
+                               const uint8_t* solid, double* red, cudaStream_t stream);
+
+// Derived or raw field of every cell into double out[ncell] (device).
+cudaError_t launch_field(int dim, int precision, const StepParams<double>& Pd, StateView st,
+                         const uint8_t* solid, int field, double* out, cudaStream_t stream);
+
+// Number of words of the reduction scratch.
+constexpr int RED_WORDS = 16;
+
+}  // namespace lbfd

@@ -1,0 +1,35 @@
+// lbfd_params.h -- parameters of one fused step as seen by the kernels,
+// already converted to the compute type R and to lattice units.
+#pragma once
+
+namespace lbfd {
+
+constexpr int NSP = 5;  // species count the kernels are built for
+
+template <typename R>
+struct StepParams {
+    int dim, nx, ny, nz;
+    long long ncell;  // nx*ny*nz
+    long long N;      // stride between SoA planes (ncell rounded up)
+    int bc[6];
+    R T_wall[6];
+    R inv_Wk[NSP];   // 1/W_k
+    R yield[NSP];    // nu_k W_k / (-nu_F W_F)
+    R a_diff[NSP];   // D_k W_k, D_k = alpha / Le_k
+    int fuel, oxid;
+    R A_lat;         // A * dt (per step)
+    R Ta;            // activation temperature [K]
+    R Q_cp;          // Q / cp [K per unit fuel mass fraction]
+    double A_lat_d, Ta_d;  // FP64 copies for the mixed-precision Arrhenius
+    R T_fp64;
+    R omega_s, omega_b, omega_hi;
+    R alpha;
+    R u_in, T_in, Y_in[NSP], invW_in, rho_in;
+    R T_solid;
+    int solid_isothermal;
+    int poiseuille;
+    R epsY, epsT;
+    R cs;            // lattice sound speed 1/sqrt(3)
+};
+
+}  // namespace lbfd

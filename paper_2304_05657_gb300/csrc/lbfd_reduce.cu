@@ -1,0 +1,274 @@
+// lbfd_reduce.cu -- FP64 reductions over the fluid cells (flame position,
+// mass, heat release, fuel consumption, max T, non-finite count) and the
+// per-cell field read-out kernel.
+//
+// Observables: flame front by maximum heat release (Sec. IV.A dead-zone
+// analysis; Sec. IV.B burner), consumption speed integrals (Sec. IV.C,
+// Eq. 40), and an integral flame position (unburnt length).
+#include <cmath>
+
+#include "lbfd_device.cuh"
+#include "lbfd_internal.h"
+
+namespace lbfd {
+
+__device__ __forceinline__ unsigned long long order_key(double v)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+template <typename S>
+__device__ __forceinline__ double hrr_of(const StepParams<double>& P, double T, const double* Y, double* rho_out,
+                                         double* q_out)
+{
+    double invW = 0.0;
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) invW += Y[k] * P.inv_Wk[k];
+    const double rho = P.T_in * P.invW_in / (T * invW);
+    const double yf = Y[P.fuel] > 0.0 ? Y[P.fuel] : 0.0;
+    const double yo = Y[P.oxid] > 0.0 ? Y[P.oxid] : 0.0;
+    const double q = P.A_lat * yf * yo * exp(-P.Ta / T);
+    *rho_out = rho;
+    *q_out = q;
+    return rho * P.Q_cp * q;
+}
+
+// red layout: [0] sum Y_F, [1] mass, [2] hrr, [3] fuel, [4] max-T key (u64),
+// [5] non-finite count (u64), [6] fluid count (u64), [7] x=0 section count (u64),
+// [8] centre-line max hrr, [9] its x
+template <int DIM, typename S>
+__global__ void __launch_bounds__(256) diag_kernel(StepParams<double> P, const S* __restrict__ g,
+                                                   const S* __restrict__ T, const S* __restrict__ Y,
+                                                   const uint8_t* __restrict__ solid, double* red)
+{
+    constexpr int Q = DIM == 2 ? 9 : 27;
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    unsigned long long tkey = 0ull, nonf = 0ull, nfl = 0ull, sec = 0ull;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < P.ncell; c += stride) {
+        if (solid[c]) continue;
+        ++nfl;
+        if (c % P.nx == 0) ++sec;
+        const double Tc = (double)T[c];
+        double Yc[NSP];
+        bool bad = !isfinite(Tc);
+#pragma unroll
+        for (int k = 0; k < NSP; ++k) {
+            Yc[k] = (double)Y[(long long)k * P.N + c];
+            bad |= !isfinite(Yc[k]);
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) bad |= !isfinite((double)g[(long long)i * P.N + c]);
+        if (bad) {
+            ++nonf;
+            continue;
+        }
+        double rho, q;
+        const double h = hrr_of<S>(P, Tc, Yc, &rho, &q);
+        s[0] += Yc[P.fuel];
+        s[1] += rho;
+        s[2] += h;
+        s[3] += rho * q;
+        const unsigned long long k = order_key(Tc);
+        tkey = k > tkey ? k : tkey;
+    }
+    // warp then block reduction
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) s[j] += __shfl_down_sync(0xffffffffu, s[j], off);
+        const unsigned long long o = __shfl_down_sync(0xffffffffu, tkey, off);
+        tkey = o > tkey ? o : tkey;
+        nonf += __shfl_down_sync(0xffffffffu, nonf, off);
+        nfl += __shfl_down_sync(0xffffffffu, nfl, off);
+        sec += __shfl_down_sync(0xffffffffu, sec, off);
+    }
+    __shared__ double sh[8][4];
+    __shared__ unsigned long long shk[8][4];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) sh[wid][j] = s[j];
+        shk[wid][0] = tkey;
+        shk[wid][1] = nonf;
+        shk[wid][2] = nfl;
+        shk[wid][3] = sec;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = blockDim.x >> 5;
+        for (int w = 1; w < nw; ++w) {
+            for (int j = 0; j < 4; ++j) s[j] += sh[w][j];
+            tkey = shk[w][0] > tkey ? shk[w][0] : tkey;
+            nonf += shk[w][1];
+            nfl += shk[w][2];
+            sec += shk[w][3];
+        }
+        for (int j = 0; j < 4; ++j) atomicAdd(&red[j], s[j]);
+        unsigned long long* ru = reinterpret_cast<unsigned long long*>(red);
+        atomicMax(&ru[4], tkey);
+        atomicAdd(&ru[5], nonf);
+        atomicAdd(&ru[6], nfl);
+        atomicAdd(&ru[7], sec);
+    }
+}
+
+// one block: argmax of the heat release on the line y = ny/2, z = nz/2
+template <int DIM, typename S>
+__global__ void __launch_bounds__(1024) centreline_kernel(StepParams<double> P, const S* __restrict__ T,
+                                                          const S* __restrict__ Y,
+                                                          const uint8_t* __restrict__ solid, double* red)
+{
+    double best = -INFINITY;
+    int bx = -1;
+    const int yc = P.ny / 2, zc = DIM == 3 ? P.nz / 2 : 0;
+    for (int x = threadIdx.x; x < P.nx; x += blockDim.x) {
+        const long long c = x + (long long)P.nx * (yc + (long long)P.ny * zc);
+        if (solid[c]) continue;
+        const double Tc = (double)T[c];
+        double Yc[NSP];
+        bool bad = !isfinite(Tc);
+#pragma unroll
+        for (int k = 0; k < NSP; ++k) {
+            Yc[k] = (double)Y[(long long)k * P.N + c];
+            bad |= !isfinite(Yc[k]);
+        }
+        if (bad) continue;
+        double rho, q;
+        const double h = hrr_of<S>(P, Tc, Yc, &rho, &q);
+        if (h > best) {  // x increases along the loop: ties keep the smaller x
+            best = h;
+            bx = x;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const double ob = __shfl_down_sync(0xffffffffu, best, off);
+        const int ox = __shfl_down_sync(0xffffffffu, bx, off);
+        if (ox >= 0 && (bx < 0 || ob > best || (ob == best && ox < bx))) {
+            best = ob;
+            bx = ox;
+        }
+    }
+    __shared__ double sb[32];
+    __shared__ int sx[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        sb[wid] = best;
+        sx[wid] = bx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = blockDim.x >> 5;
+        for (int w = 1; w < nw; ++w) {
+            if (sx[w] >= 0 && (bx < 0 || sb[w] > best || (sb[w] == best && sx[w] < bx))) {
+                best = sb[w];
+                bx = sx[w];
+            }
+        }
+        red[8] = best;
+        red[9] = (double)bx;
+    }
+}
+
+template <int DIM, typename S>
+static cudaError_t diag_launch(const StepParams<double>& P, StateView st, const uint8_t* solid, double* red,
+                               cudaStream_t stream)
+{
+    cudaError_t e = cudaMemsetAsync(red, 0, RED_WORDS * sizeof(double), stream);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long want = (P.ncell + 255) / 256;
+    long long cap = (long long)(sms > 0 ? sms : 1) * 8;
+    const unsigned blocks = (unsigned)(want < cap ? (want > 0 ? want : 1) : cap);
+    diag_kernel<DIM, S><<<blocks, 256, 0, stream>>>(P, (const S*)st.g, (const S*)st.T, (const S*)st.Y, solid, red);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    centreline_kernel<DIM, S><<<1, 1024, 0, stream>>>(P, (const S*)st.T, (const S*)st.Y, solid, red);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diagnostics(int dim, int precision, const StepParams<double>& P, StateView st,
+                               const uint8_t* solid, double* red, cudaStream_t stream)
+{
+    if (precision == 0)
+        return dim == 2 ? diag_launch<2, double>(P, st, solid, red, stream)
+                        : diag_launch<3, double>(P, st, solid, red, stream);
+    return dim == 2 ? diag_launch<2, float>(P, st, solid, red, stream)
+                    : diag_launch<3, float>(P, st, solid, red, stream);
+}
+
+// field ids follow include/lbfd.h
+template <int DIM, typename S>
+__global__ void __launch_bounds__(256) field_kernel(StepParams<double> P, const S* __restrict__ g,
+                                                    const S* __restrict__ T, const S* __restrict__ Y,
+                                                    const uint8_t* __restrict__ solid, int field,
+                                                    double* __restrict__ out)
+{
+    constexpr int Q = DIM == 2 ? 9 : 27;
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= P.ncell) return;
+    if (field >= 16) {
+        out[c] = (double)g[(long long)(field - 16) * P.N + c];
+        return;
+    }
+    if (field == 0) {
+        out[c] = (double)T[c];
+        return;
+    }
+    if (field >= 1 && field <= NSP) {
+        out[c] = (double)Y[(long long)(field - 1) * P.N + c];
+        return;
+    }
+    const double Tc = (double)T[c];
+    double Yc[NSP];
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) Yc[k] = (double)Y[(long long)k * P.N + c];
+    double rho, q;
+    const double h = hrr_of<S>(P, Tc, Yc, &rho, &q);
+    double v = 0.0;
+    if (field >= 6 && field <= 8) {
+        const int a = field - 6;
+        if (a < DIM) {
+            double m = 0.0;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) m += (double)ccomp<DIM>(i, a) * (double)g[(long long)i * P.N + c];
+            v = 3.0 * m / rho;
+        }
+    } else if (field == 9) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) v += (double)g[(long long)i * P.N + c];
+    } else if (field == 10) {
+        v = rho;
+    } else if (field == 11) {
+        v = h;
+    }
+    out[c] = v;
+}
+
+cudaError_t launch_field(int dim, int precision, const StepParams<double>& P, StateView st, const uint8_t* solid,
+                         int field, double* out, cudaStream_t stream)
+{
+    const unsigned blocks = (unsigned)((P.ncell + 255) / 256);
+    if (precision == 0) {
+        if (dim == 2)
+            field_kernel<2, double><<<blocks, 256, 0, stream>>>(P, (const double*)st.g, (const double*)st.T,
+                                                                 (const double*)st.Y, solid, field, out);
+        else
+            field_kernel<3, double><<<blocks, 256, 0, stream>>>(P, (const double*)st.g, (const double*)st.T,
+                                                                 (const double*)st.Y, solid, field, out);
+    } else {
+        if (dim == 2)
+            field_kernel<2, float><<<blocks, 256, 0, stream>>>(P, (const float*)st.g, (const float*)st.T,
+                                                                (const float*)st.Y, solid, field, out);
+        else
+            field_kernel<3, float><<<blocks, 256, 0, stream>>>(P, (const float*)st.g, (const float*)st.T,
+                                                                (const float*)st.Y, solid, field, out);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace lbfd

@@ -1,0 +1,352 @@
+// lbfd_step_general.cuh -- the fused coupled step for one fluid cell, general
+// form: every neighbour access goes through the boundary classification, so
+// it is valid for any cell (walls, solid mask, inlet, outlet, periodic
+// wrap).  One call = steps a1-a10 of one cell:
+//   a1 pull streaming with half-way bounce-back (Eq. 28), velocity inlet
+//      (Eq. 31) and convective outlet (Eq. 32);
+//   a2 EOS density and velocity (Eq. 13b);
+//   a3 ghost-node FD lines (Eq. 34); a4 WENO3/centred convection with the
+//      mass-conserving correction (Eq. 26); a5 4th-order diffusion of
+//      T (Eq. 7) and Y_k with the correction velocity (Eq. 1-2);
+//   a6 single-step Arrhenius source; a7 explicit Euler and Lambda (Eq. 6);
+//   a8-a9 source Xi (Eq. 9), pre-conditioning (Eq. 19) and cumulant
+//      collision (Eq. 14-24); a10 write g*.
+#pragma once
+#include "lbfd_device.cuh"
+
+namespace lbfd {
+
+// ---------------------------------------------------------------------------
+// a1: pull one population with the boundary rules
+// ---------------------------------------------------------------------------
+template <int DIM, typename S, typename R>
+__device__ __forceinline__ R pull_general(const StepParams<R>& P, int i, const int p[3], long long c,
+                                          const S* __restrict__ g, const uint8_t* __restrict__ solid,
+                                          R rho_cell)
+{
+    const long long N = P.N;
+    int src[3] = {p[0] - ccomp<DIM>(i, 0), p[1] - ccomp<DIM>(i, 1), DIM == 3 ? p[2] - ccomp<DIM>(i, 2) : 0};
+    int wall = 0, inlet = -1, outlet = -1;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        const int n = extent(P, a);
+        int f = -1;
+        if (src[a] < 0) f = 2 * a;
+        else if (src[a] >= n) f = 2 * a + 1;
+        if (f < 0) continue;
+        const int t = P.bc[f];
+        if (t == BC_PERIODIC) src[a] = ((src[a] % n) + n) % n;
+        else if (t == BC_INLET) { if (inlet < 0) inlet = f; }
+        else if (t == BC_OUTLET || t == BC_OUTLET_PRESSURE) { if (outlet < 0) outlet = f; }
+        else wall = 1;
+    }
+    const int ib = opposite<DIM>(i);
+    if (wall) return R(g[(long long)ib * N + c]);  // Eq. 28
+    if (inlet >= 0) {                              // Eq. 31 applied to g
+        const int a = inlet / 2;
+        R mag = P.u_in;
+        if (P.poiseuille && DIM == 2 && a == 0) {
+            const R ny = R(P.ny), y = R(p[1]) + R(0.5);
+            mag = R(6) * P.u_in * y * (ny - y) / (ny * ny);
+        }
+        const R un = (inlet % 2 == 0) ? mag : -mag;  // along the inward normal
+        const R cu = R(ccomp<DIM>(i, a)) * un;
+        return R(g[(long long)ib * N + c]) + R(2) * weight<DIM, R>(i) * P.rho_in * cu;
+    }
+    if (outlet >= 0 && P.bc[outlet] == BC_OUTLET_PRESSURE) {
+        // constant P_h = 0: anti-bounce-back with twice the even part of g^eq
+        R uc[3] = {R(0), R(0), R(0)};
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            R m = R(0);
+#pragma unroll
+            for (int j = 0; j < (DIM == 2 ? 9 : 27); ++j) {
+                const int cj = ccomp<DIM>(j, a);
+                if (cj != 0) m += R(cj) * R(g[(long long)j * N + c]);
+            }
+            uc[a] = m * R(3) / rho_cell;
+        }
+        R cu = R(0), uu = R(0);
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            cu += R(ccomp<DIM>(i, a)) * uc[a];
+            uu += uc[a] * uc[a];
+        }
+        const R wi = weight<DIM, R>(i);
+        const R geq_even = wi * rho_cell * (R(1.5) * cu * cu - R(0.5) * uu);
+        return R(2) * geq_even - R(g[(long long)ib * N + c]);
+    }
+    if (outlet >= 0) {  // Eq. 32 in lattice units
+        const int a = outlet / 2;
+        const int ns = (outlet % 2 == 1) ? 1 : -1;  // outward normal along a
+        R mom = R(0);
+#pragma unroll
+        for (int j = 0; j < (DIM == 2 ? 9 : 27); ++j) {
+            const int cj = ccomp<DIM>(j, a) * ns;
+            if (cj != 0) mom += R(cj) * R(g[(long long)j * N + c]);
+        }
+        const R un = mom / (rho_cell * (R(1) / R(3)));
+        int q[3] = {p[0], p[1], p[2]};
+        q[a] -= ns;
+        R inner = R(g[(long long)i * N + c]);
+        if (q[a] >= 0 && q[a] < extent(P, a)) {
+            const long long qi = cell_of(P, q[0], q[1], DIM == 3 ? q[2] : 0);
+            if (!solid[qi]) inner = R(g[(long long)i * N + qi]);
+        }
+        return (P.cs - un) * inner + (R(1) - P.cs + un) * R(g[(long long)i * N + c]);
+    }
+    const long long s = cell_of(P, src[0], src[1], DIM == 3 ? src[2] : 0);
+    if (solid[s]) return R(g[(long long)ib * N + c]);  // Eq. 28
+    return R(g[(long long)i * N + s]);                   // Eq. 8
+}
+
+// ---------------------------------------------------------------------------
+// a3: one FD line through the cell along an axis, with ghost points
+// ---------------------------------------------------------------------------
+template <typename R>
+struct LineDesc {
+    long long src[5];  // cell whose values feed the point (itself or its mirror)
+    int mode[5];       // G_DIRECT / G_NEUMANN / G_DIRICHLET_T / G_INLET
+    R TB[5];           // boundary temperature of Dirichlet ghosts
+    int near;          // some point of the line is not a fluid cell
+};
+
+template <int DIM, typename R>
+__device__ __forceinline__ void ghost_mode(const StepParams<R>& P, int type, int face, int* mode, R* TB)
+{
+    *TB = R(0);
+    if (type == PT_SOLID) {
+        *mode = P.solid_isothermal ? G_DIRICHLET_T : G_NEUMANN;
+        *TB = P.T_solid;
+    } else if (type == BC_WALL_ISOTHERMAL) {
+        *mode = G_DIRICHLET_T;
+        *TB = P.T_wall[face];
+    } else if (type == BC_INLET) {
+        *mode = G_INLET;
+        *TB = P.T_in;
+    } else {
+        *mode = G_NEUMANN;  // adiabatic wall, outlet
+    }
+}
+
+template <int DIM, typename R>
+__device__ __forceinline__ void build_line(const StepParams<R>& P, const int p[3], long long c, int a,
+                                           const uint8_t* __restrict__ solid, LineDesc<R>& L)
+{
+    L.near = 0;
+    L.src[2] = c;
+    L.mode[2] = G_DIRECT;
+    L.TB[2] = R(0);
+#pragma unroll
+    for (int side = -1; side <= 1; side += 2) {
+        int w = 0, wtype = 0, wface = -1;
+#pragma unroll
+        for (int j = 1; j <= 2; ++j) {
+            if (w) break;
+            int q[3] = {p[0], p[1], p[2]};
+            q[a] += side * j;
+            long long idx = 0;
+            int face = -1;
+            const int t = classify<DIM>(P, q, solid, &idx, &face);
+            if (t == PT_FLUID) {
+                L.src[2 + side * j] = idx;
+                L.mode[2 + side * j] = G_DIRECT;
+                L.TB[2 + side * j] = R(0);
+            } else {
+                w = j;
+                wtype = t;
+                wface = face;
+            }
+        }
+        if (!w) continue;
+        L.near = 1;
+        int mode;
+        R TB;
+        ghost_mode<DIM>(P, wtype, wface, &mode, &TB);
+#pragma unroll
+        for (int j = 1; j <= 2; ++j) {
+            if (j < w) continue;
+            const int m = 2 * w - 1 - j;  // mirror offset on this side
+            long long ms;
+            if (m >= 0) {
+                ms = L.src[2 + side * m];
+            } else {
+                int q[3] = {p[0], p[1], p[2]};
+                q[a] -= side;
+                long long idx = 0;
+                int face = -1;
+                ms = (classify<DIM>(P, q, solid, &idx, &face) == PT_FLUID) ? idx : c;
+            }
+            L.src[2 + side * j] = ms;
+            L.mode[2 + side * j] = mode;
+            L.TB[2 + side * j] = TB;
+        }
+    }
+}
+
+// values of one line point: T, Y_k, 1/W, rho (ghost rules of Eq. 34; the
+// density of a ghost is reconstructed directly, with rho_B = EOS(T_B, Y))
+template <typename S, typename R>
+__device__ __forceinline__ void line_point(const StepParams<R>& P, const LineDesc<R>& L, int j,
+                                           const S* __restrict__ T, const S* __restrict__ Y, R& Tj, R* Yj,
+                                           R& invWj, R& rhoj)
+{
+    const long long s = L.src[j];
+    const R Tm = R(T[s]);
+    R Ym[NSP];
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) Ym[k] = R(Y[(long long)k * P.N + s]);
+    const R invWm = inv_molar_mass(P, Ym);
+    const R rhom = eos(P, Tm, invWm);
+    const int mode = L.mode[j];
+    if (mode == G_DIRECT || mode == G_NEUMANN) {
+        Tj = Tm;
+#pragma unroll
+        for (int k = 0; k < NSP; ++k) Yj[k] = Ym[k];
+        invWj = invWm;
+        rhoj = rhom;
+    } else if (mode == G_DIRICHLET_T) {
+        Tj = R(2) * L.TB[j] - Tm;
+#pragma unroll
+        for (int k = 0; k < NSP; ++k) Yj[k] = Ym[k];
+        invWj = invWm;
+        rhoj = R(2) * eos(P, L.TB[j], invWm) - rhom;
+    } else {  // inlet: Dirichlet T_in and Y_in
+        Tj = R(2) * P.T_in - Tm;
+#pragma unroll
+        for (int k = 0; k < NSP; ++k) Yj[k] = R(2) * P.Y_in[k] - Ym[k];
+        invWj = inv_molar_mass(P, Yj);
+        rhoj = R(2) * P.rho_in - rhom;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FD right-hand side along one axis, accumulated into the cell's terms.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct FDAccum {
+    R conv_T, diff_T;
+    R conv_Y[NSP], diff_Y[NSP];
+    R grad_rho[3];
+};
+
+template <typename R>
+__device__ __forceinline__ void fd_axis(const StepParams<R>& P, int a, int near, const R* Tl, const R (*Yl)[5],
+                                        const R* invWl, const R* rhol, R u_a, R T0, const R* Y0, R invW0, R rho0,
+                                        FDAccum<R>& acc)
+{
+    const R drho = fd_d1(rhol);
+    acc.grad_rho[a] = drho;
+    const R drho_r = drho / rho0;
+    // temperature: convection without correction, diffusion (Eq. 7)
+    acc.conv_T += u_a * (near ? fd_c2(Tl) : weno3_deriv(Tl, u_a, P.epsT));
+    acc.diff_T += P.alpha * (fd_d2(Tl) + drho_r * fd_d1(Tl));
+    // species convection with the correction of Eq. 26
+    R Lk[NSP], sumL = R(0);
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) {
+        Lk[k] = near ? fd_c2(Yl[k]) : weno3_deriv(Yl[k], u_a, P.epsY);
+        sumL += Lk[k];
+    }
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) acc.conv_Y[k] += u_a * (Lk[k] - Y0[k] * sumL);
+    // species diffusion with the correction velocity (Eq. 1-2), expanded
+    const R dinvW = fd_d1(invWl);
+    R m[NSP], dm[NSP], dY[NSP], M = R(0), dM = R(0);
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) {
+        R Xl[5];
+#pragma unroll
+        for (int j = 0; j < 5; ++j) Xl[j] = Yl[k][j] * P.inv_Wk[k] / invWl[j];
+        const R dX = fd_d1(Xl), d2X = fd_d2(Xl);
+        m[k] = P.a_diff[k] * invW0 * dX;
+        dm[k] = P.a_diff[k] * (invW0 * d2X + dinvW * dX);
+        dY[k] = fd_d1(Yl[k]);
+        M += m[k];
+        dM += dm[k];
+    }
+#pragma unroll
+    for (int k = 0; k < NSP; ++k)
+        acc.diff_Y[k] += dm[k] - dY[k] * M - Y0[k] * dM + (m[k] - Y0[k] * M) * drho_r;
+}
+
+// ---------------------------------------------------------------------------
+// The whole coupled update of one fluid cell (general form).
+// ---------------------------------------------------------------------------
+template <int DIM, typename S, typename R>
+__device__ __forceinline__ void cell_step_general(const StepParams<R>& P, const int p[3], long long c,
+                                                  const S* __restrict__ g_in, S* __restrict__ g_out,
+                                                  const S* __restrict__ T_in, S* __restrict__ T_out,
+                                                  const S* __restrict__ Y_in, S* __restrict__ Y_out,
+                                                  const uint8_t* __restrict__ solid)
+{
+    constexpr int Q = DIM == 2 ? 9 : 27;
+    const long long N = P.N;
+    // a2 (density first: the outlet rule needs it)
+    const R T0 = R(T_in[c]);
+    R Y0[NSP];
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) Y0[k] = R(Y_in[(long long)k * N + c]);
+    const R invW0 = inv_molar_mass(P, Y0);
+    const R rho0 = eos(P, T0, invW0);
+    // a1
+    R g[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) g[i] = pull_general<DIM, S, R>(P, i, p, c, g_in, solid, rho0);
+    // a2: velocity, Eq. 13b
+    R u[3] = {R(0), R(0), R(0)};
+    {
+        const R inv = R(3) / rho0;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            R m = R(0);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int ci = ccomp<DIM>(i, a);
+                if (ci) m += R(ci) * g[i];
+            }
+            u[a] = m * inv;
+        }
+    }
+    // a3-a5
+    FDAccum<R> acc;
+    acc.conv_T = acc.diff_T = R(0);
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) acc.conv_Y[k] = acc.diff_Y[k] = R(0);
+    acc.grad_rho[0] = acc.grad_rho[1] = acc.grad_rho[2] = R(0);
+#pragma unroll 1
+    for (int a = 0; a < DIM; ++a) {
+        LineDesc<R> L;
+        build_line<DIM, R>(P, p, c, a, solid, L);
+        R Tl[5], Yl[NSP][5], invWl[5], rhol[5];
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            R Yj[NSP];
+            line_point<S, R>(P, L, j, T_in, Y_in, Tl[j], Yj, invWl[j], rhol[j]);
+#pragma unroll
+            for (int k = 0; k < NSP; ++k) Yl[k][j] = Yj[k];
+        }
+        fd_axis<R>(P, a, L.near, Tl, Yl, invWl, rhol, u[a], T0, Y0, invW0, rho0, acc);
+    }
+    // a6: reaction
+    const R q = arrhenius(P, T0, Y0[P.fuel], Y0[P.oxid]);
+    const R reac_T = P.Q_cp * q;
+    // a7: Euler update and Lambda from the non-convective rates (Eq. 6)
+    const R DT = acc.diff_T + reac_T;
+    T_out[c] = S(T0 + (DT - acc.conv_T));
+    R lam_Y = R(0);
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) {
+        const R DY = acc.diff_Y[k] + P.yield[k] * q;
+        Y_out[(long long)k * N + c] = S(Y0[k] + (DY - acc.conv_Y[k]));
+        lam_Y += P.inv_Wk[k] * DY;
+    }
+    const R Lam = DT / T0 + lam_Y / invW0;
+    // a8-a9
+    collide<DIM, R>(P, g, rho0, u, acc.grad_rho, Lam);
+    // a10
+#pragma unroll
+    for (int i = 0; i < Q; ++i) g_out[(long long)i * N + c] = S(g[i]);
+}
+
+}  // namespace lbfd

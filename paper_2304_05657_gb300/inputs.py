@@ -36,7 +36,7 @@ def base_config(**over) -> dict:
     sustain a flame at all."""
     cfg = dict(
         dim=2, nx=64, ny=16, nz=1,
-        bc=["inlet", "outlet", "wall_adiabatic", "wall_adiabatic", "periodic", "periodic"],
+        bc=["inlet", "outlet_pressure", "wall_adiabatic", "wall_adiabatic", "periodic", "periodic"],
         T_wall=[300.0] * 6,
         W=list(W), nu_stoich=list(NU_STOICH), Le=[1.0] * 5,
         fuel=FUEL, oxidiser=OXIDISER,
@@ -69,22 +69,64 @@ def burnt_Y(Y_unburnt) -> list[float]:
     return (m / m.sum()).tolist()
 
 
+def _isothermal_distance(cfg: dict, solid: np.ndarray, reach: int) -> np.ndarray:
+    """Distance (cells, centre to wall plane) from each cell to the nearest
+    isothermal boundary: an isothermal solid cell (when solids are
+    isothermal) or an isothermal domain face; capped at `reach`."""
+    from scipy import ndimage
+
+    dim = cfg["dim"]
+    shape = solid.shape  # (ny, nx) or (nz, ny, nx)
+    wall = solid.astype(bool) if cfg["solid_isothermal"] else np.zeros(shape, dtype=bool)
+    pads, modes = [], []
+    for ax in range(dim):
+        a = dim - 1 - ax  # array axis of grid axis `ax`
+        lo, hi = cfg["bc"][2 * ax], cfg["bc"][2 * ax + 1]
+        pads.append((a, lo, hi))
+    m = reach + 1
+    arr = wall
+    for a, lo, hi in pads:
+        if lo == "periodic":
+            width = [(0, 0)] * arr.ndim
+            width[a] = (m, m)
+            arr = np.pad(arr, width, mode="wrap")
+        else:
+            sh = list(arr.shape)
+            sh[a] = m
+            blo = np.full(sh, lo == "wall_isothermal")
+            bhi = np.full(sh, hi == "wall_isothermal")
+            arr = np.concatenate([blo, arr, bhi], axis=a)
+    if not arr.any():
+        return np.full(shape, float(reach))
+    d = ndimage.distance_transform_edt(~arr)
+    sl = tuple(slice(m, m + n) for n in shape)
+    return np.minimum(d[sl] - 0.5, float(reach))
+
+
 def ignition_fields(cfg: dict, solid: np.ndarray, x0: int = 0, x1: int = 20, T_hot: float = 2000.0,
-                    burnt: bool = True):
+                    burnt: bool = True, edge: float = 1.5, wall_taper: float = 4.0):
     """Unburnt mixture at T_in with a hot band x in [x0, x1) at T_hot; the
-    band holds burnt products (burnt=True) or the unburnt mixture."""
+    band holds burnt products (burnt=True) or the unburnt mixture.  The
+    band has tanh edges of width `edge` cells along x (no edge where it
+    starts at the inlet) and fades linearly to the cold state within
+    `wall_taper` cells of isothermal walls and solids, so that the initial
+    state is smooth on the grid (the paper starts from smooth flame
+    profiles)."""
     N = ncells(cfg)
     shape = (cfg["nz"], cfg["ny"], cfg["nx"]) if cfg["dim"] == 3 else (cfg["ny"], cfg["nx"])
-    T = np.full(shape, cfg["T_in"], dtype=np.float64)
-    T[..., x0:x1] = T_hot
-    hot = np.zeros(shape, dtype=bool)
-    hot[..., x0:x1] = True
-    hot = hot.ravel()
+    xc = np.arange(cfg["nx"]) + 0.5
+    left = np.ones_like(xc) if x0 <= 0 else 0.5 * (1.0 + np.tanh((xc - x0) / edge))
+    right = 0.5 * (1.0 - np.tanh((xc - x1) / edge))
+    prof = np.broadcast_to(left * right, shape)
+    if wall_taper > 0:
+        d = _isothermal_distance(cfg, solid, int(np.ceil(wall_taper)))
+        prof = prof * np.clip(d / wall_taper, 0.0, 1.0)
+    prof = prof.ravel()
+    T = cfg["T_in"] + (T_hot - cfg["T_in"]) * prof
     Yb = burnt_Y(cfg["Y_in"]) if burnt else cfg["Y_in"]
     Y = np.empty((5, N), dtype=np.float64)
     for k in range(5):
-        Y[k] = np.where(hot, Yb[k], cfg["Y_in"][k])
-    T = T.ravel()
+        Y[k] = cfg["Y_in"][k] + (Yb[k] - cfg["Y_in"][k]) * prof
     s = solid.ravel().astype(bool)
     T[s] = cfg["T_solid"]
     return T, Y
@@ -98,7 +140,7 @@ def channel(nx=256, ny=32, walls="adiabatic", T_wall=300.0, u_in=0.01, ignite=(0
     """2-D channel: inlet at -x, outlet at +x, walls at +-y; hot band in
     columns ignite[0]..ignite[1]-1 (256x32 adiabatic = the plain FP64 case)."""
     wt = "wall_adiabatic" if walls == "adiabatic" else "wall_isothermal"
-    cfg = base_config(dim=2, nx=nx, ny=ny, bc=["inlet", "outlet", wt, wt, "periodic", "periodic"],
+    cfg = base_config(dim=2, nx=nx, ny=ny, bc=["inlet", "outlet_pressure", wt, wt, "periodic", "periodic"],
                       T_wall=[T_wall] * 6, u_in=u_in, **over)
     solid = np.zeros((ny, nx), dtype=np.uint8)
     T, Y = ignition_fields(cfg, solid, *ignite)
@@ -115,7 +157,7 @@ def batched_channels(widths=None, length=1024, T_wall=300.0, u_in=0.01, ignite=(
         widths = [16 + 12 * j for j in range(16)]
     ny = sum(widths) + len(widths) - 1
     cfg = base_config(dim=2, nx=length, ny=ny,
-                      bc=["inlet", "outlet", "wall_isothermal", "wall_isothermal", "periodic", "periodic"],
+                      bc=["inlet", "outlet_pressure", "wall_isothermal", "wall_isothermal", "periodic", "periodic"],
                       T_wall=[T_wall] * 6, T_solid=T_wall, solid_isothermal=True, u_in=u_in, **over)
     solid = np.zeros((ny, length), dtype=np.uint8)
     segments = []
@@ -136,7 +178,7 @@ def cylinder_burner(nx=2048, ny=512, d=40, pitch=64, x_range=(512, 1536), T_wall
     alternate rows offset by pitch/2) filling x_range, isothermal at T_wall,
     periodic in y, premixed inlet at equivalence ratio phi; a hot band of
     ignite_width columns just downstream of the array."""
-    cfg = base_config(dim=2, nx=nx, ny=ny, bc=["inlet", "outlet", "periodic", "periodic", "periodic", "periodic"],
+    cfg = base_config(dim=2, nx=nx, ny=ny, bc=["inlet", "outlet_pressure", "periodic", "periodic", "periodic", "periodic"],
                       T_solid=T_wall, solid_isothermal=True, u_in=u_in, Y_in=premixed_Y(phi), **over)
     yy, xx = np.mgrid[0:ny, 0:nx]
     solid = np.zeros((ny, nx), dtype=bool)
@@ -159,7 +201,7 @@ def sphere_packing(nx=512, ny=256, nz=256, x_range=(64, 448), r_range=(8.0, 16.0
     porosity of that slab drops to `porosity`; periodic in y and z,
     isothermal solid; inlet at -x; hot band right after the packing."""
     cfg = base_config(dim=3, nx=nx, ny=ny, nz=nz,
-                      bc=["inlet", "outlet", "periodic", "periodic", "periodic", "periodic"],
+                      bc=["inlet", "outlet_pressure", "periodic", "periodic", "periodic", "periodic"],
                       T_solid=T_wall, solid_isothermal=True, u_in=u_in, **over)
     rng = np.random.Generator(np.random.PCG64(seed))
     solid = np.zeros((nz, ny, nx), dtype=bool)

@@ -1,0 +1,230 @@
+"""Thin ctypes binding of the C ABI in ``include/lbfd.h``.
+
+Function names match the C entry points; this module only marshals
+arguments.  Every step of the method runs in the CUDA kernels of
+``liblbfd.so``.  There is no CPU fallback: if the library or a CUDA device
+is missing, creation fails with an exception.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import inputs
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblbfd.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, EUNSTABLE, ENOTSUP = range(8)
+BC = {"periodic": 0, "wall_adiabatic": 1, "wall_isothermal": 2, "inlet": 3, "outlet": 4, "outlet_pressure": 5}
+FP64, MIXED = 0, 1
+NSP = 5
+FIELD_T, FIELD_Y0, FIELD_UX, FIELD_UY, FIELD_UZ, FIELD_PH, FIELD_RHO, FIELD_HRR, FIELD_G0 = 0, 1, 6, 7, 8, 9, 10, 11, 16
+NDIAG = 8
+DIAG_KEYS = ("x_f", "mass", "heat_release", "fuel_consumption", "T_max", "x_hrr_max", "n_nonfinite", "n_fluid")
+
+# exported symbols: every entry point declared in include/lbfd.h
+SYMBOLS = (
+    "lbfd_create", "lbfd_destroy", "lbfd_set_stream", "lbfd_init_fields", "lbfd_set_state", "lbfd_step",
+    "lbfd_read_field", "lbfd_diagnostics", "lbfd_flame_position", "lbfd_state_bytes", "lbfd_get_state_raw",
+    "lbfd_set_state_raw", "lbfd_steps_done", "lbfd_num_cells", "lbfd_num_populations", "lbfd_strerror",
+    "lbfd_last_error",
+)
+
+
+class LbfdError(RuntimeError):
+    def __init__(self, status: int, where: str, lib=None):
+        msg = f"{where}: status {status}"
+        if lib is not None:
+            msg += f" ({lib.lbfd_strerror(status).decode()})"
+            last = lib.lbfd_last_error().decode()
+            if last:
+                msg += f" [{last}]"
+        super().__init__(msg)
+        self.status = status
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("bc", ctypes.c_int * 6), ("T_wall", ctypes.c_double * 6)]
+
+
+class Mechanism(ctypes.Structure):
+    _fields_ = [("n_species", ctypes.c_int), ("W", ctypes.c_double * 8), ("nu_stoich", ctypes.c_double * 8),
+                ("fuel", ctypes.c_int), ("oxidiser", ctypes.c_int), ("A", ctypes.c_double),
+                ("Ta", ctypes.c_double), ("Q", ctypes.c_double), ("cp", ctypes.c_double),
+                ("Le", ctypes.c_double * 8)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("nu", ctypes.c_double), ("Pr", ctypes.c_double), ("omega_bulk", ctypes.c_double),
+                ("omega_hi", ctypes.c_double), ("u_in", ctypes.c_double), ("T_in", ctypes.c_double),
+                ("Y_in", ctypes.c_double * 8), ("T_solid", ctypes.c_double), ("solid_isothermal", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dt", ctypes.c_double), ("T_fp64", ctypes.c_double),
+                ("weno_eps", ctypes.c_double), ("precision", ctypes.c_int), ("poiseuille_inlet", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load liblbfd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2304_05657_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    H = ctypes.c_void_p
+    D = ctypes.POINTER(ctypes.c_double)
+    lib.lbfd_create.argtypes = [ctypes.POINTER(Grid), ctypes.c_void_p, ctypes.POINTER(Mechanism),
+                                ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_void_p)]
+    lib.lbfd_destroy.argtypes = [H]
+    lib.lbfd_set_stream.argtypes = [H, ctypes.c_void_p]
+    lib.lbfd_init_fields.argtypes = [H, D, D]
+    lib.lbfd_set_state.argtypes = [H, D, D, ctypes.c_void_p]
+    lib.lbfd_step.argtypes = [H, ctypes.c_int]
+    lib.lbfd_read_field.argtypes = [H, ctypes.c_int, D]
+    lib.lbfd_diagnostics.argtypes = [H, D]
+    lib.lbfd_flame_position.argtypes = [H, D, D, D]
+    lib.lbfd_state_bytes.restype = ctypes.c_size_t
+    lib.lbfd_state_bytes.argtypes = [H]
+    lib.lbfd_get_state_raw.argtypes = [H, ctypes.c_void_p, ctypes.c_size_t]
+    lib.lbfd_set_state_raw.argtypes = [H, ctypes.c_void_p, ctypes.c_size_t]
+    lib.lbfd_steps_done.restype = ctypes.c_longlong
+    lib.lbfd_steps_done.argtypes = [H]
+    lib.lbfd_num_cells.restype = ctypes.c_longlong
+    lib.lbfd_num_cells.argtypes = [H]
+    lib.lbfd_num_populations.restype = ctypes.c_int
+    lib.lbfd_num_populations.argtypes = [H]
+    lib.lbfd_strerror.restype = ctypes.c_char_p
+    lib.lbfd_strerror.argtypes = [ctypes.c_int]
+    lib.lbfd_last_error.restype = ctypes.c_char_p
+    lib.lbfd_last_error.argtypes = []
+    _lib = lib
+    return lib
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def make_structs(cfg: dict):
+    g = Grid()
+    g.dim, g.nx, g.ny = cfg["dim"], cfg["nx"], cfg["ny"]
+    g.nz = cfg["nz"] if cfg["dim"] == 3 else 1
+    for f in range(6):
+        g.bc[f] = BC[cfg["bc"][f]]
+        g.T_wall[f] = cfg["T_wall"][f]
+    m = Mechanism()
+    m.n_species = len(cfg["W"])
+    for k in range(m.n_species):
+        m.W[k], m.nu_stoich[k], m.Le[k] = cfg["W"][k], cfg["nu_stoich"][k], cfg["Le"][k]
+    m.fuel, m.oxidiser = cfg["fuel"], cfg["oxidiser"]
+    m.A, m.Ta, m.Q, m.cp = cfg["A"], cfg["Ta"], cfg["Q"], cfg["cp"]
+    p = Params()
+    p.nu, p.Pr, p.omega_bulk, p.omega_hi = cfg["nu"], cfg["Pr"], cfg["omega_bulk"], cfg["omega_hi"]
+    p.u_in, p.T_in = cfg["u_in"], cfg["T_in"]
+    for k in range(len(cfg["Y_in"])):
+        p.Y_in[k] = cfg["Y_in"][k]
+    p.T_solid, p.solid_isothermal = cfg["T_solid"], int(cfg["solid_isothermal"])
+    p.dx, p.dt, p.T_fp64, p.weno_eps = cfg["dx"], cfg["dt"], cfg["T_fp64"], cfg["weno_eps"]
+    p.precision = MIXED if cfg.get("precision", "fp64") == "mixed" else FP64
+    p.poiseuille_inlet = int(cfg["poiseuille_inlet"])
+    return g, m, p
+
+
+def _check(lib, st: int, where: str, allow=()):
+    if st != OK and st not in allow:
+        raise LbfdError(st, where, lib)
+    return st
+
+
+class Solver:
+    """One lbfd handle: device-resident state on the current CUDA device."""
+
+    def __init__(self, cfg: dict, solid: np.ndarray, stream=None):
+        self.lib = load()
+        self.cfg = dict(cfg)
+        self._structs = make_structs(cfg)
+        g, m, p = self._structs
+        solid = np.ascontiguousarray(solid, dtype=np.uint8).ravel()
+        if solid.size != inputs.ncells(cfg):
+            raise ValueError("mask size does not match the grid")
+        h = ctypes.c_void_p()
+        st = self.lib.lbfd_create(ctypes.byref(g), solid.ctypes.data_as(ctypes.c_void_p), ctypes.byref(m),
+                                  ctypes.byref(p), ctypes.byref(h))
+        _check(self.lib, st, "lbfd_create")
+        self.h = h
+        self.N = int(self.lib.lbfd_num_cells(h))
+        self.Q = int(self.lib.lbfd_num_populations(h))
+        if stream is not None:
+            self.set_stream(stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lbfd_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, an int handle, or None."""
+        handle = getattr(stream, "cuda_stream", stream)
+        _check(self.lib, self.lib.lbfd_set_stream(self.h, ctypes.c_void_p(handle or 0)), "lbfd_set_stream")
+
+    def init_fields(self, T, Y):
+        T = np.ascontiguousarray(T, dtype=np.float64).ravel()
+        Y = np.ascontiguousarray(Y, dtype=np.float64).reshape(NSP, self.N)
+        _check(self.lib, self.lib.lbfd_init_fields(self.h, _dp(T), _dp(Y)), "lbfd_init_fields")
+
+    def set_state(self, T, Y, g=None):
+        T = np.ascontiguousarray(T, dtype=np.float64).ravel()
+        Y = np.ascontiguousarray(Y, dtype=np.float64).reshape(NSP, self.N)
+        gp = None
+        if g is not None:
+            g = np.ascontiguousarray(g, dtype=np.float64).reshape(self.Q, self.N)
+            gp = g.ctypes.data_as(ctypes.c_void_p)
+        _check(self.lib, self.lib.lbfd_set_state(self.h, _dp(T), _dp(Y), gp), "lbfd_set_state")
+
+    def step(self, n: int = 1):
+        _check(self.lib, self.lib.lbfd_step(self.h, int(n)), "lbfd_step")
+
+    def read_field(self, field: int) -> np.ndarray:
+        out = np.empty(self.N)
+        _check(self.lib, self.lib.lbfd_read_field(self.h, int(field), _dp(out)), "lbfd_read_field")
+        return out
+
+    def get_state(self):
+        """(T[N], Y[5,N], g[Q,N]) as float64 host arrays."""
+        T = self.read_field(FIELD_T)
+        Y = np.stack([self.read_field(FIELD_Y0 + k) for k in range(NSP)])
+        g = np.stack([self.read_field(FIELD_G0 + i) for i in range(self.Q)])
+        return T, Y, g
+
+    def diagnostics(self) -> dict:
+        out = np.empty(NDIAG)
+        _check(self.lib, self.lib.lbfd_diagnostics(self.h, _dp(out)), "lbfd_diagnostics", allow=(ENONFINITE,))
+        return dict(zip(DIAG_KEYS, out.tolist()))
+
+    def flame_position(self):
+        x, m, q = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(self.lib, self.lib.lbfd_flame_position(self.h, ctypes.byref(x), ctypes.byref(m), ctypes.byref(q)),
+               "lbfd_flame_position", allow=(ENONFINITE,))
+        return x.value, m.value, q.value
+
+    def state_bytes(self) -> int:
+        return int(self.lib.lbfd_state_bytes(self.h))
+
+    def get_state_raw(self, ptr: int, nbytes: int):
+        _check(self.lib, self.lib.lbfd_get_state_raw(self.h, ctypes.c_void_p(ptr), nbytes), "lbfd_get_state_raw")
+
+    def set_state_raw(self, ptr: int, nbytes: int):
+        _check(self.lib, self.lib.lbfd_set_state_raw(self.h, ctypes.c_void_p(ptr), nbytes), "lbfd_set_state_raw")
+
+    @property
+    def steps_done(self) -> int:
+        return int(self.lib.lbfd_steps_done(self.h))

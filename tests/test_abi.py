@@ -1,0 +1,36 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry
+point that include/lbfd.h declares (no compute call is made here)."""
+import ctypes
+import os
+import re
+
+from paper_2304_05657_gb300 import build, lbfd
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "lbfd.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbfd_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_matches_binding_list():
+    assert declared_functions() == sorted(lbfd.SYMBOLS)
+
+
+def test_library_exports_every_declared_symbol():
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    missing = [name for name in declared_functions() if not hasattr(lib, name)]
+    assert not missing, missing
+
+
+def test_strerror_and_no_device_path():
+    lib = lbfd.load(build.build())
+    assert lib.lbfd_strerror(0) == b"ok"
+    assert lib.lbfd_strerror(6).startswith(b"parameters")
+    # null arguments are rejected before any CUDA call
+    assert lib.lbfd_create(None, None, None, None, None) == lbfd.EINVAL
+    assert lib.lbfd_step(None, 1) == lbfd.EINVAL
+    assert lib.lbfd_destroy(None) == lbfd.OK

@@ -1,0 +1,185 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (relative L2 per field, i.e. per scalar field and per population
+plane, over all cells):
+  - FP64 kernels: 1e-10 after the stated number of steps; the two codes
+    differ only in rounding order (axis-wise moment transforms on the GPU vs
+    a dense linear solve in the oracle, a rearranged WENO weight formula).
+  - mixed FP32 kernels: 1e-5 on T and Y after 1000 steps of the 256x32
+    channel; the populations are compared in absolute terms against their
+    own scale (their mean is ~0, so a relative norm is meaningless).
+"""
+import numpy as np
+import pytest
+
+from paper_2304_05657_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_l2(a, b):
+    den = np.linalg.norm(b)
+    if den == 0.0:
+        return float(np.linalg.norm(a - b))
+    return float(np.linalg.norm(a - b) / den)
+
+
+def compare_states(gpu_state, orc_state, tol, label):
+    Tg, Yg, gg = gpu_state
+    To, Yo, go = orc_state
+    errs = {"T": rel_l2(Tg, To)}
+    for k in range(Yo.shape[0]):
+        errs[f"Y{k}"] = rel_l2(Yg[k], Yo[k])
+    for i in range(go.shape[0]):
+        errs[f"g{i}"] = rel_l2(gg[i], go[i])
+    bad = {k: v for k, v in errs.items() if not (v <= tol)}
+    assert not bad, f"{label}: fields above {tol:g}: {bad}"
+    return errs
+
+
+def run_pair(lbfd, oracle, cfg, solid, T, Y, g, steps):
+    s = lbfd.Solver(cfg, solid)
+    s.set_state(T, Y, g)
+    s.step(steps)
+    gpu = s.get_state()
+    o = oracle.Sim(cfg, solid)
+    o.set_state(T, Y, g)
+    o.step(steps)
+    return s, o, gpu, o.get_state()
+
+
+# ---------------------------------------------------------------------------
+# cases: several tiles and a ragged tail, every boundary type
+# ---------------------------------------------------------------------------
+
+def case_channel_adiabatic():
+    cfg, solid, T, Y = inputs.channel(nx=83, ny=21, ignite=(0, 20))
+    g, T, Y = inputs.perturbed_state(cfg, solid, T, Y, seed=1)
+    return cfg, solid, T, Y, g
+
+
+def case_channel_isothermal_poiseuille():
+    cfg, solid, T, Y = inputs.channel(nx=70, ny=19, walls="isothermal", T_wall=350.0, ignite=(30, 50),
+                                      poiseuille_inlet=True, u_in=0.02)
+    g, T, Y = inputs.perturbed_state(cfg, solid, T, Y, seed=2)
+    return cfg, solid, T, Y, g
+
+
+def case_periodic_obstacles():
+    rng = np.random.Generator(np.random.PCG64(3))
+    cfg = inputs.base_config(dim=2, nx=67, ny=29, bc=["periodic"] * 6, u_in=0.0)
+    solid = np.zeros((29, 67), dtype=np.uint8)
+    for _ in range(6):  # blocks of 1..4 cells, incl. one-cell-thin walls
+        x, y = rng.integers(0, 67), rng.integers(0, 29)
+        solid[y:y + rng.integers(1, 5), x:x + rng.integers(1, 5)] = 1
+    solid[10, 5:40] = 1  # a thin wall with fluid on both sides
+    T, Y = inputs.ignition_fields(cfg, solid, 20, 35)
+    g, T, Y = inputs.perturbed_state(cfg, solid, T, Y, seed=4)
+    return cfg, solid, T, Y, g
+
+
+def case_obstacles_adiabatic_solid():
+    cfg, solid, T, Y = inputs.channel(nx=61, ny=23, ignite=(35, 50), solid_isothermal=False)
+    yy, xx = np.mgrid[0:23, 0:61]
+    solid = (((xx + 0.5 - 20) ** 2 + (yy + 0.5 - 11.5) ** 2) <= 36).astype(np.uint8)
+    T, Y = inputs.ignition_fields(cfg, solid, 35, 50)
+    g, T, Y = inputs.perturbed_state(cfg, solid, T, Y, seed=5)
+    return cfg, solid, T, Y, g
+
+
+def case_batched():
+    cfg, solid, T, Y, seg = inputs.batched_channels(widths=[5, 8, 13], length=45, ignite=(10, 25))
+    g, T, Y = inputs.perturbed_state(cfg, solid, T, Y, seed=6)
+    return cfg, solid, T, Y, g
+
+
+def case_d3q27():
+    cfg, solid, T, Y = inputs.sphere_packing(nx=19, ny=10, nz=9, x_range=(3, 13), r_range=(2.0, 3.5),
+                                             porosity=0.8, seed=7, ignite_width=4)
+    cfg["bc"][2] = cfg["bc"][3] = "wall_isothermal"
+    cfg["T_wall"] = [320.0] * 6
+    g, T, Y = inputs.perturbed_state(cfg, solid, T, Y, seed=8)
+    return cfg, solid, T, Y, g
+
+
+CASES_2D = {
+    "channel_adiabatic": case_channel_adiabatic,
+    "channel_isothermal_poiseuille": case_channel_isothermal_poiseuille,
+    "periodic_obstacles": case_periodic_obstacles,
+    "obstacles_adiabatic_solid": case_obstacles_adiabatic_solid,
+    "batched": case_batched,
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES_2D))
+def test_fp64_parity_2d(lbfd_lib, oracle_mod, name):
+    cfg, solid, T, Y, g = CASES_2D[name]()
+    _, _, gpu, orc = run_pair(lbfd_lib, oracle_mod, cfg, solid, T, Y, g, steps=100)
+    compare_states(gpu, orc, 1e-10, name)
+
+
+def test_fp64_parity_d3q27(lbfd_lib, oracle_mod):
+    cfg, solid, T, Y, g = case_d3q27()
+    _, _, gpu, orc = run_pair(lbfd_lib, oracle_mod, cfg, solid, T, Y, g, steps=20)
+    compare_states(gpu, orc, 1e-10, "d3q27")
+
+
+def test_fp64_parity_one_step_exact_inputs(lbfd_lib, oracle_mod):
+    """After one step every cell must agree to ~1e-13 relative (no growth)."""
+    cfg, solid, T, Y, g = case_periodic_obstacles()
+    _, _, gpu, orc = run_pair(lbfd_lib, oracle_mod, cfg, solid, T, Y, g, steps=1)
+    compare_states(gpu, orc, 1e-12, "one step")
+
+
+def test_fp64_diagnostics_match(lbfd_lib, oracle_mod):
+    cfg, solid, T, Y, g = case_channel_adiabatic()
+    s, o, _, _ = run_pair(lbfd_lib, oracle_mod, cfg, solid, T, Y, g, steps=30)
+    dg, do = s.diagnostics(), o.diagnostics()
+    for key in ("x_f", "mass", "heat_release", "fuel_consumption", "T_max"):
+        assert abs(dg[key] - do[key]) <= 1e-11 * max(1.0, abs(do[key])), (key, dg[key], do[key])
+    for key in ("x_hrr_max", "n_nonfinite", "n_fluid"):
+        assert dg[key] == do[key], (key, dg[key], do[key])
+
+
+def test_fp64_empty_and_degenerate(lbfd_lib, oracle_mod):
+    """A domain that is all solid does nothing; a one-cell-wide periodic
+    column and a one-row channel match the oracle."""
+    cfg = inputs.base_config(dim=2, nx=9, ny=4, bc=["periodic"] * 6)
+    solid = np.ones((4, 9), dtype=np.uint8)
+    T, Y = inputs.ignition_fields(cfg, solid, 0, 3)
+    s = lbfd_lib.Solver(cfg, solid)
+    s.set_state(T, Y)
+    s.step(5)
+    Tg, Yg, gg = s.get_state()
+    assert np.array_equal(Tg, T) and np.array_equal(Yg, Y) and not gg.any()
+    assert s.diagnostics()["n_fluid"] == 0
+    for (nx, ny, bc) in [(1, 7, ["periodic"] * 6),
+                         (33, 1, ["inlet", "outlet", "periodic", "periodic", "periodic", "periodic"])]:
+        cfg = inputs.base_config(dim=2, nx=nx, ny=ny, bc=bc)
+        solid = np.zeros((ny, nx), dtype=np.uint8)
+        T, Y = inputs.ignition_fields(cfg, solid, 0, min(nx, 10))
+        g, T, Y = inputs.perturbed_state(cfg, solid, T, Y, seed=9)
+        _, _, gpu, orc = run_pair(lbfd_lib, oracle_mod, cfg, solid, T, Y, g, steps=20)
+        compare_states(gpu, orc, 1e-10, f"{nx}x{ny}")
+
+
+def test_mixed_precision_channel_1000_steps(lbfd_lib, oracle_mod):
+    """FP32 storage/arithmetic (FP64 Arrhenius above 1000 K) vs the FP64
+    oracle on the 256x32 adiabatic channel after 1000 steps."""
+    cfg, solid, T, Y = inputs.channel(nx=256, ny=32)
+    T, Y = inputs.ignition_fields(cfg, solid, 0, 20, burnt=False)
+    cfg_m = dict(cfg, precision="mixed")
+    s = lbfd_lib.Solver(cfg_m, solid)
+    s.set_state(T, Y)
+    s.step(1000)
+    Tg, Yg, gg = s.get_state()
+    o = oracle_mod.Sim(cfg, solid)
+    o.set_state(T, Y)
+    o.step(1000)
+    To, Yo, go = o.get_state()
+    assert rel_l2(Tg, To) <= 1e-5
+    for k in range(5):
+        if np.linalg.norm(Yo[k]) > 0:
+            assert rel_l2(Yg[k], Yo[k]) <= 1e-5, k
+    scale = np.abs(go).max()
+    assert np.abs(gg - go).max() <= 1e-4 * scale
