@@ -238,6 +238,12 @@ def run_ours(args):
     for _ in range(args.warmup):
         one_step()
     torch.cuda.synchronize()
+    if args.variant is None:
+        best, tune_ms = s.autotune(reps=10)
+    else:
+        s.variant = args.variant
+        best, tune_ms = args.variant, []
+    torch.cuda.synchronize()
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local if world > 1 else 0]
@@ -294,7 +300,9 @@ def run_ours(args):
         "dtype": "f32" if precision == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": args.workload, "description": desc, "cells": ncell, "fluid_cells": fluid,
                    "precision": precision, "l2": "flushed before every timed step (256 MiB write)",
-                   "state_bytes_per_buffer": nbytes, "parallelism": f"replicas x{world}"},
+                   "state_bytes_per_buffer": nbytes, "parallelism": f"replicas x{world}",
+                   "kernel_variant": s.variant,
+                   "autotune_ms_per_variant": [round(float(t), 4) for t in tune_ms]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
                      "algorithmic_bytes_per_cell": bpc, "kernel": "step_kernel",
@@ -327,6 +335,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--baseline-steps", type=int, default=40)
     ap.add_argument("--no-baseline", action="store_true")
+    ap.add_argument("--variant", type=int, default=None, help="kernel variant (default: autotune)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -167,6 +167,26 @@ int lbfd_set_state(lbfd_handle* h, const double* T, const double* Y, const doubl
  * Each step is one launch of the fused kernel. */
 int lbfd_step(lbfd_handle* h, int n);
 
+/* Advance n coupled steps as one CUDA-graph launch (the n kernel launches
+ * are captured once, then replayed; a new n, kernel variant or stream
+ * re-captures).  On the legacy default stream the library captures on a
+ * stream of its own and synchronises it before returning. */
+int lbfd_step_graph(lbfd_handle* h, int n);
+
+/* Kernel variants of the step: 0 is the general form (any cell, D2Q9 and
+ * D3Q27); in 2-D, 1..4 are shared-memory tiles of 32x8, 32x4, 64x4 and
+ * 32x16 cells with a fast path for interior cells.  All variants compute
+ * the same step up to rounding order.  Default: 1 in 2-D, 0 in 3-D. */
+int lbfd_num_variants(const lbfd_handle* h);
+int lbfd_get_variant(const lbfd_handle* h);
+int lbfd_set_variant(lbfd_handle* h, int variant);
+
+/* Autotuner: time every variant over `reps` launches on the current state
+ * (the output buffer is overwritten, the state does not advance), select
+ * the fastest and return it in *best; ms_per_variant (may be NULL) gets
+ * lbfd_num_variants(h) mean launch times [ms].  Synchronises. */
+int lbfd_autotune(lbfd_handle* h, int reps, double* ms_per_variant, int* best);
+
 /* Copy one field (LBFD_FIELD_*) of all N cells to host FP64 out[N].
  * Synchronises the handle's stream. */
 int lbfd_read_field(lbfd_handle* h, int field, double* out);

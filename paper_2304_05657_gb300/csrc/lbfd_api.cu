@@ -35,8 +35,14 @@ struct lbfd_handle {
     double* tmp;          // device read-out buffer (ncell doubles)
     cudaStream_t stream;
     long long steps;
+    int variant;          // kernel variant (lbfd::launch_step)
     StepParams<double> Pd;
     StepParams<float> Pf;
+    // CUDA graph of `graph_n` steps starting from buffer `graph_parity`
+    cudaGraphExec_t graph;
+    int graph_n, graph_parity, graph_variant;
+    cudaStream_t graph_stream;  // stream the graph was captured on
+    cudaStream_t own_stream;    // created when capture needs a non-legacy stream
 };
 
 namespace {
@@ -160,6 +166,8 @@ int validate(const lbfd_grid* G, const lbfd_mechanism* M, const lbfd_params* p)
 void free_handle(lbfd_handle* h)
 {
     if (!h) return;
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->own_stream) cudaStreamDestroy(h->own_stream);
     for (int b = 0; b < 2; ++b)
         if (h->buf[b]) cudaFree(h->buf[b]);
     if (h->solid) cudaFree(h->solid);
@@ -243,6 +251,7 @@ int lbfd_create(const lbfd_grid* grid, const uint8_t* solid_mask, const lbfd_mec
     h->esz = h->precision == LBFD_FP64 ? 8 : 4;
     h->planes = (size_t)h->Q + 1 + lbfd::NSP;
     h->stream = nullptr;
+    h->variant = h->dim == 2 ? 1 : 0;
     const size_t bytes = h->planes * (size_t)h->stride * h->esz;
     for (int b = 0; b < 2; ++b) {
         e = cudaMalloc(&h->buf[b], bytes);
@@ -327,14 +336,116 @@ int lbfd_step(lbfd_handle* h, int n)
 {
     if (!h || n < 0) return LBFD_EINVAL;
     for (int it = 0; it < n; ++it) {
-        cudaError_t e = lbfd::launch_step(h->dim, h->precision, h->Pd, h->Pf, view(h, h->cur), view(h, h->cur ^ 1),
-                                          h->solid, h->stream);
+        cudaError_t e = lbfd::launch_step(h->dim, h->precision, h->variant, h->Pd, h->Pf, view(h, h->cur),
+                                          view(h, h->cur ^ 1), h->solid, h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
         h->cur ^= 1;
         h->steps++;
     }
     return LBFD_OK;
 }
+
+int lbfd_step_graph(lbfd_handle* h, int n)
+{
+    if (!h || n < 1) return LBFD_EINVAL;
+    cudaStream_t s = h->stream;
+    if (s == nullptr) {  // the legacy default stream cannot be captured
+        if (!h->own_stream) CK(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
+        s = h->own_stream;
+        CK(cudaDeviceSynchronize());
+    }
+    if (!h->graph || h->graph_n != n || h->graph_parity != h->cur || h->graph_variant != h->variant ||
+        h->graph_stream != s) {
+        if (h->graph) {
+            cudaGraphExecDestroy(h->graph);
+            h->graph = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        int cur = h->cur;
+        cudaError_t le = cudaSuccess;
+        for (int it = 0; it < n && le == cudaSuccess; ++it) {
+            le = lbfd::launch_step(h->dim, h->precision, h->variant, h->Pd, h->Pf, view(h, cur), view(h, cur ^ 1),
+                                   h->solid, s);
+            cur ^= 1;
+        }
+        cudaError_t ee = cudaStreamEndCapture(s, &g);
+        if (le != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return cuda_fail(le, "step launch during capture");
+        }
+        if (ee != cudaSuccess) return cuda_fail(ee, "cudaStreamEndCapture");
+        cudaError_t ie = cudaGraphInstantiate(&h->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) {
+            h->graph = nullptr;
+            return cuda_fail(ie, "cudaGraphInstantiate");
+        }
+        h->graph_n = n;
+        h->graph_parity = h->cur;
+        h->graph_variant = h->variant;
+        h->graph_stream = s;
+    }
+    CK(cudaGraphLaunch(h->graph, s));
+    if (s != h->stream) CK(cudaStreamSynchronize(s));
+    h->cur ^= (n & 1);
+    h->steps += n;
+    return LBFD_OK;
+}
+
+int lbfd_num_variants(const lbfd_handle* h) { return h ? lbfd::num_variants(h->dim) : -1; }
+
+int lbfd_get_variant(const lbfd_handle* h) { return h ? h->variant : -1; }
+
+int lbfd_set_variant(lbfd_handle* h, int variant)
+{
+    if (!h || variant < 0 || variant >= lbfd::num_variants(h->dim)) return LBFD_EINVAL;
+    h->variant = variant;
+    return LBFD_OK;
+}
+
+int lbfd_autotune(lbfd_handle* h, int reps, double* ms_per_variant, int* best)
+{
+    if (!h || reps < 1) return LBFD_EINVAL;
+    const int nv = lbfd::num_variants(h->dim);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int arg = h->variant;
+    float best_ms = 3.4e38f;
+    for (int v = 0; v < nv; ++v) {
+        // the input buffer is never written: the state does not advance
+        cudaError_t e = cudaSuccess;
+        for (int r = 0; r < 2 && e == cudaSuccess; ++r)
+            e = lbfd::launch_step(h->dim, h->precision, v, h->Pd, h->Pf, view(h, h->cur), view(h, h->cur ^ 1),
+                                  h->solid, h->stream);
+        cudaEventRecord(e0, h->stream);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r)
+            e = lbfd::launch_step(h->dim, h->precision, v, h->Pd, h->Pf, view(h, h->cur), view(h, h->cur ^ 1),
+                                  h->solid, h->stream);
+        cudaEventRecord(e1, h->stream);
+        cudaError_t se = cudaEventSynchronize(e1);
+        if (e != cudaSuccess || se != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return cuda_fail(e != cudaSuccess ? e : se, "autotune");
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= reps;
+        if (ms_per_variant) ms_per_variant[v] = ms;
+        if (ms < best_ms) {
+            best_ms = ms;
+            arg = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->variant = arg;
+    if (best) *best = arg;
+    return LBFD_OK;
+}
+
 
 int lbfd_read_field(lbfd_handle* h, int field, double* out)
 {

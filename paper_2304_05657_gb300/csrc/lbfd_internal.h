@@ -19,8 +19,11 @@ struct StateView {
 
 // Launch one fused coupled step: state `in` -> state `out`.
 // precision: 0 = FP64 (S = R = double), 1 = mixed (S = R = float).
-cudaError_t launch_step(int dim, int precision, const StepParams<double>& Pd, const StepParams<float>& Pf,
-                        StateView in, StateView out, const uint8_t* solid, cudaStream_t stream);
+// variant: 0 = general form, 1.. = 2-D shared-memory tiles (see lbfd_step.cu)
+cudaError_t launch_step(int dim, int precision, int variant, const StepParams<double>& Pd,
+                        const StepParams<float>& Pf, StateView in, StateView out, const uint8_t* solid,
+                        cudaStream_t stream);
+int num_variants(int dim);
 
 // Diagnostics reduction into the device scratch `red` (LBFD_NDIAG + extra
 // words, zeroed by the launcher); FP64 accumulation.

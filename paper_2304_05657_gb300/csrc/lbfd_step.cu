@@ -1,10 +1,12 @@
-// lbfd_step.cu -- the fused coupled LB/FD step kernel (sm_103a).
+// lbfd_step.cu -- launchers of the fused coupled LB/FD step (sm_103a).
 //
-// One thread updates one cell: pull streaming, FD scalar update and cumulant
-// collision are fused so that each step reads the state once and writes it
-// once (populations A/B double-buffered, SoA planes, x fastest).
+// Variant 0 is the general form (one thread per cell, every access through
+// the boundary classification; D2Q9 and D3Q27).  Variants 1.. are 2-D
+// shared-memory tiles of different shapes (lbfd_step_tiled.cuh); the
+// autotuner picks among them by timing.  All variants compute the same
+// step; they differ only in rounding order.
 #include "lbfd_internal.h"
-#include "lbfd_step_general.cuh"
+#include "lbfd_step_tiled.cuh"
 
 namespace lbfd {
 
@@ -36,14 +38,48 @@ static cudaError_t launch_general(const StepParams<R>& P, StateView in, StateVie
     return cudaGetLastError();
 }
 
-cudaError_t launch_step(int dim, int precision, const StepParams<double>& Pd, const StepParams<float>& Pf,
-                        StateView in, StateView out, const uint8_t* solid, cudaStream_t stream)
+template <typename S, typename R, int TX, int TY>
+static cudaError_t launch_tiled(const StepParams<R>& P, StateView in, StateView out, const uint8_t* solid,
+                                cudaStream_t stream)
 {
+    constexpr size_t smem = tile_smem_bytes<R, TX, TY>();
+    auto kern = step_kernel_tiled2d<S, R, TX, TY>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
+    kern<<<grid, dim3(TX, TY), smem, stream>>>(P, (const S*)in.g, (S*)out.g, (const S*)in.T, (S*)out.T,
+                                               (const S*)in.Y, (S*)out.Y, solid);
+    return cudaGetLastError();
+}
+
+template <typename S, typename R>
+static cudaError_t launch_2d(int variant, const StepParams<R>& P, StateView in, StateView out, const uint8_t* solid,
+                             cudaStream_t stream)
+{
+    switch (variant) {
+    case 0: return launch_general<2, S, R>(P, in, out, solid, stream);
+    case 1: return launch_tiled<S, R, 32, 8>(P, in, out, solid, stream);
+    case 2: return launch_tiled<S, R, 32, 4>(P, in, out, solid, stream);
+    case 3: return launch_tiled<S, R, 64, 4>(P, in, out, solid, stream);
+    case 4: return launch_tiled<S, R, 32, 16>(P, in, out, solid, stream);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+int num_variants(int dim) { return dim == 2 ? 5 : 1; }
+
+cudaError_t launch_step(int dim, int precision, int variant, const StepParams<double>& Pd,
+                        const StepParams<float>& Pf, StateView in, StateView out, const uint8_t* solid,
+                        cudaStream_t stream)
+{
+    if (variant < 0 || variant >= num_variants(dim)) return cudaErrorInvalidValue;
     if (precision == 0) {
-        if (dim == 2) return launch_general<2, double, double>(Pd, in, out, solid, stream);
+        if (dim == 2) return launch_2d<double, double>(variant, Pd, in, out, solid, stream);
         return launch_general<3, double, double>(Pd, in, out, solid, stream);
     }
-    if (dim == 2) return launch_general<2, float, float>(Pf, in, out, solid, stream);
+    if (dim == 2) return launch_2d<float, float>(variant, Pf, in, out, solid, stream);
     return launch_general<3, float, float>(Pf, in, out, solid, stream);
 }
 

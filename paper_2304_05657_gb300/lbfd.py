@@ -30,7 +30,8 @@ SYMBOLS = (
     "lbfd_create", "lbfd_destroy", "lbfd_set_stream", "lbfd_init_fields", "lbfd_set_state", "lbfd_step",
     "lbfd_read_field", "lbfd_diagnostics", "lbfd_flame_position", "lbfd_state_bytes", "lbfd_get_state_raw",
     "lbfd_set_state_raw", "lbfd_steps_done", "lbfd_num_cells", "lbfd_num_populations", "lbfd_strerror",
-    "lbfd_last_error",
+    "lbfd_last_error", "lbfd_step_graph", "lbfd_num_variants", "lbfd_get_variant", "lbfd_set_variant",
+    "lbfd_autotune",
 )
 
 
@@ -99,6 +100,11 @@ def load(path: str = LIB_PATH):
     lib.lbfd_num_cells.argtypes = [H]
     lib.lbfd_num_populations.restype = ctypes.c_int
     lib.lbfd_num_populations.argtypes = [H]
+    lib.lbfd_step_graph.argtypes = [H, ctypes.c_int]
+    lib.lbfd_num_variants.argtypes = [H]
+    lib.lbfd_get_variant.argtypes = [H]
+    lib.lbfd_set_variant.argtypes = [H, ctypes.c_int]
+    lib.lbfd_autotune.argtypes = [H, ctypes.c_int, D, ctypes.POINTER(ctypes.c_int)]
     lib.lbfd_strerror.restype = ctypes.c_char_p
     lib.lbfd_strerror.argtypes = [ctypes.c_int]
     lib.lbfd_last_error.restype = ctypes.c_char_p
@@ -192,6 +198,29 @@ class Solver:
 
     def step(self, n: int = 1):
         _check(self.lib, self.lib.lbfd_step(self.h, int(n)), "lbfd_step")
+
+    def step_graph(self, n: int):
+        _check(self.lib, self.lib.lbfd_step_graph(self.h, int(n)), "lbfd_step_graph")
+
+    @property
+    def num_variants(self) -> int:
+        return int(self.lib.lbfd_num_variants(self.h))
+
+    @property
+    def variant(self) -> int:
+        return int(self.lib.lbfd_get_variant(self.h))
+
+    @variant.setter
+    def variant(self, v: int):
+        _check(self.lib, self.lib.lbfd_set_variant(self.h, int(v)), "lbfd_set_variant")
+
+    def autotune(self, reps: int = 20):
+        """Time every kernel variant on the current state and keep the
+        fastest; returns (best, ms per variant)."""
+        ms = np.zeros(self.num_variants)
+        best = ctypes.c_int()
+        _check(self.lib, self.lib.lbfd_autotune(self.h, int(reps), _dp(ms), ctypes.byref(best)), "lbfd_autotune")
+        return best.value, ms
 
     def read_field(self, field: int) -> np.ndarray:
         out = np.empty(self.N)

@@ -34,3 +34,26 @@ def test_strerror_and_no_device_path():
     assert lib.lbfd_create(None, None, None, None, None) == lbfd.EINVAL
     assert lib.lbfd_step(None, 1) == lbfd.EINVAL
     assert lib.lbfd_destroy(None) == lbfd.OK
+
+
+def test_create_rejects_unstable_and_invalid_parameters_without_a_gpu():
+    """Validation runs before any CUDA call, so it is testable on the CPU."""
+    import ctypes
+
+    from paper_2304_05657_gb300 import inputs
+
+    lib = lbfd.load(build.build())
+
+    def create(**over):
+        cfg = inputs.base_config(**over)
+        g, m, p = lbfd.make_structs(cfg)
+        h = ctypes.c_void_p()
+        mask = (ctypes.c_uint8 * (cfg["nx"] * cfg["ny"]))()
+        return lib.lbfd_create(ctypes.byref(g), mask, ctypes.byref(m), ctypes.byref(p), ctypes.byref(h))
+
+    assert create(u_in=0.7) == lbfd.EUNSTABLE          # |u_in| >= cs
+    assert create(nu=0.2) == lbfd.EUNSTABLE            # explicit-Euler Fourier limit
+    assert create(omega_hi=2.5) == lbfd.EUNSTABLE
+    assert create(Y_in=[0.5, 0.2, 0.0, 0.0, 0.2]) == lbfd.EINVAL  # sum != 1
+    assert create(bc=["periodic", "outlet", "periodic", "periodic", "periodic", "periodic"]) == lbfd.EINVAL
+    assert create(nx=0) == lbfd.EINVAL
