@@ -208,6 +208,42 @@ size_t lbfd_state_bytes(const lbfd_handle* h);
 int lbfd_get_state_raw(lbfd_handle* h, void* host_dst, size_t bytes);
 int lbfd_set_state_raw(lbfd_handle* h, const void* host_src, size_t bytes);
 
+/* Diagnostics without any allocation, for callers that cannot call
+ * cudaMalloc: code running where the device memory belongs to someone else
+ * (a host framework's pool, a plugin with a fixed budget), code that must
+ * not trigger the device-wide synchronisation of cudaMalloc/cudaFree in a
+ * latency-bound loop, or code that may not fail on memory pressure after
+ * start-up.  The paper has no counterpart; it is an interface variant of
+ * lbfd_diagnostics and returns the same LBFD_NDIAG values (sums are FP64 in
+ * both; they may differ by the rounding of the atomic accumulation order).
+ *
+ * Inputs are the caller's: g, T, Y are DEVICE pointers to the state planes
+ * in storage precision (params->precision: 8-byte or 4-byte values),
+ * plane k of g at g + k*plane_stride values, Y likewise; solid is a DEVICE
+ * pointer to nx*ny*nz mask bytes; stream is a cudaStream_t (NULL: legacy
+ * default stream).  out is a HOST array of LBFD_NDIAG doubles.  The call
+ * synchronises the stream.
+ *
+ * Scratch: a file-scope device array of LBFD_NOALLOC_SCRATCH_WORDS doubles
+ * (512 bytes) that every GPU which loads the library holds until the
+ * process exits.  The call needs 16 words for any grid size; a request
+ * needing more than the array holds is rejected with LBFD_EINVAL and a
+ * message in lbfd_last_error().  Every call on a device shares the array,
+ * which keeps the last call's contents; the words are cleared at the start
+ * of each call, so calls that overlap on the GPU (two streams, two host
+ * threads) race and must be serialised by the caller.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) and
+ * caches it; make that first call before any stream capture.  No cudaMalloc,
+ * cudaFree or allocating library routine is called.
+ * Errors: EINVAL (null or non-device pointer, plane_stride < cells, invalid
+ * grid/parameters as in lbfd_create), EUNSTABLE/ENOTSUP as lbfd_create,
+ * ECUDA, ENONFINITE (after filling out). */
+#define LBFD_NOALLOC_SCRATCH_WORDS 64
+int lbfd_diagnostics_noalloc(const lbfd_grid* grid, const lbfd_mechanism* mech,
+                             const lbfd_params* params, const void* g, const void* T,
+                             const void* Y, long long plane_stride, const uint8_t* solid,
+                             void* stream, double* out);
+
 /* Counters and sizes. */
 long long lbfd_steps_done(const lbfd_handle* h);
 long long lbfd_num_cells(const lbfd_handle* h);

@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -535,3 +536,116 @@ long long lbfd_num_cells(const lbfd_handle* h) { return h ? h->ncell : -1; }
 int lbfd_num_populations(const lbfd_handle* h) { return h ? h->Q : -1; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free diagnostics (see lbfd_diagnostics_noalloc in lbfd.h).
+// The reduction scratch lives in this file-scope device array instead of
+// memory from cudaMalloc.  Host code cannot use the array's name as a device
+// address, so the address is looked up once per device with
+// cudaGetSymbolAddress and cached.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) double lbfd_noalloc_scratch[LBFD_NOALLOC_SCRATCH_WORDS];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[kMaxDevices] = {};
+
+int noalloc_scratch_address(void** out)
+{
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) {
+        snprintf(g_last_error, sizeof g_last_error, "lbfd_diagnostics_noalloc: device ordinal %d >= %d", dev,
+                 kMaxDevices);
+        return LBFD_ENOTSUP;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        CK(cudaGetSymbolAddress(&p, lbfd_noalloc_scratch));
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return LBFD_OK;
+}
+
+bool is_device_pointer(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // a failed query leaves its error set: clear it
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" int lbfd_diagnostics_noalloc(const lbfd_grid* grid, const lbfd_mechanism* mech,
+                                        const lbfd_params* params, const void* g, const void* T, const void* Y,
+                                        long long plane_stride, const uint8_t* solid, void* stream, double* out)
+{
+    if (!grid || !mech || !params || !g || !T || !Y || !solid || !out) return LBFD_EINVAL;
+    int st = validate(grid, mech, params);
+    if (st != LBFD_OK) return st;
+    // the call needs lbfd::RED_WORDS words of scratch whatever the grid size
+    if (lbfd::RED_WORDS > LBFD_NOALLOC_SCRATCH_WORDS) {
+        snprintf(g_last_error, sizeof g_last_error,
+                 "lbfd_diagnostics_noalloc: needs %d scratch words, the static array holds %d", lbfd::RED_WORDS,
+                 LBFD_NOALLOC_SCRATCH_WORDS);
+        return LBFD_EINVAL;
+    }
+    lbfd_handle tmp{};  // parameters only: no buffer is allocated or owned
+    tmp.grid = *grid;
+    if (grid->dim == 2) tmp.grid.nz = 1;
+    tmp.mech = *mech;
+    tmp.prm = *params;
+    tmp.dim = grid->dim;
+    tmp.Q = grid->dim == 2 ? 9 : 27;
+    tmp.precision = params->precision;
+    tmp.ncell = (long long)tmp.grid.nx * tmp.grid.ny * tmp.grid.nz;
+    if (plane_stride < tmp.ncell) {
+        snprintf(g_last_error, sizeof g_last_error, "lbfd_diagnostics_noalloc: plane_stride %lld < cells %lld",
+                 plane_stride, tmp.ncell);
+        return LBFD_EINVAL;
+    }
+    tmp.stride = plane_stride;
+    if (!is_device_pointer(g) || !is_device_pointer(T) || !is_device_pointer(Y) || !is_device_pointer(solid)) {
+        snprintf(g_last_error, sizeof g_last_error, "lbfd_diagnostics_noalloc: inputs must be device pointers");
+        return LBFD_EINVAL;
+    }
+    void* red = nullptr;
+    st = noalloc_scratch_address(&red);
+    if (st != LBFD_OK) return st;
+    StepParams<double> P;
+    fill_params(&tmp, P);
+    StateView v;
+    v.g = const_cast<void*>(g);
+    v.T = const_cast<void*>(T);
+    v.Y = const_cast<void*>(Y);
+    cudaStream_t s = (cudaStream_t)stream;
+    // launch_diagnostics clears the words it accumulates into before use
+    CK(lbfd::launch_diagnostics(tmp.dim, tmp.precision, P, v, solid, (double*)red, s));
+    double r[lbfd::RED_WORDS];
+    CK(cudaMemcpyAsync(r, red, sizeof r, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    unsigned long long u[lbfd::RED_WORDS];
+    memcpy(u, r, sizeof r);
+    const double section = (double)u[7];
+    out[LBFD_DIAG_XF] = section > 0.0 ? r[0] / (params->Y_in[mech->fuel] * section) : 0.0;
+    out[LBFD_DIAG_MASS] = r[1];
+    out[LBFD_DIAG_HRR] = r[2];
+    out[LBFD_DIAG_FUEL] = r[3];
+    double t = -INFINITY;
+    if (u[4] != 0ull) {
+        const unsigned long long b = (u[4] >> 63) ? (u[4] & 0x7fffffffffffffffull) : ~u[4];
+        memcpy(&t, &b, sizeof t);
+    }
+    out[LBFD_DIAG_TMAX] = t;
+    out[LBFD_DIAG_XHRR] = r[9];
+    out[LBFD_DIAG_NONFINITE] = (double)u[5];
+    out[LBFD_DIAG_NFLUID] = (double)u[6];
+    return u[5] ? LBFD_ENONFINITE : LBFD_OK;
+}

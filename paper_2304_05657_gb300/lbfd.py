@@ -31,7 +31,7 @@ SYMBOLS = (
     "lbfd_read_field", "lbfd_diagnostics", "lbfd_flame_position", "lbfd_state_bytes", "lbfd_get_state_raw",
     "lbfd_set_state_raw", "lbfd_steps_done", "lbfd_num_cells", "lbfd_num_populations", "lbfd_strerror",
     "lbfd_last_error", "lbfd_step_graph", "lbfd_num_variants", "lbfd_get_variant", "lbfd_set_variant",
-    "lbfd_autotune",
+    "lbfd_autotune", "lbfd_diagnostics_noalloc",
 )
 
 
@@ -105,6 +105,9 @@ def load(path: str = LIB_PATH):
     lib.lbfd_get_variant.argtypes = [H]
     lib.lbfd_set_variant.argtypes = [H, ctypes.c_int]
     lib.lbfd_autotune.argtypes = [H, ctypes.c_int, D, ctypes.POINTER(ctypes.c_int)]
+    lib.lbfd_diagnostics_noalloc.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Mechanism), ctypes.POINTER(Params),
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong,
+                                             ctypes.c_void_p, ctypes.c_void_p, D]
     lib.lbfd_strerror.restype = ctypes.c_char_p
     lib.lbfd_strerror.argtypes = [ctypes.c_int]
     lib.lbfd_last_error.restype = ctypes.c_char_p
@@ -257,3 +260,19 @@ class Solver:
     @property
     def steps_done(self) -> int:
         return int(self.lib.lbfd_steps_done(self.h))
+
+
+def diagnostics_noalloc(cfg: dict, g_ptr: int, T_ptr: int, Y_ptr: int, plane_stride: int, solid_ptr: int,
+                        stream=None) -> dict:
+    """lbfd_diagnostics_noalloc on caller-owned device buffers (integer
+    device addresses, e.g. torch tensors' data_ptr()); the library
+    allocates nothing for this call."""
+    lib = load()
+    g, m, p = make_structs(cfg)
+    out = np.empty(NDIAG)
+    handle = getattr(stream, "cuda_stream", stream) or 0
+    st = lib.lbfd_diagnostics_noalloc(ctypes.byref(g), ctypes.byref(m), ctypes.byref(p), ctypes.c_void_p(g_ptr),
+                                      ctypes.c_void_p(T_ptr), ctypes.c_void_p(Y_ptr), int(plane_stride),
+                                      ctypes.c_void_p(solid_ptr), ctypes.c_void_p(handle), _dp(out))
+    _check(lib, st, "lbfd_diagnostics_noalloc", allow=(ENONFINITE,))
+    return dict(zip(DIAG_KEYS, out.tolist()))
