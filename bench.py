@@ -301,7 +301,7 @@ def run_ours(args):
         "config": {"workload": args.workload, "description": desc, "cells": ncell, "fluid_cells": fluid,
                    "precision": precision, "l2": "flushed before every timed step (256 MiB write)",
                    "state_bytes_per_buffer": nbytes, "parallelism": f"replicas x{world}",
-                   "kernel_variant": s.variant,
+                   "kernel_variant": s.variant, "launches_per_step": s.launches_per_step,
                    "autotune_ms_per_variant": [round(float(t), 4) for t in tune_ms]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
@@ -309,7 +309,7 @@ def run_ours(args):
                      "mean_launch_ms": mean_s * 1e3},
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                 "steps": e2e_steps, "api": "lbfd_set_state_raw + lbfd_step + lbfd_get_state_raw (pinned)"},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * s.launches_per_step,
         "clocks": clocks,
         "wall_ms_per_step_with_flush": 1e3 * t_wall / args.steps,
         "diagnostics_after": {k: diag[k] for k in ("x_f", "T_max", "n_nonfinite")},

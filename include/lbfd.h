@@ -175,11 +175,16 @@ int lbfd_step_graph(lbfd_handle* h, int n);
 
 /* Kernel variants of the step: 0 is the general form (any cell, D2Q9 and
  * D3Q27); in 2-D, 1..4 are shared-memory tiles of 32x8, 32x4, 64x4 and
- * 32x16 cells with a fast path for interior cells.  All variants compute
+ * 32x16 interior cells, followed by the general form over the list of
+ * boundary cells (computed at create).  All variants compute
  * the same step up to rounding order.  Default: 1 in 2-D, 0 in 3-D. */
 int lbfd_num_variants(const lbfd_handle* h);
 int lbfd_get_variant(const lbfd_handle* h);
 int lbfd_set_variant(lbfd_handle* h, int variant);
+/* Kernel launches one step makes with the current variant: the tile
+ * variants launch the tile kernel and, when the grid has boundary cells,
+ * a second kernel over the list of those cells. */
+int lbfd_launches_per_step(const lbfd_handle* h);
 
 /* Autotuner: time every variant over `reps` launches on the current state
  * (the output buffer is overwritten, the state does not advance), select

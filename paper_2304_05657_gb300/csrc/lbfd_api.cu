@@ -32,6 +32,8 @@ struct lbfd_handle {
     void* buf[2];         // device state buffers
     int cur;
     uint8_t* solid;       // device mask
+    long long* bnd;       // device list of the cells the 2-D tile kernels skip
+    long long nbnd;
     double* red;          // device reduction scratch
     double* tmp;          // device read-out buffer (ncell doubles)
     cudaStream_t stream;
@@ -174,6 +176,7 @@ void free_handle(lbfd_handle* h)
     if (h->solid) cudaFree(h->solid);
     if (h->red) cudaFree(h->red);
     if (h->tmp) cudaFree(h->tmp);
+    if (h->bnd) cudaFree(h->bnd);
     delete h;
 }
 
@@ -279,6 +282,23 @@ int lbfd_create(const lbfd_grid* grid, const uint8_t* solid_mask, const lbfd_mec
         free_handle(h);
         return cuda_fail(e, "cudaMemcpy(mask)");
     }
+    {
+        std::vector<long long> list;
+        lbfd::boundary_cells(h->dim, h->grid.nx, h->grid.ny, h->grid.nz, m.data(), list);
+        h->nbnd = (long long)list.size();
+        if (h->nbnd > 0) {
+            if ((e = cudaMalloc(&h->bnd, list.size() * sizeof(long long))) != cudaSuccess) {
+                free_handle(h);
+                cuda_fail(e, "cudaMalloc(boundary list)");
+                return LBFD_ENOMEM;
+            }
+            if ((e = cudaMemcpy(h->bnd, list.data(), list.size() * sizeof(long long), cudaMemcpyHostToDevice)) !=
+                cudaSuccess) {
+                free_handle(h);
+                return cuda_fail(e, "cudaMemcpy(boundary list)");
+            }
+        }
+    }
     // initial state: T_in, Y_in, g = 0
     h->cur = 0;
     if ((e = cudaMemset(h->buf[0], 0, bytes)) != cudaSuccess) {
@@ -338,7 +358,8 @@ int lbfd_step(lbfd_handle* h, int n)
     if (!h || n < 0) return LBFD_EINVAL;
     for (int it = 0; it < n; ++it) {
         cudaError_t e = lbfd::launch_step(h->dim, h->precision, h->variant, h->Pd, h->Pf, view(h, h->cur),
-                                          view(h, h->cur ^ 1), h->solid, h->stream);
+                                          view(h, h->cur ^ 1), h->solid, h->bnd, h->nbnd,
+                                          h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
         h->cur ^= 1;
         h->steps++;
@@ -367,7 +388,7 @@ int lbfd_step_graph(lbfd_handle* h, int n)
         cudaError_t le = cudaSuccess;
         for (int it = 0; it < n && le == cudaSuccess; ++it) {
             le = lbfd::launch_step(h->dim, h->precision, h->variant, h->Pd, h->Pf, view(h, cur), view(h, cur ^ 1),
-                                   h->solid, s);
+                                   h->solid, h->bnd, h->nbnd, s);
             cur ^= 1;
         }
         cudaError_t ee = cudaStreamEndCapture(s, &g);
@@ -398,6 +419,12 @@ int lbfd_num_variants(const lbfd_handle* h) { return h ? lbfd::num_variants(h->d
 
 int lbfd_get_variant(const lbfd_handle* h) { return h ? h->variant : -1; }
 
+int lbfd_launches_per_step(const lbfd_handle* h)
+{
+    if (!h) return -1;
+    return (h->variant > 0 && h->dim == 2 && h->nbnd > 0) ? 2 : 1;
+}
+
 int lbfd_set_variant(lbfd_handle* h, int variant)
 {
     if (!h || variant < 0 || variant >= lbfd::num_variants(h->dim)) return LBFD_EINVAL;
@@ -419,11 +446,11 @@ int lbfd_autotune(lbfd_handle* h, int reps, double* ms_per_variant, int* best)
         cudaError_t e = cudaSuccess;
         for (int r = 0; r < 2 && e == cudaSuccess; ++r)
             e = lbfd::launch_step(h->dim, h->precision, v, h->Pd, h->Pf, view(h, h->cur), view(h, h->cur ^ 1),
-                                  h->solid, h->stream);
+                                  h->solid, h->bnd, h->nbnd, h->stream);
         cudaEventRecord(e0, h->stream);
         for (int r = 0; r < reps && e == cudaSuccess; ++r)
             e = lbfd::launch_step(h->dim, h->precision, v, h->Pd, h->Pf, view(h, h->cur), view(h, h->cur ^ 1),
-                                  h->solid, h->stream);
+                                  h->solid, h->bnd, h->nbnd, h->stream);
         cudaEventRecord(e1, h->stream);
         cudaError_t se = cudaEventSynchronize(e1);
         if (e != cudaSuccess || se != cudaSuccess) {

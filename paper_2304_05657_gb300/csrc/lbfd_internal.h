@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 
 #include "lbfd_params.h"
 
@@ -20,10 +21,15 @@ struct StateView {
 // Launch one fused coupled step: state `in` -> state `out`.
 // precision: 0 = FP64 (S = R = double), 1 = mixed (S = R = float).
 // variant: 0 = general form, 1.. = 2-D shared-memory tiles (see lbfd_step.cu)
+// bnd/nbnd: the fluid cells the 2-D tile kernels leave to the boundary
+// kernel (see boundary_cells); unused by the general variant.
 cudaError_t launch_step(int dim, int precision, int variant, const StepParams<double>& Pd,
                         const StepParams<float>& Pf, StateView in, StateView out, const uint8_t* solid,
-                        cudaStream_t stream);
+                        const long long* bnd, long long nbnd, cudaStream_t stream);
 int num_variants(int dim);
+
+// Fluid cells that are not interior for the 2-D tile kernels (host, at create).
+void boundary_cells(int dim, int nx, int ny, int nz, const uint8_t* solid, std::vector<long long>& out);
 
 // Diagnostics reduction into the device scratch `red` (LBFD_NDIAG + extra
 // words, zeroed by the launcher); FP64 accumulation.

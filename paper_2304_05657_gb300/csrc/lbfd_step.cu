@@ -5,6 +5,8 @@
 // shared-memory tiles of different shapes (lbfd_step_tiled.cuh); the
 // autotuner picks among them by timing.  All variants compute the same
 // step; they differ only in rounding order.
+#include <vector>
+
 #include "lbfd_internal.h"
 #include "lbfd_step_tiled.cuh"
 
@@ -40,7 +42,7 @@ static cudaError_t launch_general(const StepParams<R>& P, StateView in, StateVie
 
 template <typename S, typename R, int TX, int TY>
 static cudaError_t launch_tiled(const StepParams<R>& P, StateView in, StateView out, const uint8_t* solid,
-                                cudaStream_t stream)
+                                const long long* bnd, long long nbnd, cudaStream_t stream)
 {
     constexpr size_t smem = tile_smem_bytes<R, TX, TY>();
     auto kern = step_kernel_tiled2d<S, R, TX, TY>;
@@ -51,19 +53,25 @@ static cudaError_t launch_tiled(const StepParams<R>& P, StateView in, StateView 
     dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
     kern<<<grid, dim3(TX, TY), smem, stream>>>(P, (const S*)in.g, (S*)out.g, (const S*)in.T, (S*)out.T,
                                                (const S*)in.Y, (S*)out.Y, solid);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || nbnd == 0) return e;
+    // the cells the tile kernel skipped (disjoint writes, same input state)
+    const unsigned nb = (unsigned)((nbnd + 127) / 128);
+    step_kernel_boundary<2, S, R><<<nb, 128, 0, stream>>>(P, (const S*)in.g, (S*)out.g, (const S*)in.T,
+                                                          (S*)out.T, (const S*)in.Y, (S*)out.Y, solid, bnd, nbnd);
     return cudaGetLastError();
 }
 
 template <typename S, typename R>
 static cudaError_t launch_2d(int variant, const StepParams<R>& P, StateView in, StateView out, const uint8_t* solid,
-                             cudaStream_t stream)
+                             const long long* bnd, long long nbnd, cudaStream_t stream)
 {
     switch (variant) {
     case 0: return launch_general<2, S, R>(P, in, out, solid, stream);
-    case 1: return launch_tiled<S, R, 32, 8>(P, in, out, solid, stream);
-    case 2: return launch_tiled<S, R, 32, 4>(P, in, out, solid, stream);
-    case 3: return launch_tiled<S, R, 64, 4>(P, in, out, solid, stream);
-    case 4: return launch_tiled<S, R, 32, 16>(P, in, out, solid, stream);
+    case 1: return launch_tiled<S, R, 32, 8>(P, in, out, solid, bnd, nbnd, stream);
+    case 2: return launch_tiled<S, R, 32, 4>(P, in, out, solid, bnd, nbnd, stream);
+    case 3: return launch_tiled<S, R, 64, 4>(P, in, out, solid, bnd, nbnd, stream);
+    case 4: return launch_tiled<S, R, 32, 16>(P, in, out, solid, bnd, nbnd, stream);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -72,15 +80,40 @@ int num_variants(int dim) { return dim == 2 ? 5 : 1; }
 
 cudaError_t launch_step(int dim, int precision, int variant, const StepParams<double>& Pd,
                         const StepParams<float>& Pf, StateView in, StateView out, const uint8_t* solid,
-                        cudaStream_t stream)
+                        const long long* bnd, long long nbnd, cudaStream_t stream)
 {
     if (variant < 0 || variant >= num_variants(dim)) return cudaErrorInvalidValue;
     if (precision == 0) {
-        if (dim == 2) return launch_2d<double, double>(variant, Pd, in, out, solid, stream);
+        if (dim == 2) return launch_2d<double, double>(variant, Pd, in, out, solid, bnd, nbnd, stream);
         return launch_general<3, double, double>(Pd, in, out, solid, stream);
     }
-    if (dim == 2) return launch_2d<float, float>(variant, Pf, in, out, solid, stream);
+    if (dim == 2) return launch_2d<float, float>(variant, Pf, in, out, solid, bnd, nbnd, stream);
     return launch_general<3, float, float>(Pf, in, out, solid, stream);
+}
+
+void boundary_cells(int dim, int nx, int ny, int nz, const uint8_t* solid, std::vector<long long>& out)
+{
+    out.clear();
+    if (dim != 2) return;  // only the 2-D tiles use the list
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            const long long c = (long long)x + (long long)nx * y;
+            if (solid[c]) continue;
+            bool fast = true;
+            // the tile kernel's fast-path condition: +-2 along both axes and
+            // the 8 neighbours are fluid cells inside the domain
+            for (int dy = -2; dy <= 2 && fast; ++dy)
+                for (int dx = -2; dx <= 2 && fast; ++dx) {
+                    const bool axis = (dx == 0 || dy == 0);
+                    const bool near = (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1);
+                    if (!(axis || near)) continue;
+                    const int qx = x + dx, qy = y + dy;
+                    if (qx < 0 || qx >= nx || qy < 0 || qy >= ny) fast = false;
+                    else if (solid[(long long)qx + (long long)nx * qy]) fast = false;
+                }
+            if (!fast) out.push_back(c);
+        }
+    (void)nz;
 }
 
 }  // namespace lbfd

@@ -7,7 +7,8 @@
 // cells inside the domain take the fast path: FD stencils from shared
 // memory, populations pulled straight from global memory (coalesced, one
 // plane at a time).  Every other cell (walls, solids, inlet, outlet,
-// periodic wrap) takes the general path of lbfd_step_general.cuh.
+// periodic wrap) is left to step_kernel_boundary, which runs the general
+// form of lbfd_step_general.cuh over a precomputed list of those cells.
 #pragma once
 #include "lbfd_step_general.cuh"
 
@@ -48,10 +49,10 @@ __device__ __forceinline__ void fd_axis_smem(const StepParams<R>& P, const TileS
     for (int j = 0; j < 5; ++j) v[j] = sm.rho[p0 + (j - 2) * st];
     const R drho = fd_d1(v);
     acc.grad_rho[a] = drho;
-    const R drho_r = drho / rho0;
+    const R drho_r = fdiv(drho, rho0);
 #pragma unroll
     for (int j = 0; j < 5; ++j) v[j] = sm.T[p0 + (j - 2) * st];
-    acc.conv_T += u_a * weno3_deriv(v, u_a, P.epsT);
+    acc.conv_T += u_a * weno3_deriv_fast(v, u_a, P.epsT);
     acc.diff_T += P.alpha * (fd_d2(v) + drho_r * fd_d1(v));
 #pragma unroll
     for (int j = 0; j < 5; ++j) w[j] = sm.invW[p0 + (j - 2) * st];
@@ -62,7 +63,7 @@ __device__ __forceinline__ void fd_axis_smem(const StepParams<R>& P, const TileS
     for (int k = 0; k < NSP; ++k) {
 #pragma unroll
         for (int j = 0; j < 5; ++j) v[j] = sm.Y[k * npt + p0 + (j - 2) * st];
-        Lk[k] = weno3_deriv(v, u_a, P.epsY);
+        Lk[k] = weno3_deriv_fast(v, u_a, P.epsY);
         sumL += Lk[k];
         dY[k] = fd_d1(v);
 #pragma unroll
@@ -119,7 +120,7 @@ __global__ void __launch_bounds__(TX * TY) step_kernel_tiled2d(StepParams<R> P, 
 #pragma unroll
         for (int k = 0; k < NSP; ++k) Y[k] = R(Y_in[(long long)k * N + c]);
         const R invW = inv_molar_mass(P, Y);
-        const R W = R(1) / invW;
+        const R W = fdiv(R(1), invW);
         sm.T[pt] = T;
 #pragma unroll
         for (int k = 0; k < NSP; ++k) {
@@ -127,7 +128,7 @@ __global__ void __launch_bounds__(TX * TY) step_kernel_tiled2d(StepParams<R> P, 
             sm.X[k * NPT + pt] = Y[k] * P.inv_Wk[k] * W;
         }
         sm.invW[pt] = invW;
-        sm.rho[pt] = P.T_in * P.invW_in * W / T;
+        sm.rho[pt] = fdiv(P.T_in * P.invW_in * W, T);
     }
     __syncthreads();
 
@@ -142,11 +143,7 @@ __global__ void __launch_bounds__(TX * TY) step_kernel_tiled2d(StepParams<R> P, 
     for (int j = 1; j <= 2; ++j)
         fast = fast && !sm.mask[p0 + j] && !sm.mask[p0 - j] && !sm.mask[p0 + j * SX] && !sm.mask[p0 - j * SX];
     fast = fast && !sm.mask[p0 + SX + 1] && !sm.mask[p0 + SX - 1] && !sm.mask[p0 - SX + 1] && !sm.mask[p0 - SX - 1];
-    if (!fast) {
-        const int p[3] = {x, y, 0};
-        cell_step_general<2, S, R>(P, p, c, g_in, g_out, T_in, T_out, Y_in, Y_out, solid);
-        return;
-    }
+    if (!fast) return;  // boundary cell: step_kernel_boundary updates it
     // a1: pull from the neighbours (all interior)
     R g[9];
 #pragma unroll
@@ -161,7 +158,7 @@ __global__ void __launch_bounds__(TX * TY) step_kernel_tiled2d(StepParams<R> P, 
     for (int k = 0; k < NSP; ++k) Y0[k] = sm.Y[k * NPT + p0];
     R u[3];
     {
-        const R inv = R(3) / rho0;
+        const R inv = fdiv(R(3), rho0);
         u[0] = ((g[2] + g[5] + g[8]) - (g[0] + g[3] + g[6])) * inv;
         u[1] = ((g[6] + g[7] + g[8]) - (g[0] + g[1] + g[2])) * inv;
         u[2] = R(0);
@@ -187,11 +184,30 @@ __global__ void __launch_bounds__(TX * TY) step_kernel_tiled2d(StepParams<R> P, 
         Y_out[(long long)k * N + c] = S(Y0[k] + (DY - acc.conv_Y[k]));
         lam_Y += P.inv_Wk[k] * DY;
     }
-    const R Lam = DT / T0 + lam_Y / invW0;
+    const R Lam = fdiv(DT, T0) + fdiv(lam_Y, invW0);
     // a8-a10
     collide<2, R>(P, g, rho0, u, acc.grad_rho, Lam);
 #pragma unroll
     for (int i = 0; i < 9; ++i) g_out[(long long)i * N + c] = S(g[i]);
+}
+
+// The cells the tiled kernel leaves out: general form over a cell list.
+template <int DIM, typename S, typename R>
+__global__ void __launch_bounds__(128) step_kernel_boundary(StepParams<R> P, const S* __restrict__ g_in,
+                                                            S* __restrict__ g_out, const S* __restrict__ T_in,
+                                                            S* __restrict__ T_out, const S* __restrict__ Y_in,
+                                                            S* __restrict__ Y_out, const uint8_t* __restrict__ solid,
+                                                            const long long* __restrict__ cells, long long ncells)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ncells) return;
+    const long long c = cells[t];
+    int p[3];
+    p[0] = (int)(c % P.nx);
+    const long long r = c / P.nx;
+    p[1] = (int)(r % P.ny);
+    p[2] = (int)(r / P.ny);
+    cell_step_general<DIM, S, R>(P, p, c, g_in, g_out, T_in, T_out, Y_in, Y_out, solid);
 }
 
 }  // namespace lbfd

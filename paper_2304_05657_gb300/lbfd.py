@@ -31,7 +31,7 @@ SYMBOLS = (
     "lbfd_read_field", "lbfd_diagnostics", "lbfd_flame_position", "lbfd_state_bytes", "lbfd_get_state_raw",
     "lbfd_set_state_raw", "lbfd_steps_done", "lbfd_num_cells", "lbfd_num_populations", "lbfd_strerror",
     "lbfd_last_error", "lbfd_step_graph", "lbfd_num_variants", "lbfd_get_variant", "lbfd_set_variant",
-    "lbfd_autotune", "lbfd_diagnostics_noalloc",
+    "lbfd_autotune", "lbfd_diagnostics_noalloc", "lbfd_launches_per_step",
 )
 
 
@@ -104,6 +104,7 @@ def load(path: str = LIB_PATH):
     lib.lbfd_num_variants.argtypes = [H]
     lib.lbfd_get_variant.argtypes = [H]
     lib.lbfd_set_variant.argtypes = [H, ctypes.c_int]
+    lib.lbfd_launches_per_step.argtypes = [H]
     lib.lbfd_autotune.argtypes = [H, ctypes.c_int, D, ctypes.POINTER(ctypes.c_int)]
     lib.lbfd_diagnostics_noalloc.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Mechanism), ctypes.POINTER(Params),
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong,
@@ -216,6 +217,10 @@ class Solver:
     @variant.setter
     def variant(self, v: int):
         _check(self.lib, self.lib.lbfd_set_variant(self.h, int(v)), "lbfd_set_variant")
+
+    @property
+    def launches_per_step(self) -> int:
+        return int(self.lib.lbfd_launches_per_step(self.h))
 
     def autotune(self, reps: int = 20):
         """Time every kernel variant on the current state and keep the
