@@ -202,6 +202,40 @@ def cpu_baseline(args, precision):
             "gpu_rel_l2_vs_oracle": {"T": err_T, "Y_max": err_Y, "steps": steps}}
 
 
+def gradient_rate(args):
+    """Gradient steps per second of flame position w.r.t. (ln A, Ta, T_wall,
+    u_in) on the 512x64 cold-wall channel (tangent precision), next to plain
+    FP64 steps per second on the same case; CUDA events on the handle's
+    stream."""
+    import torch
+
+    from paper_2304_05657_gb300 import lbfd
+
+    cfg, solid, T, Y = inputs.channel(nx=512, ny=64, walls="isothermal", T_wall=300.0)
+    out = {"workload": "D2Q9 channel 512x64, isothermal 300 K walls, objective: flame position",
+           "mode": "tangent-linear (forward), 4 directions, FP64", "steps": args.grad_steps}
+    stream = torch.cuda.current_stream()
+    for prec in ("tangent", "fp64"):
+        s = lbfd.Solver(dict(cfg, precision=prec), solid, stream=stream)
+        s.init_fields(T, Y)
+        if prec == "fp64":
+            s.autotune(reps=5)
+        s.step(5)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(args.grad_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rate = args.grad_steps / (e0.elapsed_time(e1) * 1e-3)
+        out["grad_steps_per_s" if prec == "tangent" else "fp64_steps_per_s"] = rate
+        if prec == "tangent":
+            J, g = s.gradient(lbfd.OBJ_FLAME_POSITION)
+            out["dJ_dtheta"] = dict(zip(lbfd.THETA, [float(x) for x in g]))
+        s.close()
+    out["grad_vs_fp64_step_time"] = out["fp64_steps_per_s"] / out["grad_steps_per_s"]
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -316,6 +350,8 @@ def run_ours(args):
     }
     if rank == 0 and world == 1 and not args.no_baseline:
         line["cpu_baseline"] = cpu_baseline(args, precision)
+    if rank == 0 and world == 1 and args.grad_steps > 0:
+        line["gradient"] = gradient_rate(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
     s.close()
@@ -335,6 +371,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--baseline-steps", type=int, default=40)
     ap.add_argument("--no-baseline", action="store_true")
+    ap.add_argument("--grad-steps", type=int, default=200, help="gradient-rate steps (0: skip)")
     ap.add_argument("--variant", type=int, default=None, help="kernel variant (default: autotune)")
     args = ap.parse_args()
     if args.warmup < 3:

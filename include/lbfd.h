@@ -61,6 +61,14 @@ extern "C" {
 /* arithmetic of the step */
 #define LBFD_FP64 0  /* FP64 storage and arithmetic */
 #define LBFD_MIXED 1 /* FP32 storage and arithmetic; FP64 Arrhenius above T_fp64 */
+#define LBFD_TANGENT 2 /* FP64 values each carrying 4 derivatives (forward mode),
+                          with respect to theta = (ln A, Ta, T_wall, u_in); 2-D only,
+                          general-form kernel.  T_wall moves every isothermal wall face
+                          and, when solids are isothermal, T_solid together. */
+
+/* objectives of lbfd_gradient */
+#define LBFD_OBJ_FLAME_POSITION 0 /* x_f [m] as in lbfd_flame_position */
+#define LBFD_OBJ_HEAT_RELEASE 1   /* sum of LBFD_FIELD_HRR over fluid cells */
 
 /* number of species the kernels are built for */
 #define LBFD_NSP 5
@@ -201,11 +209,34 @@ int lbfd_read_field(lbfd_handle* h, int field, double* out);
  * when a fluid cell holds a non-finite value. */
 int lbfd_diagnostics(lbfd_handle* h, double* out);
 
+/* lbfd_diagnostics restricted to the rows y0 <= y < y1 (all x and z), e.g.
+ * one channel of a batch packed along y; x_f is normalised by the fluid
+ * cells of that part of the x = 0 section and LBFD_DIAG_XHRR uses the line
+ * y = (y0 + y1)/2.  EINVAL unless 0 <= y0 < y1 <= ny. */
+int lbfd_diagnostics_rows(lbfd_handle* h, int y0, int y1, double* out);
+
+/* Change the inlet velocity of subsequent steps (the flow rate control that
+ * holds a flame in place, Sec. IV.A).  EUNSTABLE if |u_in| >= cs.  A
+ * captured step graph is re-captured at its next use. */
+int lbfd_set_inlet_velocity(lbfd_handle* h, double u_in);
+
 /* Flame position x_f [m] (LBFD_DIAG_XF times dx), fluid mass sum rho and
  * total heat release (LBFD_DIAG_HRR).  Any pointer may be NULL. */
 int lbfd_flame_position(lbfd_handle* h, double* x_f, double* mass, double* heat_release);
 
-/* Raw state in storage precision (4 or 8 bytes per value):
+/* Tangent precision only: derivative k (0..3, order of theta) of a raw
+ * field (LBFD_FIELD_T, LBFD_FIELD_Y0 + k, LBFD_FIELD_G0 + i) of all cells
+ * into host out[N].  The state set by lbfd_init_fields/lbfd_set_state has
+ * zero derivatives; every step propagates them exactly (the derivative of
+ * the discrete step; branch decisions are taken on the values).
+ * Synchronises. */
+int lbfd_read_tangent(lbfd_handle* h, int field, int k, double* out);
+
+/* Tangent precision only: objective J (LBFD_OBJ_*) of the current state and
+ * its gradient dJ/dtheta[4].  Either pointer may be NULL.  Synchronises. */
+int lbfd_gradient(lbfd_handle* h, int objective, double* value, double* grad);
+
+/* Raw state in storage precision (4 or 8 bytes per value; 40 for tangent):
  * layout g[Q][N], T[N], Y[nsp][N], contiguous; lbfd_state_bytes gives the size.
  * The host buffer may be pageable or pinned; the copy is ordered on the
  * handle's stream and the call synchronises it. */

@@ -624,6 +624,17 @@ static double pull(const orc_sim *S, int i, const int p[3], long cidx)
     const double *g = S->g;
     long N = S->N;
     int ib = S->opp[i];
+    if (!wall && (inlet >= 0 || outlet >= 0)) {
+        /* a link that leaves through an inlet or outlet face where the
+         * boundary column is solid hits the solid: bounce-back, as when it
+         * also crosses a wall face */
+        int q[3] = {src[0], src[1], src[2]};
+        for (int a = 0; a < S->s.dim; ++a) {
+            if (q[a] < 0) q[a] = 0;
+            else if (q[a] >= extent(S, a)) q[a] = extent(S, a) - 1;
+        }
+        if (S->solid[cell_index(S, q)]) wall = 1;
+    }
     if (wall) return g[(long)ib * N + cidx];                              /* Eq. 28 */
     if (inlet >= 0) {                                                     /* Eq. 31 */
         double uin[3];

@@ -20,6 +20,7 @@
 
 using lbfd::StateView;
 using lbfd::StepParams;
+using lbfd::Tan;
 
 struct lbfd_handle {
     lbfd_grid grid;
@@ -41,11 +42,14 @@ struct lbfd_handle {
     int variant;          // kernel variant (lbfd::launch_step)
     StepParams<double> Pd;
     StepParams<float> Pf;
+    StepParams<lbfd::Tan> Pt;  // tangent precision: parameters with their seeds
+    double section;            // fluid cells of the x = 0 section
     // CUDA graph of `graph_n` steps starting from buffer `graph_parity`
     cudaGraphExec_t graph;
     int graph_n, graph_parity, graph_variant;
     cudaStream_t graph_stream;  // stream the graph was captured on
     cudaStream_t own_stream;    // created when capture needs a non-legacy stream
+    lbfd::SideStream side;      // boundary kernel next to the tile kernel
 };
 
 namespace {
@@ -128,6 +132,17 @@ void fill_params(const lbfd_handle* h, StepParams<R>& P)
     P.cs = (R)sqrt(cs2);
 }
 
+// derivative directions of the tangent precision: (ln A, Ta, T_wall, u_in)
+void seed_tangents(const lbfd_handle* h, StepParams<Tan>& P)
+{
+    P.A_lat.d[0] = P.A_lat.v;  // d(A dt)/d(ln A)
+    P.Ta.d[1] = 1.0;
+    for (int f = 0; f < 6; ++f)
+        if (P.bc[f] == LBFD_BC_WALL_ISOTHERMAL) P.T_wall[f].d[2] = 1.0;
+    if (h->prm.solid_isothermal) P.T_solid.d[2] = 1.0;
+    P.u_in.d[3] = 1.0;
+}
+
 int validate(const lbfd_grid* G, const lbfd_mechanism* M, const lbfd_params* p)
 {
     if (G->dim != 2 && G->dim != 3) return LBFD_EINVAL;
@@ -148,7 +163,8 @@ int validate(const lbfd_grid* G, const lbfd_mechanism* M, const lbfd_params* p)
         if (!(M->W[k] > 0.0) || !(M->Le[k] > 0.0)) return LBFD_EINVAL;
     if (!(M->A >= 0.0) || !(M->Ta >= 0.0) || !(M->cp > 0.0) || !std::isfinite(M->Q)) return LBFD_EINVAL;
     if (!(p->T_in > 0.0) || !(p->dt > 0.0) || !(p->Pr > 0.0) || !(p->weno_eps > 0.0)) return LBFD_EINVAL;
-    if (p->precision != LBFD_FP64 && p->precision != LBFD_MIXED) return LBFD_EINVAL;
+    if (p->precision != LBFD_FP64 && p->precision != LBFD_MIXED && p->precision != LBFD_TANGENT) return LBFD_EINVAL;
+    if (p->precision == LBFD_TANGENT && G->dim != 2) return LBFD_ENOTSUP;
     double ysum = 0.0;
     for (int k = 0; k < lbfd::NSP; ++k) ysum += p->Y_in[k];
     if (fabs(ysum - 1.0) > 1e-6) return LBFD_EINVAL;
@@ -171,6 +187,9 @@ void free_handle(lbfd_handle* h)
     if (!h) return;
     if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    if (h->side.stream) cudaStreamDestroy(h->side.stream);
+    if (h->side.fork) cudaEventDestroy(h->side.fork);
+    if (h->side.join) cudaEventDestroy(h->side.join);
     for (int b = 0; b < 2; ++b)
         if (h->buf[b]) cudaFree(h->buf[b]);
     if (h->solid) cudaFree(h->solid);
@@ -187,9 +206,12 @@ int upload_planes(lbfd_handle* h, int which, int first_plane, int nplanes, const
     std::vector<char> stage(n * h->esz * nplanes);
     if (h->precision == LBFD_FP64) {
         memcpy(stage.data(), src, n * sizeof(double) * nplanes);
-    } else {
+    } else if (h->precision == LBFD_MIXED) {
         float* d = (float*)stage.data();
         for (size_t i = 0; i < n * nplanes; ++i) d[i] = (float)src[i];
+    } else {  // tangent: the given state carries no derivative
+        Tan* d = (Tan*)stage.data();
+        for (size_t i = 0; i < n * nplanes; ++i) d[i] = Tan(src[i]);
     }
     char* dst = (char*)h->buf[which] + (size_t)first_plane * h->stride * h->esz;
     CK(cudaMemcpy2DAsync(dst, (size_t)h->stride * h->esz, stage.data(), n * h->esz, n * h->esz, nplanes,
@@ -204,6 +226,20 @@ int sync_other_buffer(lbfd_handle* h)
     CK(cudaMemcpyAsync(h->buf[h->cur ^ 1], h->buf[h->cur], bytes, cudaMemcpyDeviceToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return LBFD_OK;
+}
+
+// one step from buffer `from` to buffer `from ^ 1` with kernel variant v
+cudaError_t launch_one(lbfd_handle* h, int from, int v, cudaStream_t s)
+{
+    if (h->precision == LBFD_TANGENT)
+        return lbfd::launch_step_tangent(h->dim, h->Pt, view(h, from), view(h, from ^ 1), h->solid, s);
+    return lbfd::launch_step(h->dim, h->precision, v, h->Pd, h->Pf, view(h, from), view(h, from ^ 1), h->solid,
+                             h->bnd, h->nbnd, h->side, s);
+}
+
+int num_variants_of(const lbfd_handle* h)
+{
+    return h->precision == LBFD_TANGENT ? 1 : lbfd::num_variants(h->dim);
 }
 
 }  // namespace
@@ -252,10 +288,10 @@ int lbfd_create(const lbfd_grid* grid, const uint8_t* solid_mask, const lbfd_mec
     h->precision = params->precision;
     h->ncell = (long long)h->grid.nx * h->grid.ny * h->grid.nz;
     h->stride = (h->ncell + 63) / 64 * 64;  // 256-byte aligned FP32 planes
-    h->esz = h->precision == LBFD_FP64 ? 8 : 4;
+    h->esz = h->precision == LBFD_FP64 ? 8 : (h->precision == LBFD_MIXED ? 4 : sizeof(Tan));
     h->planes = (size_t)h->Q + 1 + lbfd::NSP;
     h->stream = nullptr;
-    h->variant = h->dim == 2 ? 1 : 0;
+    h->variant = (h->dim == 2 && h->precision != LBFD_TANGENT) ? 1 : 0;
     const size_t bytes = h->planes * (size_t)h->stride * h->esz;
     for (int b = 0; b < 2; ++b) {
         e = cudaMalloc(&h->buf[b], bytes);
@@ -274,6 +310,8 @@ int lbfd_create(const lbfd_grid* grid, const uint8_t* solid_mask, const lbfd_mec
     }
     fill_params(h, h->Pd);
     fill_params(h, h->Pf);
+    fill_params(h, h->Pt);
+    seed_tangents(h, h->Pt);
     // mask
     std::vector<uint8_t> m((size_t)h->ncell, 0);
     if (solid_mask)
@@ -282,6 +320,16 @@ int lbfd_create(const lbfd_grid* grid, const uint8_t* solid_mask, const lbfd_mec
         free_handle(h);
         return cuda_fail(e, "cudaMemcpy(mask)");
     }
+    if (h->dim == 2 &&
+        ((e = cudaStreamCreateWithFlags(&h->side.stream, cudaStreamNonBlocking)) != cudaSuccess ||
+         (e = cudaEventCreateWithFlags(&h->side.fork, cudaEventDisableTiming)) != cudaSuccess ||
+         (e = cudaEventCreateWithFlags(&h->side.join, cudaEventDisableTiming)) != cudaSuccess)) {
+        free_handle(h);
+        return cuda_fail(e, "side stream");
+    }
+    h->section = 0.0;
+    for (long long c = 0; c < h->ncell; c += h->grid.nx)
+        if (!m[c]) h->section += 1.0;
     {
         std::vector<long long> list;
         lbfd::boundary_cells(h->dim, h->grid.nx, h->grid.ny, h->grid.nz, m.data(), list);
@@ -357,9 +405,7 @@ int lbfd_step(lbfd_handle* h, int n)
 {
     if (!h || n < 0) return LBFD_EINVAL;
     for (int it = 0; it < n; ++it) {
-        cudaError_t e = lbfd::launch_step(h->dim, h->precision, h->variant, h->Pd, h->Pf, view(h, h->cur),
-                                          view(h, h->cur ^ 1), h->solid, h->bnd, h->nbnd,
-                                          h->stream);
+        cudaError_t e = launch_one(h, h->cur, h->variant, h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
         h->cur ^= 1;
         h->steps++;
@@ -387,8 +433,7 @@ int lbfd_step_graph(lbfd_handle* h, int n)
         int cur = h->cur;
         cudaError_t le = cudaSuccess;
         for (int it = 0; it < n && le == cudaSuccess; ++it) {
-            le = lbfd::launch_step(h->dim, h->precision, h->variant, h->Pd, h->Pf, view(h, cur), view(h, cur ^ 1),
-                                   h->solid, h->bnd, h->nbnd, s);
+            le = launch_one(h, cur, h->variant, s);
             cur ^= 1;
         }
         cudaError_t ee = cudaStreamEndCapture(s, &g);
@@ -415,19 +460,19 @@ int lbfd_step_graph(lbfd_handle* h, int n)
     return LBFD_OK;
 }
 
-int lbfd_num_variants(const lbfd_handle* h) { return h ? lbfd::num_variants(h->dim) : -1; }
+int lbfd_num_variants(const lbfd_handle* h) { return h ? num_variants_of(h) : -1; }
 
 int lbfd_get_variant(const lbfd_handle* h) { return h ? h->variant : -1; }
 
 int lbfd_launches_per_step(const lbfd_handle* h)
 {
     if (!h) return -1;
-    return (h->variant > 0 && h->dim == 2 && h->nbnd > 0) ? 2 : 1;
+    return (h->variant > 0 && h->dim == 2 && h->nbnd > 0 && h->precision != LBFD_TANGENT) ? 2 : 1;
 }
 
 int lbfd_set_variant(lbfd_handle* h, int variant)
 {
-    if (!h || variant < 0 || variant >= lbfd::num_variants(h->dim)) return LBFD_EINVAL;
+    if (!h || variant < 0 || variant >= num_variants_of(h)) return LBFD_EINVAL;
     h->variant = variant;
     return LBFD_OK;
 }
@@ -435,7 +480,7 @@ int lbfd_set_variant(lbfd_handle* h, int variant)
 int lbfd_autotune(lbfd_handle* h, int reps, double* ms_per_variant, int* best)
 {
     if (!h || reps < 1) return LBFD_EINVAL;
-    const int nv = lbfd::num_variants(h->dim);
+    const int nv = num_variants_of(h);
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -445,12 +490,10 @@ int lbfd_autotune(lbfd_handle* h, int reps, double* ms_per_variant, int* best)
         // the input buffer is never written: the state does not advance
         cudaError_t e = cudaSuccess;
         for (int r = 0; r < 2 && e == cudaSuccess; ++r)
-            e = lbfd::launch_step(h->dim, h->precision, v, h->Pd, h->Pf, view(h, h->cur), view(h, h->cur ^ 1),
-                                  h->solid, h->bnd, h->nbnd, h->stream);
+            e = launch_one(h, h->cur, v, h->stream);
         cudaEventRecord(e0, h->stream);
         for (int r = 0; r < reps && e == cudaSuccess; ++r)
-            e = lbfd::launch_step(h->dim, h->precision, v, h->Pd, h->Pf, view(h, h->cur), view(h, h->cur ^ 1),
-                                  h->solid, h->bnd, h->nbnd, h->stream);
+            e = launch_one(h, h->cur, v, h->stream);
         cudaEventRecord(e1, h->stream);
         cudaError_t se = cudaEventSynchronize(e1);
         if (e != cudaSuccess || se != cudaSuccess) {
@@ -487,11 +530,11 @@ int lbfd_read_field(lbfd_handle* h, int field, double* out)
     return LBFD_OK;
 }
 
-int lbfd_diagnostics(lbfd_handle* h, double* out)
+int lbfd_diagnostics_rows(lbfd_handle* h, int y0, int y1, double* out)
 {
-    if (!h || !out) return LBFD_EINVAL;
+    if (!h || !out || y0 < 0 || y1 > h->grid.ny || y0 >= y1) return LBFD_EINVAL;
     double r[lbfd::RED_WORDS];
-    CK(lbfd::launch_diagnostics(h->dim, h->precision, h->Pd, view(h, h->cur), h->solid, h->red, h->stream));
+    CK(lbfd::launch_diagnostics(h->dim, h->precision, h->Pd, view(h, h->cur), h->solid, y0, y1, h->red, h->stream));
     CK(cudaMemcpyAsync(r, h->red, sizeof r, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     unsigned long long u[lbfd::RED_WORDS];
@@ -517,6 +560,29 @@ int lbfd_diagnostics(lbfd_handle* h, double* out)
     out[LBFD_DIAG_NONFINITE] = (double)u[5];
     out[LBFD_DIAG_NFLUID] = (double)u[6];
     return u[5] ? LBFD_ENONFINITE : LBFD_OK;
+}
+
+int lbfd_diagnostics(lbfd_handle* h, double* out)
+{
+    if (!h) return LBFD_EINVAL;
+    return lbfd_diagnostics_rows(h, 0, h->grid.ny, out);
+}
+
+int lbfd_set_inlet_velocity(lbfd_handle* h, double u_in)
+{
+    if (!h) return LBFD_EINVAL;
+    if (!(fabs(u_in) < sqrt(1.0 / 3.0))) return LBFD_EUNSTABLE;
+    h->prm.u_in = u_in;
+    h->Pd.u_in = u_in;
+    h->Pf.u_in = (float)u_in;
+    const double seed = h->Pt.u_in.d[3];
+    h->Pt.u_in = Tan(u_in);
+    h->Pt.u_in.d[3] = seed;
+    if (h->graph) {  // kernel parameters are baked into a captured graph
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    return LBFD_OK;
 }
 
 int lbfd_flame_position(lbfd_handle* h, double* x_f, double* mass, double* heat_release)
@@ -555,6 +621,37 @@ int lbfd_set_state_raw(lbfd_handle* h, const void* src, size_t bytes)
     const size_t all = h->planes * (size_t)h->stride * h->esz;
     CK(cudaMemcpyAsync(h->buf[h->cur ^ 1], h->buf[h->cur], all, cudaMemcpyDeviceToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    return LBFD_OK;
+}
+
+int lbfd_read_tangent(lbfd_handle* h, int field, int k, double* out)
+{
+    if (!h || !out || h->precision != LBFD_TANGENT || k < 0 || k >= lbfd::NTAN) return LBFD_EINVAL;
+    int plane;
+    if (field == LBFD_FIELD_T) plane = h->Q;
+    else if (field >= LBFD_FIELD_Y0 && field < LBFD_FIELD_Y0 + lbfd::NSP) plane = h->Q + 1 + (field - LBFD_FIELD_Y0);
+    else if (field >= LBFD_FIELD_G0 && field < LBFD_FIELD_G0 + h->Q) plane = field - LBFD_FIELD_G0;
+    else return LBFD_EINVAL;
+    CK(lbfd::launch_tangent_field(h->ncell, h->stride, h->buf[h->cur], plane, k, h->tmp, h->stream));
+    CK(cudaMemcpyAsync(out, h->tmp, (size_t)h->ncell * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LBFD_OK;
+}
+
+int lbfd_gradient(lbfd_handle* h, int objective, double* value, double* grad)
+{
+    if (!h || h->precision != LBFD_TANGENT || (objective != LBFD_OBJ_FLAME_POSITION && objective != LBFD_OBJ_HEAT_RELEASE))
+        return LBFD_EINVAL;
+    double r[1 + lbfd::NTAN];
+    CK(lbfd::launch_objective(h->Pt, view(h, h->cur), h->solid, objective, h->red, h->stream));
+    CK(cudaMemcpyAsync(r, h->red, sizeof r, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    double scale = 1.0;
+    if (objective == LBFD_OBJ_FLAME_POSITION)  // x_f = dx sum Y_F / (Y_F,in * section)
+        scale = h->section > 0.0 ? h->prm.dx / (h->prm.Y_in[h->mech.fuel] * h->section) : 0.0;
+    if (value) *value = r[0] * scale;
+    if (grad)
+        for (int k = 0; k < lbfd::NTAN; ++k) grad[k] = r[1 + k] * scale;
     return LBFD_OK;
 }
 
@@ -654,7 +751,7 @@ extern "C" int lbfd_diagnostics_noalloc(const lbfd_grid* grid, const lbfd_mechan
     v.Y = const_cast<void*>(Y);
     cudaStream_t s = (cudaStream_t)stream;
     // launch_diagnostics clears the words it accumulates into before use
-    CK(lbfd::launch_diagnostics(tmp.dim, tmp.precision, P, v, solid, (double*)red, s));
+    CK(lbfd::launch_diagnostics(tmp.dim, tmp.precision, P, v, solid, 0, tmp.grid.ny, (double*)red, s));
     double r[lbfd::RED_WORDS];
     CK(cudaMemcpyAsync(r, red, sizeof r, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));

@@ -7,7 +7,9 @@
 // Method: Hosseini & Thevenin, arXiv 2304.05657, Sec. II-III.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 
+#include "lbfd_dual.cuh"
 #include "lbfd_params.h"
 
 namespace lbfd {
@@ -106,12 +108,17 @@ __device__ __forceinline__ R arrhenius(const StepParams<R>& P, R T, R yf, R yo)
 {
     yf = yf > R(0) ? yf : R(0);
     yo = yo > R(0) ? yo : R(0);
-    if (sizeof(R) == 4 && T > P.T_fp64) {
-        double q = P.A_lat_d * (double)yf * (double)yo * exp(-P.Ta_d / (double)T);
-        return (R)q;
+    if constexpr (std::is_same<R, float>::value) {
+        if (T > P.T_fp64) {
+            const double q = P.A_lat_d * (double)yf * (double)yo * ::exp(-P.Ta_d / (double)T);
+            return (float)q;
+        }
+        return P.A_lat * yf * yo * expf(-(P.Ta / T));
+    } else if constexpr (std::is_same<R, double>::value) {
+        return P.A_lat * yf * yo * ::exp(-(P.Ta / T));
+    } else {
+        return P.A_lat * yf * yo * exp(-(P.Ta / T));  // the Dual overload
     }
-    if (sizeof(R) == 4) return P.A_lat * yf * yo * (R)expf(-(float)(P.Ta / T));
-    return P.A_lat * yf * yo * (R)exp(-(double)(P.Ta / T));
 }
 
 // ---------------------------------------------------------------------------

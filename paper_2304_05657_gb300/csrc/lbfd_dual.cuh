@@ -103,6 +103,12 @@ __host__ __device__ inline Dual<T, N> exp(const Dual<T, N>& a)
 template <typename T, int N>
 __device__ __forceinline__ Dual<T, N> fdiv(const Dual<T, N>& a, const Dual<T, N>& b) { return a / b; }
 
+// value part of a stored number
+__host__ __device__ inline double val(double x) { return x; }
+__host__ __device__ inline double val(float x) { return (double)x; }
+template <typename T, int N>
+__host__ __device__ inline double val(const Dual<T, N>& x) { return (double)x.v; }
+
 // tangents with respect to (ln A, Ta, T_wall, u_in)
 constexpr int NTAN = 4;
 using Tan = Dual<double, NTAN>;

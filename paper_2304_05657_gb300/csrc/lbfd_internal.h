@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <vector>
 
+#include "lbfd_dual.cuh"
 #include "lbfd_params.h"
 
 namespace lbfd {
@@ -21,24 +22,42 @@ struct StateView {
 // Launch one fused coupled step: state `in` -> state `out`.
 // precision: 0 = FP64 (S = R = double), 1 = mixed (S = R = float).
 // variant: 0 = general form, 1.. = 2-D shared-memory tiles (see lbfd_step.cu)
+// A second stream and two events used to run the boundary kernel next to
+// the tile kernel (fork on `fork`, join on `join`); stream == nullptr runs
+// both on the launch stream.
+struct SideStream {
+    cudaStream_t stream;
+    cudaEvent_t fork, join;
+};
+
 // bnd/nbnd: the fluid cells the 2-D tile kernels leave to the boundary
 // kernel (see boundary_cells); unused by the general variant.
 cudaError_t launch_step(int dim, int precision, int variant, const StepParams<double>& Pd,
                         const StepParams<float>& Pf, StateView in, StateView out, const uint8_t* solid,
-                        const long long* bnd, long long nbnd, cudaStream_t stream);
+                        const long long* bnd, long long nbnd, const SideStream& side, cudaStream_t stream);
 int num_variants(int dim);
 
 // Fluid cells that are not interior for the 2-D tile kernels (host, at create).
 void boundary_cells(int dim, int nx, int ny, int nz, const uint8_t* solid, std::vector<long long>& out);
 
-// Diagnostics reduction into the device scratch `red` (LBFD_NDIAG + extra
-// words, zeroed by the launcher); FP64 accumulation.
+// Diagnostics reduction over the rows y0 <= y < y1 (all x, all z) into the
+// device scratch `red` (RED_WORDS words, zeroed by the launcher); FP64
+// accumulation.
 cudaError_t launch_diagnostics(int dim, int precision, const StepParams<double>& Pd, StateView st,
-                               const uint8_t* solid, double* red, cudaStream_t stream);
+                               const uint8_t* solid, int y0, int y1, double* red, cudaStream_t stream);
 
 // Derived or raw field of every cell into double out[ncell] (device).
 cudaError_t launch_field(int dim, int precision, const StepParams<double>& Pd, StateView st,
                          const uint8_t* solid, int field, double* out, cudaStream_t stream);
+
+// Tangent-linear step (precision 2: Dual<double, 4> values, general form,
+// 2-D), tangent read-out and objective gradients (lbfd_tangent.cu).
+cudaError_t launch_step_tangent(int dim, const StepParams<Tan>& P, StateView in, StateView out, const uint8_t* solid,
+                                cudaStream_t stream);
+cudaError_t launch_tangent_field(long long ncell, long long N, const void* state_base, int plane, int k, double* out,
+                                 cudaStream_t stream);
+cudaError_t launch_objective(const StepParams<Tan>& P, StateView st, const uint8_t* solid, int objective, double* red,
+                             cudaStream_t stream);
 
 // Number of words of the reduction scratch.
 constexpr int RED_WORDS = 16;

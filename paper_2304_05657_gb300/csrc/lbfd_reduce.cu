@@ -28,7 +28,7 @@ __device__ __forceinline__ double hrr_of(const StepParams<double>& P, double T, 
     const double rho = P.T_in * P.invW_in / (T * invW);
     const double yf = Y[P.fuel] > 0.0 ? Y[P.fuel] : 0.0;
     const double yo = Y[P.oxid] > 0.0 ? Y[P.oxid] : 0.0;
-    const double q = P.A_lat * yf * yo * exp(-P.Ta / T);
+    const double q = P.A_lat * yf * yo * ::exp(-P.Ta / T);
     *rho_out = rho;
     *q_out = q;
     return rho * P.Q_cp * q;
@@ -40,26 +40,30 @@ __device__ __forceinline__ double hrr_of(const StepParams<double>& P, double T, 
 template <int DIM, typename S>
 __global__ void __launch_bounds__(256) diag_kernel(StepParams<double> P, const S* __restrict__ g,
                                                    const S* __restrict__ T, const S* __restrict__ Y,
-                                                   const uint8_t* __restrict__ solid, double* red)
+                                                   const uint8_t* __restrict__ solid, int y0, int y1, double* red)
 {
     constexpr int Q = DIM == 2 ? 9 : 27;
     double s[4] = {0.0, 0.0, 0.0, 0.0};
     unsigned long long tkey = 0ull, nonf = 0ull, nfl = 0ull, sec = 0ull;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < P.ncell; c += stride) {
+    const int rows = y1 - y0;
+    const long long ncount = (long long)P.nx * rows * P.nz;  // cells with y0 <= y < y1
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < ncount; t += stride) {
+        const long long r = t / P.nx;
+        const long long c = t % P.nx + (long long)P.nx * (y0 + r % rows + (long long)P.ny * (r / rows));
         if (solid[c]) continue;
         ++nfl;
         if (c % P.nx == 0) ++sec;
-        const double Tc = (double)T[c];
+        const double Tc = val(T[c]);
         double Yc[NSP];
         bool bad = !isfinite(Tc);
 #pragma unroll
         for (int k = 0; k < NSP; ++k) {
-            Yc[k] = (double)Y[(long long)k * P.N + c];
+            Yc[k] = val(Y[(long long)k * P.N + c]);
             bad |= !isfinite(Yc[k]);
         }
 #pragma unroll
-        for (int i = 0; i < Q; ++i) bad |= !isfinite((double)g[(long long)i * P.N + c]);
+        for (int i = 0; i < Q; ++i) bad |= !isfinite(val(g[(long long)i * P.N + c]));
         if (bad) {
             ++nonf;
             continue;
@@ -118,20 +122,21 @@ __global__ void __launch_bounds__(256) diag_kernel(StepParams<double> P, const S
 template <int DIM, typename S>
 __global__ void __launch_bounds__(1024) centreline_kernel(StepParams<double> P, const S* __restrict__ T,
                                                           const S* __restrict__ Y,
-                                                          const uint8_t* __restrict__ solid, double* red)
+                                                          const uint8_t* __restrict__ solid, int y0, int y1,
+                                                          double* red)
 {
     double best = -INFINITY;
     int bx = -1;
-    const int yc = P.ny / 2, zc = DIM == 3 ? P.nz / 2 : 0;
+    const int yc = (y0 + y1) / 2, zc = DIM == 3 ? P.nz / 2 : 0;
     for (int x = threadIdx.x; x < P.nx; x += blockDim.x) {
         const long long c = x + (long long)P.nx * (yc + (long long)P.ny * zc);
         if (solid[c]) continue;
-        const double Tc = (double)T[c];
+        const double Tc = val(T[c]);
         double Yc[NSP];
         bool bad = !isfinite(Tc);
 #pragma unroll
         for (int k = 0; k < NSP; ++k) {
-            Yc[k] = (double)Y[(long long)k * P.N + c];
+            Yc[k] = val(Y[(long long)k * P.N + c]);
             bad |= !isfinite(Yc[k]);
         }
         if (bad) continue;
@@ -173,32 +178,35 @@ __global__ void __launch_bounds__(1024) centreline_kernel(StepParams<double> P, 
 }
 
 template <int DIM, typename S>
-static cudaError_t diag_launch(const StepParams<double>& P, StateView st, const uint8_t* solid, double* red,
-                               cudaStream_t stream)
+static cudaError_t diag_launch(const StepParams<double>& P, StateView st, const uint8_t* solid, int y0, int y1,
+                               double* red, cudaStream_t stream)
 {
     cudaError_t e = cudaMemsetAsync(red, 0, RED_WORDS * sizeof(double), stream);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    long long want = (P.ncell + 255) / 256;
+    long long want = ((long long)P.nx * (y1 - y0) * P.nz + 255) / 256;
     long long cap = (long long)(sms > 0 ? sms : 1) * 8;
     const unsigned blocks = (unsigned)(want < cap ? (want > 0 ? want : 1) : cap);
-    diag_kernel<DIM, S><<<blocks, 256, 0, stream>>>(P, (const S*)st.g, (const S*)st.T, (const S*)st.Y, solid, red);
+    diag_kernel<DIM, S><<<blocks, 256, 0, stream>>>(P, (const S*)st.g, (const S*)st.T, (const S*)st.Y, solid, y0, y1,
+                                                    red);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    centreline_kernel<DIM, S><<<1, 1024, 0, stream>>>(P, (const S*)st.T, (const S*)st.Y, solid, red);
+    centreline_kernel<DIM, S><<<1, 1024, 0, stream>>>(P, (const S*)st.T, (const S*)st.Y, solid, y0, y1, red);
     return cudaGetLastError();
 }
 
 cudaError_t launch_diagnostics(int dim, int precision, const StepParams<double>& P, StateView st,
-                               const uint8_t* solid, double* red, cudaStream_t stream)
+                               const uint8_t* solid, int y0, int y1, double* red, cudaStream_t stream)
 {
     if (precision == 0)
-        return dim == 2 ? diag_launch<2, double>(P, st, solid, red, stream)
-                        : diag_launch<3, double>(P, st, solid, red, stream);
-    return dim == 2 ? diag_launch<2, float>(P, st, solid, red, stream)
-                    : diag_launch<3, float>(P, st, solid, red, stream);
+        return dim == 2 ? diag_launch<2, double>(P, st, solid, y0, y1, red, stream)
+                        : diag_launch<3, double>(P, st, solid, y0, y1, red, stream);
+    if (precision == 2)
+        return dim == 2 ? diag_launch<2, Tan>(P, st, solid, y0, y1, red, stream) : cudaErrorInvalidValue;
+    return dim == 2 ? diag_launch<2, float>(P, st, solid, y0, y1, red, stream)
+                    : diag_launch<3, float>(P, st, solid, y0, y1, red, stream);
 }
 
 // field ids follow include/lbfd.h
@@ -212,21 +220,21 @@ __global__ void __launch_bounds__(256) field_kernel(StepParams<double> P, const 
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= P.ncell) return;
     if (field >= 16) {
-        out[c] = (double)g[(long long)(field - 16) * P.N + c];
+        out[c] = val(g[(long long)(field - 16) * P.N + c]);
         return;
     }
     if (field == 0) {
-        out[c] = (double)T[c];
+        out[c] = val(T[c]);
         return;
     }
     if (field >= 1 && field <= NSP) {
-        out[c] = (double)Y[(long long)(field - 1) * P.N + c];
+        out[c] = val(Y[(long long)(field - 1) * P.N + c]);
         return;
     }
-    const double Tc = (double)T[c];
+    const double Tc = val(T[c]);
     double Yc[NSP];
 #pragma unroll
-    for (int k = 0; k < NSP; ++k) Yc[k] = (double)Y[(long long)k * P.N + c];
+    for (int k = 0; k < NSP; ++k) Yc[k] = val(Y[(long long)k * P.N + c]);
     double rho, q;
     const double h = hrr_of<S>(P, Tc, Yc, &rho, &q);
     double v = 0.0;
@@ -235,12 +243,12 @@ __global__ void __launch_bounds__(256) field_kernel(StepParams<double> P, const 
         if (a < DIM) {
             double m = 0.0;
 #pragma unroll
-            for (int i = 0; i < Q; ++i) m += (double)ccomp<DIM>(i, a) * (double)g[(long long)i * P.N + c];
+            for (int i = 0; i < Q; ++i) m += (double)ccomp<DIM>(i, a) * val(g[(long long)i * P.N + c]);
             v = 3.0 * m / rho;
         }
     } else if (field == 9) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) v += (double)g[(long long)i * P.N + c];
+        for (int i = 0; i < Q; ++i) v += val(g[(long long)i * P.N + c]);
     } else if (field == 10) {
         v = rho;
     } else if (field == 11) {
@@ -253,6 +261,12 @@ cudaError_t launch_field(int dim, int precision, const StepParams<double>& P, St
                          int field, double* out, cudaStream_t stream)
 {
     const unsigned blocks = (unsigned)((P.ncell + 255) / 256);
+    if (precision == 2) {
+        if (dim != 2) return cudaErrorInvalidValue;
+        field_kernel<2, Tan><<<blocks, 256, 0, stream>>>(P, (const Tan*)st.g, (const Tan*)st.T, (const Tan*)st.Y,
+                                                          solid, field, out);
+        return cudaGetLastError();
+    }
     if (precision == 0) {
         if (dim == 2)
             field_kernel<2, double><<<blocks, 256, 0, stream>>>(P, (const double*)st.g, (const double*)st.T,

@@ -42,7 +42,7 @@ static cudaError_t launch_general(const StepParams<R>& P, StateView in, StateVie
 
 template <typename S, typename R, int TX, int TY>
 static cudaError_t launch_tiled(const StepParams<R>& P, StateView in, StateView out, const uint8_t* solid,
-                                const long long* bnd, long long nbnd, cudaStream_t stream)
+                                const long long* bnd, long long nbnd, const SideStream& side, cudaStream_t stream)
 {
     constexpr size_t smem = tile_smem_bytes<R, TX, TY>();
     auto kern = step_kernel_tiled2d<S, R, TX, TY>;
@@ -51,27 +51,41 @@ static cudaError_t launch_tiled(const StepParams<R>& P, StateView in, StateView 
         if (e != cudaSuccess) return e;
     }
     dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
+    // the cells the tile kernel skips go to the boundary kernel: disjoint
+    // writes, same input state, so it runs concurrently on the side stream
+    const bool fork = nbnd > 0 && side.stream != nullptr;
+    cudaError_t e = cudaSuccess;
+    if (fork) {
+        if ((e = cudaEventRecord(side.fork, stream)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(side.stream, side.fork, 0)) != cudaSuccess) return e;
+    }
+    cudaStream_t bs = fork ? side.stream : stream;
+    if (nbnd > 0) {
+        const unsigned nb = (unsigned)((nbnd + 127) / 128);
+        step_kernel_boundary<2, S, R><<<nb, 128, 0, bs>>>(P, (const S*)in.g, (S*)out.g, (const S*)in.T, (S*)out.T,
+                                                          (const S*)in.Y, (S*)out.Y, solid, bnd, nbnd);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     kern<<<grid, dim3(TX, TY), smem, stream>>>(P, (const S*)in.g, (S*)out.g, (const S*)in.T, (S*)out.T,
                                                (const S*)in.Y, (S*)out.Y, solid);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || nbnd == 0) return e;
-    // the cells the tile kernel skipped (disjoint writes, same input state)
-    const unsigned nb = (unsigned)((nbnd + 127) / 128);
-    step_kernel_boundary<2, S, R><<<nb, 128, 0, stream>>>(P, (const S*)in.g, (S*)out.g, (const S*)in.T,
-                                                          (S*)out.T, (const S*)in.Y, (S*)out.Y, solid, bnd, nbnd);
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (fork) {
+        if ((e = cudaEventRecord(side.join, side.stream)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(stream, side.join, 0)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 template <typename S, typename R>
 static cudaError_t launch_2d(int variant, const StepParams<R>& P, StateView in, StateView out, const uint8_t* solid,
-                             const long long* bnd, long long nbnd, cudaStream_t stream)
+                             const long long* bnd, long long nbnd, const SideStream& side, cudaStream_t stream)
 {
     switch (variant) {
     case 0: return launch_general<2, S, R>(P, in, out, solid, stream);
-    case 1: return launch_tiled<S, R, 32, 8>(P, in, out, solid, bnd, nbnd, stream);
-    case 2: return launch_tiled<S, R, 32, 4>(P, in, out, solid, bnd, nbnd, stream);
-    case 3: return launch_tiled<S, R, 64, 4>(P, in, out, solid, bnd, nbnd, stream);
-    case 4: return launch_tiled<S, R, 32, 16>(P, in, out, solid, bnd, nbnd, stream);
+    case 1: return launch_tiled<S, R, 32, 8>(P, in, out, solid, bnd, nbnd, side, stream);
+    case 2: return launch_tiled<S, R, 32, 4>(P, in, out, solid, bnd, nbnd, side, stream);
+    case 3: return launch_tiled<S, R, 64, 4>(P, in, out, solid, bnd, nbnd, side, stream);
+    case 4: return launch_tiled<S, R, 32, 16>(P, in, out, solid, bnd, nbnd, side, stream);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -80,14 +94,14 @@ int num_variants(int dim) { return dim == 2 ? 5 : 1; }
 
 cudaError_t launch_step(int dim, int precision, int variant, const StepParams<double>& Pd,
                         const StepParams<float>& Pf, StateView in, StateView out, const uint8_t* solid,
-                        const long long* bnd, long long nbnd, cudaStream_t stream)
+                        const long long* bnd, long long nbnd, const SideStream& side, cudaStream_t stream)
 {
     if (variant < 0 || variant >= num_variants(dim)) return cudaErrorInvalidValue;
     if (precision == 0) {
-        if (dim == 2) return launch_2d<double, double>(variant, Pd, in, out, solid, bnd, nbnd, stream);
+        if (dim == 2) return launch_2d<double, double>(variant, Pd, in, out, solid, bnd, nbnd, side, stream);
         return launch_general<3, double, double>(Pd, in, out, solid, stream);
     }
-    if (dim == 2) return launch_2d<float, float>(variant, Pf, in, out, solid, bnd, nbnd, stream);
+    if (dim == 2) return launch_2d<float, float>(variant, Pf, in, out, solid, bnd, nbnd, side, stream);
     return launch_general<3, float, float>(Pf, in, out, solid, stream);
 }
 

@@ -41,6 +41,17 @@ __device__ __forceinline__ R pull_general(const StepParams<R>& P, int i, const i
         else wall = 1;
     }
     const int ib = opposite<DIM>(i);
+    if (!wall && (inlet >= 0 || outlet >= 0)) {
+        // leaving through an inlet/outlet face where the boundary column is
+        // solid: the link hits the solid (bounce-back, as at a wall corner)
+        int q[3] = {src[0], src[1], src[2]};
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            const int n = extent(P, a);
+            q[a] = q[a] < 0 ? 0 : (q[a] >= n ? n - 1 : q[a]);
+        }
+        if (solid[cell_of(P, q[0], q[1], DIM == 3 ? q[2] : 0)]) wall = 1;
+    }
     if (wall) return R(g[(long long)ib * N + c]);  // Eq. 28
     if (inlet >= 0) {                              // Eq. 31 applied to g
         const int a = inlet / 2;

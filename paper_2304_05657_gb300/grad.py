@@ -1,0 +1,70 @@
+"""Gradients of flame observables with respect to the model parameters
+theta = (ln A, Ta, T_wall, u_in), behind a torch.autograd.Function.
+
+The forward pass runs the coupled step in the library's tangent precision
+(every state value carries its four derivatives, propagated exactly through
+the discrete step), so the gradient is ready when the forward pass ends;
+backward only scales it by the incoming gradient.  With four parameters
+this needs one pass and no stored trajectory.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import lbfd
+
+
+def apply_theta(cfg: dict, theta) -> dict:
+    """Configuration with theta = (ln A, Ta, T_wall, u_in) substituted;
+    T_wall sets every isothermal wall face and the solid temperature."""
+    lnA, Ta, Tw, u_in = (float(t) for t in theta)
+    out = dict(cfg)
+    out["A"] = math.exp(lnA)
+    out["Ta"] = Ta
+    out["T_wall"] = [Tw if b == "wall_isothermal" else cfg["T_wall"][f] for f, b in enumerate(cfg["bc"])]
+    out["T_solid"] = Tw if cfg["solid_isothermal"] else cfg["T_solid"]
+    out["u_in"] = u_in
+    return out
+
+
+def theta_of(cfg: dict):
+    walls = [cfg["T_wall"][f] for f, b in enumerate(cfg["bc"]) if b == "wall_isothermal"]
+    Tw = walls[0] if walls else cfg["T_solid"]
+    return np.array([math.log(cfg["A"]), cfg["Ta"], Tw, cfg["u_in"]])
+
+
+def run_tangent(cfg: dict, solid, T0, Y0, steps: int, objective: int = lbfd.OBJ_FLAME_POSITION, theta=None):
+    """J after `steps` steps from (T0, Y0, g = 0) and dJ/dtheta."""
+    c = apply_theta(cfg, theta) if theta is not None else dict(cfg)
+    c["precision"] = "tangent"
+    s = lbfd.Solver(c, solid)
+    s.init_fields(T0, Y0)
+    s.step(steps)
+    J, g = s.gradient(objective)
+    s.close()
+    return J, g
+
+
+try:
+    import torch
+
+    class FlameObjective(torch.autograd.Function):
+        """J(theta) = flame position (or heat release) after `steps` steps.
+
+        forward(theta[4] float64 tensor, cfg, solid, T0, Y0, steps, objective)."""
+
+        @staticmethod
+        def forward(ctx, theta, cfg, solid, T0, Y0, steps, objective=lbfd.OBJ_FLAME_POSITION):
+            J, g = run_tangent(cfg, solid, T0, Y0, int(steps), int(objective), theta.detach().cpu().numpy())
+            ctx.save_for_backward(torch.as_tensor(g, dtype=theta.dtype, device=theta.device))
+            return theta.new_tensor(J)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (g,) = ctx.saved_tensors
+            return grad_out * g, None, None, None, None, None, None
+
+except ImportError:  # torch is optional for the C-ABI user
+    FlameObjective = None

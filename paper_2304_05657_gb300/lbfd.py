@@ -19,7 +19,10 @@ LIB_PATH = os.path.join(HERE, "liblbfd.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, EUNSTABLE, ENOTSUP = range(8)
 BC = {"periodic": 0, "wall_adiabatic": 1, "wall_isothermal": 2, "inlet": 3, "outlet": 4, "outlet_pressure": 5}
-FP64, MIXED = 0, 1
+FP64, MIXED, TANGENT = 0, 1, 2
+PRECISION = {"fp64": FP64, "mixed": MIXED, "tangent": TANGENT}
+OBJ_FLAME_POSITION, OBJ_HEAT_RELEASE = 0, 1
+THETA = ("ln_A", "Ta", "T_wall", "u_in")
 NSP = 5
 FIELD_T, FIELD_Y0, FIELD_UX, FIELD_UY, FIELD_UZ, FIELD_PH, FIELD_RHO, FIELD_HRR, FIELD_G0 = 0, 1, 6, 7, 8, 9, 10, 11, 16
 NDIAG = 8
@@ -31,7 +34,8 @@ SYMBOLS = (
     "lbfd_read_field", "lbfd_diagnostics", "lbfd_flame_position", "lbfd_state_bytes", "lbfd_get_state_raw",
     "lbfd_set_state_raw", "lbfd_steps_done", "lbfd_num_cells", "lbfd_num_populations", "lbfd_strerror",
     "lbfd_last_error", "lbfd_step_graph", "lbfd_num_variants", "lbfd_get_variant", "lbfd_set_variant",
-    "lbfd_autotune", "lbfd_diagnostics_noalloc", "lbfd_launches_per_step",
+    "lbfd_autotune", "lbfd_diagnostics_noalloc", "lbfd_launches_per_step", "lbfd_read_tangent", "lbfd_gradient",
+    "lbfd_diagnostics_rows", "lbfd_set_inlet_velocity",
 )
 
 
@@ -105,6 +109,10 @@ def load(path: str = LIB_PATH):
     lib.lbfd_get_variant.argtypes = [H]
     lib.lbfd_set_variant.argtypes = [H, ctypes.c_int]
     lib.lbfd_launches_per_step.argtypes = [H]
+    lib.lbfd_read_tangent.argtypes = [H, ctypes.c_int, ctypes.c_int, D]
+    lib.lbfd_diagnostics_rows.argtypes = [H, ctypes.c_int, ctypes.c_int, D]
+    lib.lbfd_set_inlet_velocity.argtypes = [H, ctypes.c_double]
+    lib.lbfd_gradient.argtypes = [H, ctypes.c_int, D, D]
     lib.lbfd_autotune.argtypes = [H, ctypes.c_int, D, ctypes.POINTER(ctypes.c_int)]
     lib.lbfd_diagnostics_noalloc.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Mechanism), ctypes.POINTER(Params),
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong,
@@ -142,7 +150,7 @@ def make_structs(cfg: dict):
         p.Y_in[k] = cfg["Y_in"][k]
     p.T_solid, p.solid_isothermal = cfg["T_solid"], int(cfg["solid_isothermal"])
     p.dx, p.dt, p.T_fp64, p.weno_eps = cfg["dx"], cfg["dt"], cfg["T_fp64"], cfg["weno_eps"]
-    p.precision = MIXED if cfg.get("precision", "fp64") == "mixed" else FP64
+    p.precision = PRECISION[cfg.get("precision", "fp64")]
     p.poiseuille_inlet = int(cfg["poiseuille_inlet"])
     return g, m, p
 
@@ -218,6 +226,19 @@ class Solver:
     def variant(self, v: int):
         _check(self.lib, self.lib.lbfd_set_variant(self.h, int(v)), "lbfd_set_variant")
 
+    def read_tangent(self, field: int, k: int) -> np.ndarray:
+        """Derivative k (order of THETA) of a raw field; tangent precision."""
+        out = np.empty(self.N)
+        _check(self.lib, self.lib.lbfd_read_tangent(self.h, int(field), int(k), _dp(out)), "lbfd_read_tangent")
+        return out
+
+    def gradient(self, objective: int = OBJ_FLAME_POSITION):
+        """(J, dJ/dtheta) of the current state; tangent precision."""
+        val = np.zeros(1)
+        grad = np.zeros(4)
+        _check(self.lib, self.lib.lbfd_gradient(self.h, int(objective), _dp(val), _dp(grad)), "lbfd_gradient")
+        return float(val[0]), grad
+
     @property
     def launches_per_step(self) -> int:
         return int(self.lib.lbfd_launches_per_step(self.h))
@@ -242,10 +263,19 @@ class Solver:
         g = np.stack([self.read_field(FIELD_G0 + i) for i in range(self.Q)])
         return T, Y, g
 
-    def diagnostics(self) -> dict:
+    def diagnostics(self, rows=None) -> dict:
+        """Reductions over the fluid cells (all, or the rows y0 <= y < y1)."""
         out = np.empty(NDIAG)
-        _check(self.lib, self.lib.lbfd_diagnostics(self.h, _dp(out)), "lbfd_diagnostics", allow=(ENONFINITE,))
+        if rows is None:
+            st = self.lib.lbfd_diagnostics(self.h, _dp(out))
+        else:
+            st = self.lib.lbfd_diagnostics_rows(self.h, int(rows[0]), int(rows[1]), _dp(out))
+        _check(self.lib, st, "lbfd_diagnostics", allow=(ENONFINITE,))
         return dict(zip(DIAG_KEYS, out.tolist()))
+
+    def set_inlet_velocity(self, u_in: float):
+        _check(self.lib, self.lib.lbfd_set_inlet_velocity(self.h, float(u_in)), "lbfd_set_inlet_velocity")
+        self.cfg["u_in"] = float(u_in)
 
     def flame_position(self):
         x, m, q = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()

@@ -305,3 +305,27 @@ def test_adiabatic_flame_temperature(oracle_mod):
     burnt = T2[45:front - 40]
     assert burnt.size > 5
     assert np.abs(burnt / T_ad - 1.0).max() < 5e-3, (burnt.min(), burnt.max(), T_ad)
+
+
+def test_packed_channels_are_independent_problems(oracle_mod):
+    """Channels stacked along y with one isothermal solid row between them
+    evolve exactly as the same channels run alone with isothermal walls:
+    no stencil or population crosses a solid row."""
+    widths = [4, 7, 10]
+    cfg, solid, T, Y, seg = inputs.batched_channels(widths=widths, length=30, ignite=(5, 15))
+    nx = cfg["nx"]
+    o = oracle_mod.Sim(cfg, solid)
+    rng = np.random.default_rng(5)
+    g = rng.uniform(-1e-3, 1e-3, size=(9, solid.size))
+    g[:, solid.ravel() == 1] = 0.0
+    o.set_state(T, Y, g)
+    o.step(25)
+    Tb, Yb, gb = o.get_state()
+    for (y0, y1), w in zip(seg, widths):
+        c1, s1, _, _ = inputs.channel(nx=nx, ny=w, walls="isothermal", T_wall=cfg["T_wall"][2])
+        sl = slice(y0 * nx, y1 * nx)
+        o1 = oracle_mod.Sim(c1, s1)
+        o1.set_state(T[sl], Y[:, sl], g[:, sl])
+        o1.step(25)
+        T1, Y1, g1 = o1.get_state()
+        assert np.array_equal(T1, Tb[sl]) and np.array_equal(Y1, Yb[:, sl]) and np.array_equal(g1, gb[:, sl])
