@@ -78,6 +78,7 @@ def _load():
         lib.orc_set_state.argtypes = [P, D, D, ctypes.c_void_p]
         lib.orc_get_state.argtypes = [P, D, D, D]
         lib.orc_step.argtypes = [P, ctypes.c_int]
+        lib.orc_step_slab.argtypes = [P, ctypes.c_int, ctypes.c_int]
         lib.orc_cell_terms.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, D]
         lib.orc_collide_cell.argtypes = [P, D, ctypes.c_double, D, D, ctypes.c_double, D, D, D]
         lib.orc_central_moments.argtypes = [P, D, D, D]
@@ -173,6 +174,10 @@ class Sim:
 
     def step(self, n: int = 1):
         self.lib.orc_step(self.h, int(n))
+
+    def step_slab(self, x0: int, x1: int):
+        """One step of the cells x0 <= x < x1 only."""
+        self.lib.orc_step_slab(self.h, int(x0), int(x1))
 
     def cell_terms(self, x: int, y: int, z: int = 0) -> dict:
         nsp, Q = self.nsp, self.Q

@@ -880,6 +880,35 @@ void orc_step(orc_sim *S, int n)
     }
 }
 
+/* One step of the cells with x0 <= x < x1 only (a slab of a domain
+ * decomposition along x); every other cell keeps its current state.  Used
+ * by the decomposition test: the update of a slab reads nothing beyond
+ * two cells on each side of it. */
+void orc_step_slab(orc_sim *S, int x0, int x1)
+{
+    long N = S->N;
+    double gin[27], gst[27], Yn[ORC_MAXSP], Tn;
+    memcpy(S->gn, S->g, sizeof(double) * (size_t)S->Q * N);
+    memcpy(S->Tn, S->T, sizeof(double) * (size_t)N);
+    memcpy(S->Yn, S->Y, sizeof(double) * (size_t)S->nsp * N);
+    for (int z = 0; z < S->s.nz; ++z)
+        for (int y = 0; y < S->s.ny; ++y)
+            for (int x = x0; x < x1; ++x) {
+                int p[3] = {x, y, z};
+                long c = cell_index(S, p);
+                if (S->solid[c]) continue;
+                cell_update(S, p, c, gin, NULL, &Tn, Yn, gst);
+                S->Tn[c] = Tn;
+                for (int k = 0; k < S->nsp; ++k) S->Yn[(long)k * N + c] = Yn[k];
+                for (int i = 0; i < S->Q; ++i) S->gn[(long)i * N + c] = gst[i];
+            }
+    double *t;
+    t = S->g; S->g = S->gn; S->gn = t;
+    t = S->T; S->T = S->Tn; S->Tn = t;
+    t = S->Y; S->Y = S->Yn; S->Yn = t;
+    S->steps++;
+}
+
 /* Per-cell terms of the next step at cell (x,y,z), without advancing.
  * out layout: rho, u[3], grad_rho[3], conv_T, diff_T, reac_T, Lambda, P_h,
  * then conv_Y[nsp], diff_Y[nsp], reac_Y[nsp], then g_in[Q], g*[Q],
