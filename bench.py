@@ -40,7 +40,8 @@ def workload(name: str, precision: str):
     """(cfg, solid, T, Y, description) of a named workload."""
     if name == "batched16x1024":
         cfg, solid, T, Y, seg = inputs.batched_channels()
-        desc = "16 D2Q9 channels, widths 16..196 (step 12), length 1024, isothermal 300 K walls, 1 solid row between"
+        desc = ("16 D2Q9 channels, widths 16..196 (step 12), length 1024, isothermal 300 K walls, 1 solid row "
+                "between, closed adiabatic ignition end, constant-pressure open end")
     elif name == "channel256x32":
         cfg, solid, T, Y = inputs.channel(nx=256, ny=32)
         T, Y = inputs.ignition_fields(cfg, solid, 0, 20, burnt=False)
@@ -51,6 +52,9 @@ def workload(name: str, precision: str):
     elif name == "porous512x256x256":
         cfg, solid, T, Y = inputs.sphere_packing()
         desc = "D3Q27 512x256x256 overlapping spheres r in [8,16], porosity 0.80"
+    elif name == "porous128x64x64":
+        cfg, solid, T, Y = inputs.sphere_packing(nx=128, ny=64, nz=64, x_range=(16, 112))
+        desc = "D3Q27 128x64x64 overlapping spheres r in [8,16], porosity 0.80 (profiling size)"
     else:
         raise SystemExit(f"unknown workload {name}")
     cfg["precision"] = precision
@@ -70,6 +74,9 @@ def sample_workload(name: str, precision: str, length: int = 96):
     if name == "burner2048x512":
         cfg, solid, T, Y = inputs.cylinder_burner(nx=256, ny=128, x_range=(64, 192))
         return cfg, solid, T, Y, "a 256x128 crop of the burner geometry"
+    if name == "porous128x64x64":
+        cfg, solid, T, Y = inputs.sphere_packing(nx=32, ny=16, nz=16, x_range=(4, 28), r_range=(2.0, 4.0))
+        return cfg, solid, T, Y, "a 32x16x16 sphere packing"
     cfg, solid, T, Y = inputs.sphere_packing(nx=32, ny=16, nz=16, x_range=(4, 28), r_range=(2.0, 4.0))
     return cfg, solid, T, Y, "a 32x16x16 sphere packing"
 
@@ -236,6 +243,40 @@ def gradient_rate(args):
     return out
 
 
+def fp64_form(args, flush):
+    """The plain FP64 form on the same workload and state recipe, timed the
+    same way (flush + events per step) over fewer steps."""
+    import torch
+
+    from paper_2304_05657_gb300 import lbfd
+
+    cfg, solid, T, Y, _ = workload(args.workload, "fp64")
+    stream = torch.cuda.current_stream()
+    s = lbfd.Solver(cfg, solid, stream=stream)
+    s.init_fields(T, Y)
+    done = 0
+    while done < args.prerun:
+        n = min(1000, args.prerun - done)
+        s.step_graph(n)
+        done += n
+    s.step(3)
+    best, _ = s.autotune(reps=3)
+    ms = []
+    for _ in range(args.fp64_steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(1)
+        e1.record(stream)
+        ms.append((e0, e1))
+    torch.cuda.synchronize()
+    t = sum(a.elapsed_time(b) for a, b in ms) / len(ms)
+    fluid = int((solid == 0).sum())
+    s.close()
+    return {"value": fluid / (t * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": t, "steps": args.fp64_steps,
+            "kernel_variant": best, "dtype": "f64", "roofline_frac": fluid * 241 / (t * 1e-3) / 1e9 / peaks()[0]}
+
+
 def run_ours(args):
     import torch
 
@@ -257,6 +298,15 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     s = lbfd.Solver(cfg, solid, stream=stream)
     s.init_fields(T, Y)
+    # advance the physical state to mid-run (flames burning) before timing
+    done = 0
+    while done < args.prerun:
+        n = min(1000, args.prerun - done)
+        s.step_graph(n)
+        done += n
+    torch.cuda.synchronize()
+    T_now = s.read_field(lbfd.FIELD_T)
+    hot_fraction = float(((T_now > cfg["T_fp64"]) & (solid.ravel() == 0)).sum() / max(1, (solid == 0).sum()))
     fluid = int((solid == 0).sum())
     ncell = solid.size
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -347,11 +397,15 @@ def run_ours(args):
         "clocks": clocks,
         "wall_ms_per_step_with_flush": 1e3 * t_wall / args.steps,
         "diagnostics_after": {k: diag[k] for k in ("x_f", "T_max", "n_nonfinite")},
+        "prerun_steps": args.prerun,
+        "fluid_fraction_above_T_fp64": hot_fraction,
     }
     if rank == 0 and world == 1 and not args.no_baseline:
         line["cpu_baseline"] = cpu_baseline(args, precision)
     if rank == 0 and world == 1 and args.grad_steps > 0:
         line["gradient"] = gradient_rate(args)
+    if rank == 0 and world == 1 and args.fp64_steps > 0 and precision == "mixed":
+        line["fp64_form"] = fp64_form(args, flush)
     if rank == 0:
         print(json.dumps(line), flush=True)
     s.close()
@@ -366,16 +420,22 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="batched16x1024",
-                    choices=["batched16x1024", "channel256x32", "burner2048x512", "porous512x256x256"])
+                    choices=["batched16x1024", "channel256x32", "burner2048x512", "porous512x256x256",
+                             "porous128x64x64"])
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--baseline-steps", type=int, default=40)
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--grad-steps", type=int, default=200, help="gradient-rate steps (0: skip)")
+    ap.add_argument("--fp64-steps", type=int, default=100, help="steps of the FP64 comparison (0: skip)")
+    ap.add_argument("--prerun", type=int, default=None,
+                    help="untimed physical steps before warm-up (default: 10000 for the batched channels)")
     ap.add_argument("--variant", type=int, default=None, help="kernel variant (default: autotune)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
+    if args.prerun is None:
+        args.prerun = 10000 if args.workload == "batched16x1024" else 0
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -183,9 +183,12 @@ int lbfd_step_graph(lbfd_handle* h, int n);
 
 /* Kernel variants of the step: 0 is the general form (any cell, D2Q9 and
  * D3Q27); in 2-D, 1..4 are shared-memory tiles of 32x8, 32x4, 64x4 and
- * 32x16 interior cells, followed by the general form over the list of
- * boundary cells (computed at create).  All variants compute
- * the same step up to rounding order.  Default: 1 in 2-D, 0 in 3-D. */
+ * 32x16 interior cells and 5..8 the same tiles that also update the cells
+ * next to in-domain solid cells (staircase walls, from shared memory); in 3-D, 1..2 are 32x4 columns marching through 16
+ * or 32 z-planes with a five-plane shared-memory ring.  The tile variants
+ * are followed by the general form over the list of boundary cells
+ * (computed at create).  All variants compute the same step up to rounding
+ * order.  Default: 1 (0 for LBFD_TANGENT, which has the general form only). */
 int lbfd_num_variants(const lbfd_handle* h);
 int lbfd_get_variant(const lbfd_handle* h);
 int lbfd_set_variant(lbfd_handle* h, int variant);
@@ -279,6 +282,24 @@ int lbfd_diagnostics_noalloc(const lbfd_grid* grid, const lbfd_mechanism* mech,
                              const lbfd_params* params, const void* g, const void* T,
                              const void* Y, long long plane_stride, const uint8_t* solid,
                              void* stream, double* out);
+
+/* Curved walls (Sec. III): n analytic primitives, 5 doubles each,
+ *   {0, cx, cy, cz, r}: sphere (circle in 2-D), solid inside;
+ *   {1, nx, ny, nz, d}: half-space, unit normal pointing into the solid,
+ *                      solid where n.x > d;
+ * in lattice coordinates with the centre of cell (x, y, z) at
+ * (x+1/2, y+1/2, z+1/2) (z ignored in 2-D).  The solid mask given to
+ * lbfd_create stays the definition of solid cells and should agree with the
+ * primitives.  Every population pulled from a solid cell then uses the
+ * interpolated bounce-back of Eq. 29 with the wall distance q of its link
+ * (Eq. 30; half-way bounce-back when the link meets no primitive), and the
+ * FD stencils read, at solid cells within two cells of fluid, image-point
+ * ghost values (Eq. 34): the mirror image across the nearest wall point,
+ * valued by Shepard inverse-distance weighting (p = 2) of the fluid cells
+ * within 4 dr (Eq. 35-38; the density reconstructed itself).  Domain faces
+ * keep their own rules.  n = 0 restores staircase walls.  Computes the
+ * tables on the host; adds a ghost-fill launch to every step. */
+int lbfd_set_curved_walls(lbfd_handle* h, int n, const double* prims);
 
 /* Counters and sizes. */
 long long lbfd_steps_done(const lbfd_handle* h);

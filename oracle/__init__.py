@@ -79,6 +79,9 @@ def _load():
         lib.orc_get_state.argtypes = [P, D, D, D]
         lib.orc_step.argtypes = [P, ctypes.c_int]
         lib.orc_step_slab.argtypes = [P, ctypes.c_int, ctypes.c_int]
+        lib.orc_set_geometry.argtypes = [P, ctypes.c_int, D]
+        lib.orc_num_ghosts.restype = ctypes.c_long
+        lib.orc_num_ghosts.argtypes = [P]
         lib.orc_cell_terms.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, D]
         lib.orc_collide_cell.argtypes = [P, D, ctypes.c_double, D, D, ctypes.c_double, D, D, D]
         lib.orc_central_moments.argtypes = [P, D, D, D]
@@ -174,6 +177,18 @@ class Sim:
 
     def step(self, n: int = 1):
         self.lib.orc_step(self.h, int(n))
+
+    def set_geometry(self, prims):
+        """Curved walls: prims is a list of (type, p0, p1, p2, p3) with
+        type 0 = sphere/circle (centre, radius), 1 = half-space (unit normal
+        into the solid, offset); cell centres at (x+.5, y+.5, z+.5)."""
+        arr = np.ascontiguousarray(np.asarray(prims, dtype=np.float64).reshape(-1, 5))
+        self._prims = arr
+        self.lib.orc_set_geometry(self.h, int(arr.shape[0]), _dp(arr))
+
+    @property
+    def num_ghosts(self) -> int:
+        return int(self.lib.orc_num_ghosts(self.h))
 
     def step_slab(self, x0: int, x1: int):
         """One step of the cells x0 <= x < x1 only."""

@@ -105,6 +105,16 @@ typedef struct {
     double cs2, cs, omega_s, omega_b, alpha, D[ORC_MAXSP], A_lat;
     double invW_in, rho_in;
     long steps;
+    /* curved walls (optional) */
+    int curved, nprims;
+    double *prims;      /* 5 per primitive */
+    double *linkq;      /* [Q][N] wall distance fraction of cut links, -1 elsewhere */
+    long *ghost_of;     /* [N] ghost index of a solid cell, -1 if none */
+    long nghost;
+    long *gh_start;     /* [nghost+1] CSR of the image-point neighbours */
+    long *gh_idx;
+    double *gh_w;
+    double *gh_B;       /* [nghost][3] boundary points */
 } orc_sim;
 
 /* one point of an FD line: primitive and derived values */
@@ -257,6 +267,248 @@ static void ghost_pt(const orc_sim *S, int type, int face, const orc_pt *m, orc_
     }
 }
 
+/* ------------------------------------------------------------------ */
+/* curved walls: interpolated bounce-back (Eq. 29-30) and image-point   */
+/* ghosts with Shepard inverse-distance weighting (Eq. 34-38)           */
+/* ------------------------------------------------------------------ */
+
+/* Primitive k: prim[5k] = type (0: sphere/circle, 1: half-space), then
+ * sphere: centre (p0, p1, p2), radius p3, solid inside;
+ * half-space: unit normal (p0, p1, p2) pointing into the solid, offset p3,
+ * solid where n.x > p3.  Cell (x,y,z) has its centre at (x+.5, y+.5, z+.5);
+ * in 2-D the z components are ignored. */
+
+static void cell_centre(const orc_sim *S, const int p[3], double c[3])
+{
+    c[0] = p[0] + 0.5;
+    c[1] = p[1] + 0.5;
+    c[2] = S->s.dim == 3 ? p[2] + 0.5 : 0.0;
+}
+
+static int prim_inside(const orc_sim *S, int k, const double x[3])
+{
+    const double *P = &S->prims[5 * k];
+    if ((int)P[0] == 0) {
+        double d2 = 0.0;
+        for (int a = 0; a < S->s.dim; ++a) d2 += (x[a] - P[1 + a]) * (x[a] - P[1 + a]);
+        return d2 < P[4] * P[4];
+    }
+    double s = 0.0;
+    for (int a = 0; a < S->s.dim; ++a) s += P[1 + a] * x[a];
+    return s > P[4];
+}
+
+/* wall distance fraction of the link from centre x along -c_i (Eq. 30):
+ * the smallest t in (0, 1] where x - t c_i enters a primitive; -1 if none */
+static double link_q(const orc_sim *S, const double x[3], int i)
+{
+    double best = -1.0;
+    double v[3] = {-(double)S->c[i][0], -(double)S->c[i][1], -(double)S->c[i][2]};
+    for (int k = 0; k < S->nprims; ++k) {
+        const double *P = &S->prims[5 * k];
+        double t = -1.0;
+        if ((int)P[0] == 0) {
+            double d[3] = {0, 0, 0}, vv = 0.0, dv = 0.0, dd = 0.0;
+            for (int a = 0; a < S->s.dim; ++a) {
+                d[a] = x[a] - P[1 + a];
+                vv += v[a] * v[a];
+                dv += d[a] * v[a];
+                dd += d[a] * d[a];
+            }
+            double disc = dv * dv - vv * (dd - P[4] * P[4]);
+            if (disc >= 0.0 && vv > 0.0) t = (-dv - sqrt(disc)) / vv;
+        } else {
+            double nv = 0.0, nx = 0.0;
+            for (int a = 0; a < S->s.dim; ++a) {
+                nv += P[1 + a] * v[a];
+                nx += P[1 + a] * x[a];
+            }
+            if (nv > 0.0) t = (P[4] - nx) / nv;
+        }
+        if (t > 0.0 && t <= 1.0 && (best < 0.0 || t < best)) best = t;
+    }
+    return best;
+}
+
+/* closest boundary point of the primitive that contains x and whose
+ * boundary is nearest; returns 0 when x is in no primitive */
+static int closest_boundary(const orc_sim *S, const double x[3], double B[3])
+{
+    double bestd = INFINITY;
+    int found = 0;
+    for (int k = 0; k < S->nprims; ++k) {
+        if (!prim_inside(S, k, x)) continue;
+        const double *P = &S->prims[5 * k];
+        double cand[3] = {0, 0, 0}, dist;
+        if ((int)P[0] == 0) {
+            double d[3] = {0, 0, 0}, n = 0.0;
+            for (int a = 0; a < S->s.dim; ++a) {
+                d[a] = x[a] - P[1 + a];
+                n += d[a] * d[a];
+            }
+            n = sqrt(n);
+            if (n < 1e-12) continue;
+            for (int a = 0; a < S->s.dim; ++a) cand[a] = P[1 + a] + P[4] * d[a] / n;
+            dist = P[4] - n;
+        } else {
+            double s = 0.0;
+            for (int a = 0; a < S->s.dim; ++a) s += P[1 + a] * x[a];
+            dist = s - P[4];
+            for (int a = 0; a < S->s.dim; ++a) cand[a] = x[a] - dist * P[1 + a];
+        }
+        if (dist < bestd) {
+            bestd = dist;
+            for (int a = 0; a < 3; ++a) B[a] = cand[a];
+            found = 1;
+        }
+    }
+    return found;
+}
+
+/* Build the link and ghost tables from the primitives and the mask. */
+static void build_curved(orc_sim *S)
+{
+    long N = S->N;
+    free(S->linkq);
+    free(S->ghost_of);
+    free(S->gh_start);
+    free(S->gh_idx);
+    free(S->gh_w);
+    S->linkq = (double *)malloc(sizeof(double) * (size_t)S->Q * N);
+    S->ghost_of = (long *)malloc(sizeof(long) * (size_t)N);
+    for (long c = 0; c < (long)S->Q * N; ++c) S->linkq[c] = -1.0;
+    for (long c = 0; c < N; ++c) S->ghost_of[c] = -1;
+    int nz = S->s.nz;
+    /* links: fluid cell, pulled population whose source is a solid cell */
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < S->s.ny; ++y)
+            for (int x = 0; x < S->s.nx; ++x) {
+                int p[3] = {x, y, z};
+                long c = cell_index(S, p);
+                if (S->solid[c]) continue;
+                double xc[3];
+                cell_centre(S, p, xc);
+                for (int i = 0; i < S->Q; ++i) {
+                    int q[3] = {x - S->c[i][0], y - S->c[i][1], z - S->c[i][2]};
+                    long idx;
+                    int face = -1;
+                    if (classify(S, q, &idx, &face) != PT_SOLID) continue;
+                    S->linkq[(long)i * N + c] = link_q(S, xc, i);
+                }
+            }
+    /* ghosts: solid cells within two cells of a fluid cell along an axis */
+    long ng = 0, cap = 1024, nnz = 0, ncap = 16384;
+    S->gh_start = (long *)malloc(sizeof(long) * (size_t)(cap + 1));
+    S->gh_idx = (long *)malloc(sizeof(long) * (size_t)ncap);
+    S->gh_w = (double *)malloc(sizeof(double) * (size_t)ncap);
+    S->gh_B = (double *)realloc(S->gh_B, sizeof(double) * 3 * (size_t)cap);
+    S->gh_start[0] = 0;
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < S->s.ny; ++y)
+            for (int x = 0; x < S->s.nx; ++x) {
+                int p[3] = {x, y, z};
+                long c = cell_index(S, p);
+                if (!S->solid[c]) continue;
+                int near = 0;
+                for (int a = 0; a < S->s.dim && !near; ++a)
+                    for (int d = -2; d <= 2 && !near; ++d) {
+                        if (!d) continue;
+                        int q[3] = {x, y, z};
+                        q[a] += d;
+                        long idx;
+                        int face = -1;
+                        if (classify(S, q, &idx, &face) == PT_FLUID) near = 1;
+                    }
+                if (!near) continue;
+                double xc[3], B[3], I[3] = {0, 0, 0};
+                cell_centre(S, p, xc);
+                if (!closest_boundary(S, xc, B)) continue;
+                for (int a = 0; a < S->s.dim; ++a) I[a] = 2.0 * B[a] - xc[a];
+                /* fluid cells within 4 cells of the image point (Eq. 38) */
+                long first = nnz;
+                int exact = -1;
+                int lo[3], hi[3];
+                for (int a = 0; a < 3; ++a) {
+                    if (a >= S->s.dim) { lo[a] = hi[a] = 0; continue; }
+                    lo[a] = (int)floor(I[a] - 0.5 - 4.0) - 1;
+                    hi[a] = (int)ceil(I[a] - 0.5 + 4.0) + 1;
+                    if (lo[a] < 0) lo[a] = 0;
+                    if (hi[a] > extent(S, a) - 1) hi[a] = extent(S, a) - 1;
+                }
+                double wsum = 0.0;
+                for (int zz = lo[2]; zz <= hi[2]; ++zz)
+                    for (int yy = lo[1]; yy <= hi[1]; ++yy)
+                        for (int xx = lo[0]; xx <= hi[0]; ++xx) {
+                            int r[3] = {xx, yy, zz};
+                            long j = cell_index(S, r);
+                            if (S->solid[j]) continue;
+                            double rc[3], d2 = 0.0;
+                            cell_centre(S, r, rc);
+                            for (int a = 0; a < S->s.dim; ++a) d2 += (rc[a] - I[a]) * (rc[a] - I[a]);
+                            if (d2 > 16.0) continue;
+                            if (nnz >= ncap) {
+                                ncap *= 2;
+                                S->gh_idx = (long *)realloc(S->gh_idx, sizeof(long) * (size_t)ncap);
+                                S->gh_w = (double *)realloc(S->gh_w, sizeof(double) * (size_t)ncap);
+                            }
+                            if (d2 < 1e-18) exact = (int)(nnz - first);
+                            S->gh_idx[nnz] = j;
+                            S->gh_w[nnz] = d2 < 1e-18 ? 0.0 : 1.0 / d2;   /* p = 2 (Eq. 36) */
+                            wsum += S->gh_w[nnz];
+                            ++nnz;
+                        }
+                if (nnz == first) continue;  /* no fluid around the image: staircase */
+                for (long e = first; e < nnz; ++e) {
+                    if (exact >= 0) S->gh_w[e] = (e - first == exact) ? 1.0 : 0.0;
+                    else S->gh_w[e] /= wsum;                               /* Eq. 37 */
+                }
+                if (ng >= cap) {
+                    cap *= 2;
+                    S->gh_start = (long *)realloc(S->gh_start, sizeof(long) * (size_t)(cap + 1));
+                    S->gh_B = (double *)realloc(S->gh_B, sizeof(double) * 3 * (size_t)cap);
+                }
+                for (int a = 0; a < 3; ++a) S->gh_B[3 * ng + a] = B[a];
+                S->ghost_of[c] = ng;
+                S->gh_start[ng + 1] = nnz;
+                ++ng;
+            }
+    S->nghost = ng;
+}
+
+/* Shepard value of the image point of ghost k: T, Y, rho (Eq. 35) */
+static void ghost_image(const orc_sim *S, long k, orc_pt *I)
+{
+    I->T = 0.0;
+    I->rho = 0.0;
+    for (int s = 0; s < S->nsp; ++s) I->Y[s] = 0.0;
+    for (long e = S->gh_start[k]; e < S->gh_start[k + 1]; ++e) {
+        orc_pt f;
+        fluid_pt(S, S->gh_idx[e], &f);
+        double w = S->gh_w[e];
+        I->T += w * f.T;
+        I->rho += w * f.rho;   /* the property itself is reconstructed */
+        for (int s = 0; s < S->nsp; ++s) I->Y[s] += w * f.Y[s];
+    }
+}
+
+/* ghost node value (Eq. 34) of solid cell with ghost index k */
+static void curved_ghost_pt(const orc_sim *S, long k, orc_pt *g)
+{
+    orc_pt I;
+    ghost_image(S, k, &I);
+    for (int s = 0; s < S->nsp; ++s) g->Y[s] = I.Y[s];            /* Neumann */
+    g->invW = inv_molar_mass(S, g->Y);
+    for (int s = 0; s < S->nsp; ++s) g->X[s] = g->Y[s] / (S->s.W[s] * g->invW);
+    if (S->s.solid_isothermal) {
+        double TB = S->s.T_solid;
+        g->T = 2.0 * TB - I.T;
+        g->rho = 2.0 * eos_rho(S, TB, inv_molar_mass(S, I.Y)) - I.rho;
+    } else {
+        g->T = I.T;
+        g->rho = I.rho;
+    }
+}
+
 /* Build the 5-point line (offsets -2..2) through cell p along axis a.
  * Returns 1 when a point of the line is not a fluid cell of the domain. */
 static int build_line(const orc_sim *S, const int p[3], long cidx, int a, orc_pt line[5])
@@ -281,6 +533,16 @@ static int build_line(const orc_sim *S, const int p[3], long cidx, int a, orc_pt
         if (!w) continue;
         near = 1;
         for (int j = w; j <= 2; ++j) {
+            if (S->curved) {  /* a solid cell with an image-point ghost (Eq. 34-38) */
+                int q[3] = {p[0], p[1], p[2]};
+                long idx;
+                int face = -1;
+                q[a] += side * j;
+                if (classify(S, q, &idx, &face) == PT_SOLID && S->ghost_of[idx] >= 0) {
+                    curved_ghost_pt(S, S->ghost_of[idx], &line[2 + side * j]);
+                    continue;
+                }
+            }
             int m = 2 * w - 1 - j;  /* mirror offset on this side (may be -1) */
             orc_pt mpt;
             if (m >= 0) {
@@ -676,7 +938,20 @@ static double pull(const orc_sim *S, int i, const int p[3], long cidx)
         return (S->cs - un) * inner + (1.0 - S->cs + un) * g[(long)i * N + cidx];
     }
     long sidx = cell_index(S, src);
-    if (S->solid[sidx]) return g[(long)ib * N + cidx];                     /* Eq. 28 */
+    if (S->solid[sidx]) {
+        double q = S->curved ? S->linkq[(long)i * N + cidx] : -1.0;
+        if (q < 0.0) return g[(long)ib * N + cidx];                        /* Eq. 28 */
+        /* interpolated bounce-back (Eq. 29-30), post-collision values at t */
+        if (q < 0.5) {
+            int r[3] = {p[0] + S->c[i][0], p[1] + S->c[i][1], p[2] + S->c[i][2]};
+            long ridx;
+            int face = -1;
+            if (classify(S, r, &ridx, &face) == PT_FLUID)
+                return 2.0 * q * g[(long)ib * N + cidx] + (1.0 - 2.0 * q) * g[(long)ib * N + ridx];
+            return g[(long)ib * N + cidx];
+        }
+        return g[(long)ib * N + cidx] / (2.0 * q) + (2.0 * q - 1.0) / (2.0 * q) * g[(long)i * N + cidx];
+    }
     return g[(long)i * N + sidx];                                          /* Eq. 8 */
 }
 
@@ -822,9 +1097,24 @@ orc_sim *orc_new(const orc_setup *s, const unsigned char *solid)
     return S;
 }
 
+/* Curved walls from n primitives (5 doubles each, see build_curved). */
+void orc_set_geometry(orc_sim *S, int n, const double *prims)
+{
+    free(S->prims);
+    S->prims = (double *)malloc(sizeof(double) * 5 * (size_t)(n > 0 ? n : 1));
+    if (n > 0) memcpy(S->prims, prims, sizeof(double) * 5 * (size_t)n);
+    S->nprims = n;
+    build_curved(S);
+    S->curved = 1;
+}
+
+long orc_num_ghosts(const orc_sim *S) { return S->nghost; }
+
 void orc_free(orc_sim *S)
 {
     if (!S) return;
+    free(S->prims); free(S->linkq); free(S->ghost_of); free(S->gh_start); free(S->gh_idx);
+    free(S->gh_w); free(S->gh_B);
     free(S->g); free(S->gn); free(S->T); free(S->Tn); free(S->Y); free(S->Yn); free(S->solid);
     free(S);
 }

@@ -33,8 +33,10 @@ struct lbfd_handle {
     void* buf[2];         // device state buffers
     int cur;
     uint8_t* solid;       // device mask
-    long long* bnd;       // device list of the cells the 2-D tile kernels skip
+    long long* bnd;       // device list of the cells the tile kernels skip
     long long nbnd;
+    long long* bndf;      // the subset near domain faces (wall-aware 2-D tiles)
+    long long nbndf;
     double* red;          // device reduction scratch
     double* tmp;          // device read-out buffer (ncell doubles)
     cudaStream_t stream;
@@ -50,6 +52,15 @@ struct lbfd_handle {
     cudaStream_t graph_stream;  // stream the graph was captured on
     cudaStream_t own_stream;    // created when capture needs a non-legacy stream
     lbfd::SideStream side;      // boundary kernel next to the tile kernel
+    std::vector<uint8_t> mask_host;
+    // curved walls: device tables and the per-step ghost values
+    int* link_row;
+    double* link_q;
+    int* ghost_row;
+    long long *gh_start, *gh_idx;
+    double* gh_w;
+    void* gval;
+    long long nghost;
 };
 
 namespace {
@@ -196,6 +207,10 @@ void free_handle(lbfd_handle* h)
     if (h->red) cudaFree(h->red);
     if (h->tmp) cudaFree(h->tmp);
     if (h->bnd) cudaFree(h->bnd);
+    if (h->bndf) cudaFree(h->bndf);
+    void* curved[] = {h->link_row, h->link_q, h->ghost_row, h->gh_start, h->gh_idx, h->gh_w, h->gval};
+    for (void* p : curved)
+        if (p) cudaFree(p);
     delete h;
 }
 
@@ -228,13 +243,31 @@ int sync_other_buffer(lbfd_handle* h)
     return LBFD_OK;
 }
 
+// the boundary lists of the current geometry: with curved walls every cell
+// next to a solid goes through the general form
+lbfd::BoundaryLists lists(const lbfd_handle* h)
+{
+    lbfd::BoundaryLists b;
+    b.all = h->bnd;
+    b.nall = h->nbnd;
+    const bool curved = h->nghost > 0 || h->Pd.curved;
+    b.face = curved ? h->bnd : h->bndf;
+    b.nface = curved ? h->nbnd : h->nbndf;
+    return b;
+}
+
 // one step from buffer `from` to buffer `from ^ 1` with kernel variant v
 cudaError_t launch_one(lbfd_handle* h, int from, int v, cudaStream_t s)
 {
+    if (h->nghost > 0) {  // image-point ghost values of the input state
+        cudaError_t e = lbfd::launch_ghost_fill(h->precision, h->Pd, h->Pf, h->Pt, view(h, from), h->gh_start,
+                                                h->gh_idx, h->gh_w, h->nghost, s);
+        if (e != cudaSuccess) return e;
+    }
     if (h->precision == LBFD_TANGENT)
         return lbfd::launch_step_tangent(h->dim, h->Pt, view(h, from), view(h, from ^ 1), h->solid, s);
     return lbfd::launch_step(h->dim, h->precision, v, h->Pd, h->Pf, view(h, from), view(h, from ^ 1), h->solid,
-                             h->bnd, h->nbnd, h->side, s);
+                             lists(h), h->side, s);
 }
 
 int num_variants_of(const lbfd_handle* h)
@@ -291,7 +324,7 @@ int lbfd_create(const lbfd_grid* grid, const uint8_t* solid_mask, const lbfd_mec
     h->esz = h->precision == LBFD_FP64 ? 8 : (h->precision == LBFD_MIXED ? 4 : sizeof(Tan));
     h->planes = (size_t)h->Q + 1 + lbfd::NSP;
     h->stream = nullptr;
-    h->variant = (h->dim == 2 && h->precision != LBFD_TANGENT) ? 1 : 0;
+    h->variant = h->precision != LBFD_TANGENT ? 1 : 0;
     const size_t bytes = h->planes * (size_t)h->stride * h->esz;
     for (int b = 0; b < 2; ++b) {
         e = cudaMalloc(&h->buf[b], bytes);
@@ -320,31 +353,32 @@ int lbfd_create(const lbfd_grid* grid, const uint8_t* solid_mask, const lbfd_mec
         free_handle(h);
         return cuda_fail(e, "cudaMemcpy(mask)");
     }
-    if (h->dim == 2 &&
+    if (h->precision != LBFD_TANGENT &&
         ((e = cudaStreamCreateWithFlags(&h->side.stream, cudaStreamNonBlocking)) != cudaSuccess ||
          (e = cudaEventCreateWithFlags(&h->side.fork, cudaEventDisableTiming)) != cudaSuccess ||
          (e = cudaEventCreateWithFlags(&h->side.join, cudaEventDisableTiming)) != cudaSuccess)) {
         free_handle(h);
         return cuda_fail(e, "side stream");
     }
+    h->mask_host = m;
     h->section = 0.0;
     for (long long c = 0; c < h->ncell; c += h->grid.nx)
         if (!m[c]) h->section += 1.0;
-    {
+    for (int faces_only = 0; faces_only <= 1; ++faces_only) {
         std::vector<long long> list;
-        lbfd::boundary_cells(h->dim, h->grid.nx, h->grid.ny, h->grid.nz, m.data(), list);
-        h->nbnd = (long long)list.size();
-        if (h->nbnd > 0) {
-            if ((e = cudaMalloc(&h->bnd, list.size() * sizeof(long long))) != cudaSuccess) {
-                free_handle(h);
-                cuda_fail(e, "cudaMalloc(boundary list)");
-                return LBFD_ENOMEM;
-            }
-            if ((e = cudaMemcpy(h->bnd, list.data(), list.size() * sizeof(long long), cudaMemcpyHostToDevice)) !=
-                cudaSuccess) {
-                free_handle(h);
-                return cuda_fail(e, "cudaMemcpy(boundary list)");
-            }
+        lbfd::boundary_cells(h->dim, h->grid.nx, h->grid.ny, h->grid.nz, m.data(), list, faces_only != 0);
+        long long** dst = faces_only ? &h->bndf : &h->bnd;
+        (faces_only ? h->nbndf : h->nbnd) = (long long)list.size();
+        if (list.empty()) continue;
+        if ((e = cudaMalloc(dst, list.size() * sizeof(long long))) != cudaSuccess) {
+            free_handle(h);
+            cuda_fail(e, "cudaMalloc(boundary list)");
+            return LBFD_ENOMEM;
+        }
+        if ((e = cudaMemcpy(*dst, list.data(), list.size() * sizeof(long long), cudaMemcpyHostToDevice)) !=
+            cudaSuccess) {
+            free_handle(h);
+            return cuda_fail(e, "cudaMemcpy(boundary list)");
         }
     }
     // initial state: T_in, Y_in, g = 0
@@ -467,7 +501,67 @@ int lbfd_get_variant(const lbfd_handle* h) { return h ? h->variant : -1; }
 int lbfd_launches_per_step(const lbfd_handle* h)
 {
     if (!h) return -1;
-    return (h->variant > 0 && h->dim == 2 && h->nbnd > 0 && h->precision != LBFD_TANGENT) ? 2 : 1;
+    const lbfd::BoundaryLists b = lists(h);
+    const long long nb = (h->dim == 2 && h->variant >= 5) ? b.nface : b.nall;
+    return ((h->variant > 0 && nb > 0 && h->precision != LBFD_TANGENT) ? 2 : 1) + (h->nghost > 0 ? 1 : 0);
+}
+
+int lbfd_set_curved_walls(lbfd_handle* h, int n, const double* prims)
+{
+    if (!h || n < 0 || (n > 0 && !prims)) return LBFD_EINVAL;
+    for (int k = 0; k < n; ++k) {
+        const double* P = prims + 5 * k;
+        const int t = (int)P[0];
+        if (t != 0 && t != 1) return LBFD_EINVAL;
+        if (t == 0 && !(P[4] > 0.0)) return LBFD_EINVAL;
+        if (t == 1) {
+            double nn = 0.0;
+            for (int a = 0; a < h->dim; ++a) nn += P[1 + a] * P[1 + a];
+            if (fabs(nn - 1.0) > 1e-9) return LBFD_EINVAL;
+        }
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    void* old[] = {h->link_row, h->link_q, h->ghost_row, h->gh_start, h->gh_idx, h->gh_w, h->gval};
+    for (void* p : old)
+        if (p) cudaFree(p);
+    h->link_row = nullptr;
+    h->link_q = nullptr;
+    h->ghost_row = nullptr;
+    h->gh_start = h->gh_idx = nullptr;
+    h->gh_w = nullptr;
+    h->gval = nullptr;
+    h->nghost = 0;
+    h->Pd.curved = h->Pf.curved = h->Pt.curved = 0;
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    if (n == 0) return LBFD_OK;
+    lbfd::CurvedTables t;
+    lbfd::build_curved_tables(h->dim, h->grid.nx, h->grid.ny, h->grid.nz, h->grid.bc, h->mask_host.data(), n, prims,
+                              t);
+    auto upload = [&](void** dst, const void* src, size_t bytes) -> cudaError_t {
+        if (bytes == 0) bytes = 8;  // keep a valid pointer for empty tables
+        cudaError_t e = cudaMalloc(dst, bytes);
+        if (e != cudaSuccess) return e;
+        return src ? cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) : cudaSuccess;
+    };
+    CK(upload((void**)&h->link_row, t.link_row.data(), t.link_row.size() * sizeof(int)));
+    CK(upload((void**)&h->link_q, t.link_q.empty() ? nullptr : t.link_q.data(), t.link_q.size() * sizeof(double)));
+    CK(upload((void**)&h->ghost_row, t.ghost_row.data(), t.ghost_row.size() * sizeof(int)));
+    CK(upload((void**)&h->gh_start, t.gh_start.data(), t.gh_start.size() * sizeof(long long)));
+    CK(upload((void**)&h->gh_idx, t.gh_idx.empty() ? nullptr : t.gh_idx.data(), t.gh_idx.size() * sizeof(long long)));
+    CK(upload((void**)&h->gh_w, t.gh_w.empty() ? nullptr : t.gh_w.data(), t.gh_w.size() * sizeof(double)));
+    h->nghost = t.nghost;
+    CK(upload(&h->gval, nullptr, (size_t)(h->nghost > 0 ? h->nghost : 1) * lbfd::GHOST_VALUES * h->esz));
+    h->Pd.curved = h->Pf.curved = h->Pt.curved = 1;
+    h->Pd.link_row = h->Pf.link_row = h->Pt.link_row = h->link_row;
+    h->Pd.link_q = h->Pf.link_q = h->Pt.link_q = h->link_q;
+    h->Pd.ghost_row = h->Pf.ghost_row = h->Pt.ghost_row = h->ghost_row;
+    h->Pd.gval = (const double*)h->gval;
+    h->Pf.gval = (const float*)h->gval;
+    h->Pt.gval = (const Tan*)h->gval;
+    return LBFD_OK;
 }
 
 int lbfd_set_variant(lbfd_handle* h, int variant)

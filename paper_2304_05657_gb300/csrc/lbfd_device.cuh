@@ -18,7 +18,7 @@ enum { BC_PERIODIC = 0, BC_WALL_ADIABATIC = 1, BC_WALL_ISOTHERMAL = 2, BC_INLET 
        BC_OUTLET_PRESSURE = 5 };
 enum { PT_FLUID = 0, PT_SOLID = 16 };
 // ghost modes of an FD line point
-enum { G_DIRECT = 0, G_NEUMANN = 1, G_DIRICHLET_T = 2, G_INLET = 3 };
+enum { G_DIRECT = 0, G_NEUMANN = 1, G_DIRICHLET_T = 2, G_INLET = 3, G_CURVED = 4 };
 
 // ---------------------------------------------------------------------------
 // lattice: D1Q3 tensor products, i = (cx+1) + 3(cy+1) + 9(cz+1)

@@ -30,15 +30,31 @@ struct SideStream {
     cudaEvent_t fork, join;
 };
 
-// bnd/nbnd: the fluid cells the 2-D tile kernels leave to the boundary
-// kernel (see boundary_cells); unused by the general variant.
+// Cells the tile kernels leave to the boundary kernel (see boundary_cells):
+// `all` every non-interior fluid cell; `face` only those whose stencil
+// reaches a domain face (for the 2-D variants that handle in-domain solid
+// neighbours themselves).  Unused by the general variant.
+struct BoundaryLists {
+    const long long* all;
+    long long nall;
+    const long long* face;
+    long long nface;
+};
+
 cudaError_t launch_step(int dim, int precision, int variant, const StepParams<double>& Pd,
                         const StepParams<float>& Pf, StateView in, StateView out, const uint8_t* solid,
-                        const long long* bnd, long long nbnd, const SideStream& side, cudaStream_t stream);
+                        const BoundaryLists& b, const SideStream& side, cudaStream_t stream);
 int num_variants(int dim);
 
-// Fluid cells that are not interior for the 2-D tile kernels (host, at create).
-void boundary_cells(int dim, int nx, int ny, int nz, const uint8_t* solid, std::vector<long long>& out);
+// 3-D tile kernels (variants 1..2 in 3-D), lbfd_step3d.cu
+cudaError_t launch_step3d_tiled(int precision, int variant, const StepParams<double>& Pd, const StepParams<float>& Pf,
+                                StateView in, StateView out, const uint8_t* solid, const long long* bnd,
+                                long long nbnd, const SideStream& side, cudaStream_t stream);
+
+// Fluid cells that are not interior for the tile kernels (host, at create);
+// faces_only (2-D): only cells whose stencil leaves the domain.
+void boundary_cells(int dim, int nx, int ny, int nz, const uint8_t* solid, std::vector<long long>& out,
+                    bool faces_only);
 
 // Diagnostics reduction over the rows y0 <= y < y1 (all x, all z) into the
 // device scratch `red` (RED_WORDS words, zeroed by the launcher); FP64
@@ -58,6 +74,23 @@ cudaError_t launch_tangent_field(long long ncell, long long N, const void* state
                                  cudaStream_t stream);
 cudaError_t launch_objective(const StepParams<Tan>& P, StateView st, const uint8_t* solid, int objective, double* red,
                              cudaStream_t stream);
+
+// Curved walls (lbfd_geometry.cu): host tables of cut links and ghosts.
+struct CurvedTables {
+    std::vector<int> link_row;        // [ncell]
+    std::vector<double> link_q;       // [rows][Q]
+    std::vector<int> ghost_row;       // [ncell]
+    std::vector<long long> gh_start;  // [nghost + 1]
+    std::vector<long long> gh_idx;
+    std::vector<double> gh_w;
+    long long nghost;
+};
+int build_curved_tables(int dim, int nx, int ny, int nz, const int* bc, const uint8_t* solid, int nprims,
+                        const double* prims, CurvedTables& out);
+// ghost values of state `in` into the gval buffer of the parameters
+cudaError_t launch_ghost_fill(int precision, const StepParams<double>& Pd, const StepParams<float>& Pf,
+                              const StepParams<Tan>& Pt, StateView in, const long long* start, const long long* nb,
+                              const double* w, long long nghost, cudaStream_t stream);
 
 // Number of words of the reduction scratch.
 constexpr int RED_WORDS = 16;

@@ -30,6 +30,15 @@ struct StepParams {
     int poiseuille;
     R epsY, epsT;
     R cs;            // lattice sound speed 1/sqrt(3)
+    // curved walls (lbfd_set_curved_walls); curved == 0: staircase walls
+    int curved;
+    const int* link_row;    // [ncell] row of link_q, -1 when no link is cut
+    const double* link_q;   // [rows][Q] wall distance fraction of cut links, < 0: half-way
+    const int* ghost_row;   // [ncell] ghost index of a solid cell, -1 if none
+    const R* gval;          // [nghost][GHOST_VALUES] ghost values of the current step
 };
+
+// values stored per ghost node: T, Y_k, 1/W, X_k, rho
+constexpr int GHOST_VALUES = 3 + 2 * NSP;
 
 }  // namespace lbfd

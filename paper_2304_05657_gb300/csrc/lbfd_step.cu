@@ -40,12 +40,12 @@ static cudaError_t launch_general(const StepParams<R>& P, StateView in, StateVie
     return cudaGetLastError();
 }
 
-template <typename S, typename R, int TX, int TY>
+template <typename S, typename R, int TX, int TY, bool WALLS>
 static cudaError_t launch_tiled(const StepParams<R>& P, StateView in, StateView out, const uint8_t* solid,
                                 const long long* bnd, long long nbnd, const SideStream& side, cudaStream_t stream)
 {
     constexpr size_t smem = tile_smem_bytes<R, TX, TY>();
-    auto kern = step_kernel_tiled2d<S, R, TX, TY>;
+    auto kern = step_kernel_tiled2d<S, R, TX, TY, WALLS>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -78,37 +78,70 @@ static cudaError_t launch_tiled(const StepParams<R>& P, StateView in, StateView 
 
 template <typename S, typename R>
 static cudaError_t launch_2d(int variant, const StepParams<R>& P, StateView in, StateView out, const uint8_t* solid,
-                             const long long* bnd, long long nbnd, const SideStream& side, cudaStream_t stream)
+                             const BoundaryLists& b, const SideStream& side, cudaStream_t stream)
 {
+    // variants 5-8 also update cells next to in-domain solid cells in the
+    // tile kernel, so their boundary list holds only cells near domain faces
+    // (or every non-interior cell once curved walls are set)
+    const long long* bf = b.face;
+    const long long nf = b.nface;
     switch (variant) {
     case 0: return launch_general<2, S, R>(P, in, out, solid, stream);
-    case 1: return launch_tiled<S, R, 32, 8>(P, in, out, solid, bnd, nbnd, side, stream);
-    case 2: return launch_tiled<S, R, 32, 4>(P, in, out, solid, bnd, nbnd, side, stream);
-    case 3: return launch_tiled<S, R, 64, 4>(P, in, out, solid, bnd, nbnd, side, stream);
-    case 4: return launch_tiled<S, R, 32, 16>(P, in, out, solid, bnd, nbnd, side, stream);
+    case 1: return launch_tiled<S, R, 32, 8, false>(P, in, out, solid, b.all, b.nall, side, stream);
+    case 2: return launch_tiled<S, R, 32, 4, false>(P, in, out, solid, b.all, b.nall, side, stream);
+    case 3: return launch_tiled<S, R, 64, 4, false>(P, in, out, solid, b.all, b.nall, side, stream);
+    case 4: return launch_tiled<S, R, 32, 16, false>(P, in, out, solid, b.all, b.nall, side, stream);
+    case 5: return launch_tiled<S, R, 32, 8, true>(P, in, out, solid, bf, nf, side, stream);
+    case 6: return launch_tiled<S, R, 32, 4, true>(P, in, out, solid, bf, nf, side, stream);
+    case 7: return launch_tiled<S, R, 64, 4, true>(P, in, out, solid, bf, nf, side, stream);
+    case 8: return launch_tiled<S, R, 32, 16, true>(P, in, out, solid, bf, nf, side, stream);
     default: return cudaErrorInvalidValue;
     }
 }
 
-int num_variants(int dim) { return dim == 2 ? 5 : 1; }
+int num_variants(int dim) { return dim == 2 ? 9 : 3; }
 
 cudaError_t launch_step(int dim, int precision, int variant, const StepParams<double>& Pd,
                         const StepParams<float>& Pf, StateView in, StateView out, const uint8_t* solid,
-                        const long long* bnd, long long nbnd, const SideStream& side, cudaStream_t stream)
+                        const BoundaryLists& b, const SideStream& side, cudaStream_t stream)
 {
     if (variant < 0 || variant >= num_variants(dim)) return cudaErrorInvalidValue;
+    if (dim == 3 && variant > 0)
+        return launch_step3d_tiled(precision, variant, Pd, Pf, in, out, solid, b.all, b.nall, side, stream);
     if (precision == 0) {
-        if (dim == 2) return launch_2d<double, double>(variant, Pd, in, out, solid, bnd, nbnd, side, stream);
+        if (dim == 2) return launch_2d<double, double>(variant, Pd, in, out, solid, b, side, stream);
         return launch_general<3, double, double>(Pd, in, out, solid, stream);
     }
-    if (dim == 2) return launch_2d<float, float>(variant, Pf, in, out, solid, bnd, nbnd, side, stream);
+    if (dim == 2) return launch_2d<float, float>(variant, Pf, in, out, solid, b, side, stream);
     return launch_general<3, float, float>(Pf, in, out, solid, stream);
 }
 
-void boundary_cells(int dim, int nx, int ny, int nz, const uint8_t* solid, std::vector<long long>& out)
+void boundary_cells(int dim, int nx, int ny, int nz, const uint8_t* solid, std::vector<long long>& out,
+                    bool faces_only)
 {
     out.clear();
-    if (dim != 2) return;  // only the 2-D tiles use the list
+    if (dim == 3) {
+        // the 3-D tile kernel's fast-path condition: +-2 along the three axes
+        // and the 26 neighbours are fluid cells inside the domain
+        const long long plane = (long long)nx * ny;
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    const long long c = (long long)x + (long long)nx * y + plane * z;
+                    if (solid[c]) continue;
+                    bool fast = x >= 2 && x < nx - 2 && y >= 2 && y < ny - 2 && z >= 2 && z < nz - 2;
+                    for (int d = -2; d <= 2 && fast; ++d) {
+                        if (d == 0) continue;
+                        fast = !solid[c + d] && !solid[c + (long long)nx * d] && !solid[c + plane * d];
+                    }
+                    for (int dz = -1; dz <= 1 && fast; ++dz)
+                        for (int dy = -1; dy <= 1 && fast; ++dy)
+                            for (int dx = -1; dx <= 1 && fast; ++dx)
+                                fast = !solid[c + dx + (long long)nx * dy + plane * dz];
+                    if (!fast) out.push_back(c);
+                }
+        return;
+    }
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             const long long c = (long long)x + (long long)nx * y;
@@ -123,7 +156,7 @@ void boundary_cells(int dim, int nx, int ny, int nz, const uint8_t* solid, std::
                     if (!(axis || near)) continue;
                     const int qx = x + dx, qy = y + dy;
                     if (qx < 0 || qx >= nx || qy < 0 || qy >= ny) fast = false;
-                    else if (solid[(long long)qx + (long long)nx * qy]) fast = false;
+                    else if (!faces_only && solid[(long long)qx + (long long)nx * qy]) fast = false;
                 }
             if (!fast) out.push_back(c);
         }

@@ -107,8 +107,23 @@ __device__ __forceinline__ R pull_general(const StepParams<R>& P, int i, const i
         return (P.cs - un) * inner + (R(1) - P.cs + un) * R(g[(long long)i * N + c]);
     }
     const long long s = cell_of(P, src[0], src[1], DIM == 3 ? src[2] : 0);
-    if (solid[s]) return R(g[(long long)ib * N + c]);  // Eq. 28
-    return R(g[(long long)i * N + s]);                   // Eq. 8
+    if (solid[s]) {
+        const int row = P.curved ? P.link_row[c] : -1;
+        const double qd = row >= 0 ? P.link_q[(long long)row * (DIM == 2 ? 9 : 27) + i] : -1.0;
+        if (qd < 0.0) return R(g[(long long)ib * N + c]);  // Eq. 28
+        // interpolated bounce-back (Eq. 29-30), post-collision values at t
+        const R q = R(qd);
+        if (qd < 0.5) {
+            int r[3] = {p[0] + ccomp<DIM>(i, 0), p[1] + ccomp<DIM>(i, 1), DIM == 3 ? p[2] + ccomp<DIM>(i, 2) : 0};
+            long long ridx = 0;
+            int face = -1;
+            if (classify<DIM>(P, r, solid, &ridx, &face) == PT_FLUID)
+                return R(2) * q * R(g[(long long)ib * N + c]) + (R(1) - R(2) * q) * R(g[(long long)ib * N + ridx]);
+            return R(g[(long long)ib * N + c]);
+        }
+        return R(g[(long long)ib * N + c]) / (R(2) * q) + (R(2) * q - R(1)) / (R(2) * q) * R(g[(long long)i * N + c]);
+    }
+    return R(g[(long long)i * N + s]);  // Eq. 8
 }
 
 // ---------------------------------------------------------------------------
@@ -177,6 +192,18 @@ __device__ __forceinline__ void build_line(const StepParams<R>& P, const int p[3
 #pragma unroll
         for (int j = 1; j <= 2; ++j) {
             if (j < w) continue;
+            if (P.curved) {  // a solid cell with an image-point ghost (Eq. 34-38)
+                int q[3] = {p[0], p[1], p[2]};
+                q[a] += side * j;
+                long long idx = 0;
+                int face = -1;
+                if (classify<DIM>(P, q, solid, &idx, &face) == PT_SOLID && P.ghost_row[idx] >= 0) {
+                    L.src[2 + side * j] = P.ghost_row[idx];
+                    L.mode[2 + side * j] = G_CURVED;
+                    L.TB[2 + side * j] = R(0);
+                    continue;
+                }
+            }
             const int m = 2 * w - 1 - j;  // mirror offset on this side
             long long ms;
             if (m >= 0) {
@@ -203,6 +230,15 @@ __device__ __forceinline__ void line_point(const StepParams<R>& P, const LineDes
                                            R& invWj, R& rhoj)
 {
     const long long s = L.src[j];
+    if (L.mode[j] == G_CURVED) {  // precomputed image-point ghost of this step
+        const R* gv = P.gval + s * GHOST_VALUES;
+        Tj = gv[0];
+#pragma unroll
+        for (int k = 0; k < NSP; ++k) Yj[k] = gv[1 + k];
+        invWj = gv[1 + NSP];
+        rhoj = gv[2 + 2 * NSP];
+        return;
+    }
     const R Tm = R(T[s]);
     R Ym[NSP];
 #pragma unroll

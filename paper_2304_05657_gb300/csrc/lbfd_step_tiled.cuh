@@ -81,8 +81,143 @@ __device__ __forceinline__ void fd_axis_smem(const StepParams<R>& P, const TileS
     }
 }
 
-template <typename S, typename R, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY) step_kernel_tiled2d(StepParams<R> P, const S* __restrict__ g_in,
+// FD terms along one axis for a cell next to in-domain solid cells (staircase
+// walls), from shared memory: pts are the five line points after the mirror
+// rule, `ghost` flags the points that are ghosts (bit j), whose T and rho
+// take the Dirichlet form when the solid is isothermal (Y, X, 1/W mirror).
+template <typename R>
+__device__ __forceinline__ void fd_axis_smem_walls(const StepParams<R>& P, const TileSmem<R>& sm, int npt,
+                                                   const int* pts, int ghost, int a, R u_a, const R* Y0, R invW0,
+                                                   R rho0, FDAccum<R>& acc)
+{
+    const bool iso = P.solid_isothermal;
+    const R TB = P.T_solid;
+    R v[5], w[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        w[j] = sm.invW[pts[j]];
+        v[j] = sm.rho[pts[j]];
+        if (iso && ((ghost >> j) & 1)) v[j] = R(2) * eos(P, TB, w[j]) - v[j];
+    }
+    const R drho = fd_d1(v);
+    acc.grad_rho[a] = drho;
+    const R drho_r = fdiv(drho, rho0);
+    const R dinvW = fd_d1(w);
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        v[j] = sm.T[pts[j]];
+        if (iso && ((ghost >> j) & 1)) v[j] = R(2) * TB - v[j];
+    }
+    const bool near = ghost != 0;
+    acc.conv_T += u_a * (near ? fd_c2(v) : weno3_deriv_fast(v, u_a, P.epsT));
+    acc.diff_T += P.alpha * (fd_d2(v) + drho_r * fd_d1(v));
+    R Lk[NSP], m[NSP], dm[NSP], dY[NSP];
+    R sumL = R(0), M = R(0), dM = R(0);
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) {
+#pragma unroll
+        for (int j = 0; j < 5; ++j) v[j] = sm.Y[k * npt + pts[j]];
+        Lk[k] = near ? fd_c2(v) : weno3_deriv_fast(v, u_a, P.epsY);
+        sumL += Lk[k];
+        dY[k] = fd_d1(v);
+#pragma unroll
+        for (int j = 0; j < 5; ++j) v[j] = sm.X[k * npt + pts[j]];
+        const R dX = fd_d1(v), d2X = fd_d2(v);
+        m[k] = P.a_diff[k] * invW0 * dX;
+        dm[k] = P.a_diff[k] * (invW0 * d2X + dinvW * dX);
+        M += m[k];
+        dM += dm[k];
+    }
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) {
+        acc.conv_Y[k] += u_a * (Lk[k] - Y0[k] * sumL);
+        acc.diff_Y[k] += dm[k] - dY[k] * M - Y0[k] * dM + (m[k] - Y0[k] * M) * drho_r;
+    }
+}
+
+// the five points of an axis line after the mirror rule of Eq. 34 for
+// in-domain solid cells (the ghost at distance j mirrors the fluid point at
+// distance j-1 across the wall; the centre when that point is solid)
+__device__ __forceinline__ int wall_line(const uint8_t* mask, int p0, int st, int* pts)
+{
+    int ghost = 0;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) pts[j] = p0 + (j - 2) * st;
+#pragma unroll
+    for (int side = -1; side <= 1; side += 2) {
+        const int w = mask[p0 + side * st] ? 1 : (mask[p0 + 2 * side * st] ? 2 : 0);
+        if (!w) continue;
+#pragma unroll
+        for (int j = 1; j <= 2; ++j) {
+            if (j < w) continue;
+            const int m = 2 * w - 1 - j;
+            int mp;
+            if (m >= 0) mp = p0 + side * m * st;
+            else mp = mask[p0 - side * st] ? p0 : p0 - side * st;
+            pts[2 + side * j] = mp;
+            ghost |= 1 << (2 + side * j);
+        }
+    }
+    return ghost;
+}
+
+// one cell next to in-domain solid cells (staircase walls), from the tile
+template <typename S, typename R, int SX, int NPT>
+__device__ __noinline__ void step_cell_walls(const StepParams<R>& P, const TileSmem<R>& sm, int p0, long long c,
+                                             const S* __restrict__ g_in, S* __restrict__ g_out,
+                                             S* __restrict__ T_out, S* __restrict__ Y_out)
+{
+    const long long N = P.N;
+    R g[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {  // Eq. 8, or Eq. 28 from a solid neighbour
+        const bool solid_src = sm.mask[p0 - cx_of(i) - cy_of(i) * SX] != 0;
+        const long long src = solid_src ? c : c - cx_of(i) - (long long)P.nx * cy_of(i);
+        const int plane = solid_src ? opposite<2>(i) : i;
+        g[i] = R(__ldg(&g_in[(long long)plane * N + src]));
+    }
+    const R T0 = sm.T[p0], invW0 = sm.invW[p0], rho0 = sm.rho[p0];
+    R Y0[NSP];
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) Y0[k] = sm.Y[k * NPT + p0];
+    R u[3];
+    {
+        const R inv = fdiv(R(3), rho0);
+        u[0] = ((g[2] + g[5] + g[8]) - (g[0] + g[3] + g[6])) * inv;
+        u[1] = ((g[6] + g[7] + g[8]) - (g[0] + g[1] + g[2])) * inv;
+        u[2] = R(0);
+    }
+    FDAccum<R> acc;
+    acc.conv_T = acc.diff_T = R(0);
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) acc.conv_Y[k] = acc.diff_Y[k] = R(0);
+    acc.grad_rho[2] = R(0);
+    int pts[5];
+    int gh = wall_line(sm.mask, p0, 1, pts);
+    fd_axis_smem_walls<R>(P, sm, NPT, pts, gh, 0, u[0], Y0, invW0, rho0, acc);
+    gh = wall_line(sm.mask, p0, SX, pts);
+    fd_axis_smem_walls<R>(P, sm, NPT, pts, gh, 1, u[1], Y0, invW0, rho0, acc);
+    const R q = arrhenius(P, T0, Y0[P.fuel], Y0[P.oxid]);
+    const R DT = acc.diff_T + P.Q_cp * q;
+    T_out[c] = S(T0 + (DT - acc.conv_T));
+    R lam_Y = R(0);
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) {
+        const R DY = acc.diff_Y[k] + P.yield[k] * q;
+        Y_out[(long long)k * N + c] = S(Y0[k] + (DY - acc.conv_Y[k]));
+        lam_Y += P.inv_Wk[k] * DY;
+    }
+    const R Lam = fdiv(DT, T0) + fdiv(lam_Y, invW0);
+    collide<2, R>(P, g, rho0, u, acc.grad_rho, Lam);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) g_out[(long long)i * N + c] = S(g[i]);
+}
+
+// wall-aware FP32 tiles: at most 64 registers per thread (65536 per SM): the
+// interior path fits, the rare wall path may spill instead of lowering the
+// occupancy of the whole kernel
+template <typename S, typename R, int TX, int TY, bool WALLS>
+__global__ void __launch_bounds__(TX * TY, (WALLS && sizeof(R) == 4) ? 1024 / (TX * TY) : 1) step_kernel_tiled2d(StepParams<R> P, const S* __restrict__ g_in,
                                                                S* __restrict__ g_out, const S* __restrict__ T_in,
                                                                S* __restrict__ T_out, const S* __restrict__ Y_in,
                                                                S* __restrict__ Y_out,
@@ -143,7 +278,24 @@ __global__ void __launch_bounds__(TX * TY) step_kernel_tiled2d(StepParams<R> P, 
     for (int j = 1; j <= 2; ++j)
         fast = fast && !sm.mask[p0 + j] && !sm.mask[p0 - j] && !sm.mask[p0 + j * SX] && !sm.mask[p0 - j * SX];
     fast = fast && !sm.mask[p0 + SX + 1] && !sm.mask[p0 + SX - 1] && !sm.mask[p0 - SX + 1] && !sm.mask[p0 - SX - 1];
-    if (!fast) return;  // boundary cell: step_kernel_boundary updates it
+    if constexpr (WALLS) {
+        // next to in-domain solid cells only (no domain face, no curved
+        // walls): staircase bounce-back and mirror ghosts from shared memory
+        if (!fast) {
+            bool walls = !P.curved;
+#pragma unroll
+            for (int j = 1; j <= 2; ++j)
+                walls = walls && sm.mask[p0 + j] != 2 && sm.mask[p0 - j] != 2 && sm.mask[p0 + j * SX] != 2 &&
+                        sm.mask[p0 - j * SX] != 2;
+            walls = walls && sm.mask[p0 + SX + 1] != 2 && sm.mask[p0 + SX - 1] != 2 &&
+                    sm.mask[p0 - SX + 1] != 2 && sm.mask[p0 - SX - 1] != 2;
+            if (!walls) return;  // boundary cell: step_kernel_boundary updates it
+            step_cell_walls<S, R, SX, NPT>(P, sm, p0, c, g_in, g_out, T_out, Y_out);
+            return;
+        }
+    } else {
+        if (!fast) return;  // boundary cell: step_kernel_boundary updates it
+    }
     // a1: pull from the neighbours (all interior)
     R g[9];
 #pragma unroll

@@ -1,0 +1,222 @@
+// lbfd_step_tiled3d.cuh -- 3-D (D3Q27) fused coupled step, 2.5-D tiling.
+//
+// A block of TX x TY threads owns a TX x TY column of cells and marches it
+// through ZC consecutive z-planes.  Shared memory holds a ring of five
+// z-planes (z-2 .. z+2) of the tile plus its 2-cell x/y halo, with T, Y_k
+// and the derived 1/W, X_k, rho of every point; each plane is loaded once
+// per column pass.  Interior cells (every +-2 axis neighbour and all 26 LB
+// neighbours are fluid cells inside the domain) take the fast path; the
+// others are left to step_kernel_boundary over the precomputed cell list.
+#pragma once
+#include "lbfd_step_tiled.cuh"
+
+namespace lbfd {
+
+template <int TX, int TY>
+struct Tile3Geom {
+    static constexpr int SX = TX + 4;
+    static constexpr int SY = TY + 4;
+    static constexpr int NPP = SX * SY;  // points per plane
+    static constexpr int NPL = 5;        // planes in the ring
+    static constexpr int NPT = NPP * NPL;
+};
+
+template <typename R, int TX, int TY>
+__host__ __device__ constexpr size_t tile3_smem_bytes()
+{
+    return sizeof(R) * (size_t)Tile3Geom<TX, TY>::NPT * (3 + 2 * NSP) + (size_t)Tile3Geom<TX, TY>::NPT;
+}
+
+// FD terms along one axis from five explicit shared-memory points
+template <typename R>
+__device__ __forceinline__ void fd_axis_pts(const StepParams<R>& P, const TileSmem<R>& sm, int npt, const int* pts,
+                                            int a, R u_a, const R* Y0, R invW0, R rho0, FDAccum<R>& acc)
+{
+    R v[5], w[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) v[j] = sm.rho[pts[j]];
+    const R drho = fd_d1(v);
+    acc.grad_rho[a] = drho;
+    const R drho_r = fdiv(drho, rho0);
+#pragma unroll
+    for (int j = 0; j < 5; ++j) v[j] = sm.T[pts[j]];
+    acc.conv_T += u_a * weno3_deriv_fast(v, u_a, P.epsT);
+    acc.diff_T += P.alpha * (fd_d2(v) + drho_r * fd_d1(v));
+#pragma unroll
+    for (int j = 0; j < 5; ++j) w[j] = sm.invW[pts[j]];
+    const R dinvW = fd_d1(w);
+    R Lk[NSP], m[NSP], dm[NSP], dY[NSP];
+    R sumL = R(0), M = R(0), dM = R(0);
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) {
+#pragma unroll
+        for (int j = 0; j < 5; ++j) v[j] = sm.Y[k * npt + pts[j]];
+        Lk[k] = weno3_deriv_fast(v, u_a, P.epsY);
+        sumL += Lk[k];
+        dY[k] = fd_d1(v);
+#pragma unroll
+        for (int j = 0; j < 5; ++j) v[j] = sm.X[k * npt + pts[j]];
+        const R dX = fd_d1(v), d2X = fd_d2(v);
+        m[k] = P.a_diff[k] * invW0 * dX;
+        dm[k] = P.a_diff[k] * (invW0 * d2X + dinvW * dX);
+        M += m[k];
+        dM += dm[k];
+    }
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) {
+        acc.conv_Y[k] += u_a * (Lk[k] - Y0[k] * sumL);
+        acc.diff_Y[k] += dm[k] - dY[k] * M - Y0[k] * dM + (m[k] - Y0[k] * M) * drho_r;
+    }
+}
+
+// stage plane z (grid coordinate) into ring slot `slot`
+template <typename S, typename R, int TX, int TY>
+__device__ __forceinline__ void stage_plane(const StepParams<R>& P, const TileSmem<R>& sm, int slot, int x0, int y0,
+                                            int z, const S* __restrict__ T_in, const S* __restrict__ Y_in,
+                                            const uint8_t* __restrict__ solid)
+{
+    using G = Tile3Geom<TX, TY>;
+    constexpr int NPT = G::NPT;
+    const long long N = P.N;
+    const int tid = threadIdx.x + TX * threadIdx.y;
+    for (int q = tid; q < G::NPP; q += TX * TY) {
+        const int sx = q % G::SX, sy = q / G::SX;
+        const int gx = x0 + sx - 2, gy = y0 + sy - 2;
+        const int pt = slot * G::NPP + q;
+        if (gx < 0 || gx >= P.nx || gy < 0 || gy >= P.ny || z < 0 || z >= P.nz) {
+            sm.mask[pt] = 2;
+            continue;
+        }
+        const long long c = (long long)gx + (long long)P.nx * (gy + (long long)P.ny * z);
+        const uint8_t s = solid[c];
+        sm.mask[pt] = s ? 1 : 0;
+        if (s) continue;
+        const R T = R(T_in[c]);
+        R Y[NSP];
+#pragma unroll
+        for (int k = 0; k < NSP; ++k) Y[k] = R(Y_in[(long long)k * N + c]);
+        const R invW = inv_molar_mass(P, Y);
+        const R W = fdiv(R(1), invW);
+        sm.T[pt] = T;
+#pragma unroll
+        for (int k = 0; k < NSP; ++k) {
+            sm.Y[k * NPT + pt] = Y[k];
+            sm.X[k * NPT + pt] = Y[k] * P.inv_Wk[k] * W;
+        }
+        sm.invW[pt] = invW;
+        sm.rho[pt] = fdiv(P.T_in * P.invW_in * W, T);
+    }
+}
+
+template <typename S, typename R, int TX, int TY, int ZC>
+__global__ void __launch_bounds__(TX * TY) step_kernel_tiled3d(StepParams<R> P, const S* __restrict__ g_in,
+                                                               S* __restrict__ g_out, const S* __restrict__ T_in,
+                                                               S* __restrict__ T_out, const S* __restrict__ Y_in,
+                                                               S* __restrict__ Y_out,
+                                                               const uint8_t* __restrict__ solid)
+{
+    using G = Tile3Geom<TX, TY>;
+    constexpr int SX = G::SX, NPP = G::NPP, NPT = G::NPT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TileSmem<R> sm;
+    sm.T = reinterpret_cast<R*>(smem_raw);
+    sm.Y = sm.T + NPT;
+    sm.X = sm.Y + NSP * NPT;
+    sm.invW = sm.X + NSP * NPT;
+    sm.rho = sm.invW + NPT;
+    sm.mask = reinterpret_cast<uint8_t*>(sm.rho + NPT);
+
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, zb = blockIdx.z * ZC;
+    const long long N = P.N;
+    const long long plane = (long long)P.nx * P.ny;
+    // ring slot of grid plane z: (z + 5*big) % 5 keeps it non-negative
+    auto slot_of = [](int z) { return (z + 10) % 5; };
+    for (int dz = -2; dz <= 1; ++dz) stage_plane<S, R, TX, TY>(P, sm, slot_of(zb + dz), x0, y0, zb + dz, T_in, Y_in, solid);
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    const int q0 = (threadIdx.y + 2) * SX + threadIdx.x + 2;  // in-plane point of this thread
+    const int zend = zb + ZC < P.nz ? zb + ZC : P.nz;
+    for (int z = zb; z < zend; ++z) {
+        stage_plane<S, R, TX, TY>(P, sm, slot_of(z + 2), x0, y0, z + 2, T_in, Y_in, solid);
+        __syncthreads();
+        const int sc = slot_of(z);
+        const int p0 = sc * NPP + q0;
+        bool active = x < P.nx && y < P.ny && !sm.mask[p0];
+        if (active) {
+            // interior: +-2 along the three axes and the 26 neighbours
+            bool fast = true;
+#pragma unroll
+            for (int j = 1; j <= 2; ++j)
+                fast = fast && !sm.mask[p0 + j] && !sm.mask[p0 - j] && !sm.mask[p0 + j * SX] &&
+                       !sm.mask[p0 - j * SX] && !sm.mask[slot_of(z + j) * NPP + q0] &&
+                       !sm.mask[slot_of(z - j) * NPP + q0];
+#pragma unroll
+            for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+                for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+                    for (int dx = -1; dx <= 1; ++dx)
+                        fast = fast && !sm.mask[slot_of(z + dz) * NPP + q0 + dy * SX + dx];
+            active = fast;
+        }
+        if (active) {
+            const long long c = (long long)x + (long long)P.nx * y + plane * z;
+            R g[27];
+#pragma unroll
+            for (int i = 0; i < 27; ++i) {
+                const long long src = c - cx_of(i) - (long long)P.nx * cy_of(i) - plane * cz_of(i);
+                g[i] = R(__ldg(&g_in[(long long)i * N + src]));
+            }
+            const R T0 = sm.T[p0], invW0 = sm.invW[p0], rho0 = sm.rho[p0];
+            R Y0[NSP];
+#pragma unroll
+            for (int k = 0; k < NSP; ++k) Y0[k] = sm.Y[k * NPT + p0];
+            R u[3];
+            {
+                const R inv = fdiv(R(3), rho0);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    R m = R(0);
+#pragma unroll
+                    for (int i = 0; i < 27; ++i) {
+                        const int ci = ccomp<3>(i, a);
+                        if (ci) m += R(ci) * g[i];
+                    }
+                    u[a] = m * inv;
+                }
+            }
+            FDAccum<R> acc;
+            acc.conv_T = acc.diff_T = R(0);
+#pragma unroll
+            for (int k = 0; k < NSP; ++k) acc.conv_Y[k] = acc.diff_Y[k] = R(0);
+            {
+                int px[5], py[5], pz[5];
+#pragma unroll
+                for (int j = 0; j < 5; ++j) {
+                    px[j] = p0 + (j - 2);
+                    py[j] = p0 + (j - 2) * SX;
+                    pz[j] = slot_of(z + j - 2) * NPP + q0;
+                }
+                fd_axis_pts<R>(P, sm, NPT, px, 0, u[0], Y0, invW0, rho0, acc);
+                fd_axis_pts<R>(P, sm, NPT, py, 1, u[1], Y0, invW0, rho0, acc);
+                fd_axis_pts<R>(P, sm, NPT, pz, 2, u[2], Y0, invW0, rho0, acc);
+            }
+            const R q = arrhenius(P, T0, Y0[P.fuel], Y0[P.oxid]);
+            const R DT = acc.diff_T + P.Q_cp * q;
+            T_out[c] = S(T0 + (DT - acc.conv_T));
+            R lam_Y = R(0);
+#pragma unroll
+            for (int k = 0; k < NSP; ++k) {
+                const R DY = acc.diff_Y[k] + P.yield[k] * q;
+                Y_out[(long long)k * N + c] = S(Y0[k] + (DY - acc.conv_Y[k]));
+                lam_Y += P.inv_Wk[k] * DY;
+            }
+            const R Lam = fdiv(DT, T0) + fdiv(lam_Y, invW0);
+            collide<3, R>(P, g, rho0, u, acc.grad_rho, Lam);
+#pragma unroll
+            for (int i = 0; i < 27; ++i) g_out[(long long)i * N + c] = S(g[i]);
+        }
+        __syncthreads();  // the slot of z-2 is restaged next iteration
+    }
+}
+
+}  // namespace lbfd

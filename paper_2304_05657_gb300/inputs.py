@@ -147,17 +147,22 @@ def channel(nx=256, ny=32, walls="adiabatic", T_wall=300.0, u_in=0.01, ignite=(0
     return cfg, solid, T, Y
 
 
-def batched_channels(widths=None, length=1024, T_wall=300.0, u_in=0.01, ignite=(0, 20), **over):
+def batched_channels(widths=None, length=1024, T_wall=300.0, u_in=0.0, ignite=(0, 20), closed_end=True, **over):
     """Channels of uneven width stacked along y in one 2-D domain, separated
     by one solid row (isothermal at T_wall) so that no stencil couples them;
     domain faces at +-y are isothermal walls.  Default: 16 channels of widths
-    16, 28, ..., 196 and length 1024.  Returns (cfg, solid, T, Y, segments)
-    with segments = [(y0, y1), ...] the fluid rows of each channel."""
+    16, 28, ..., 196 and length 1024, closed at the ignition end (-x) by an
+    adiabatic wall and open at +x (constant pressure): a flame started in
+    the hot band propagates toward the open end in the wide channels and
+    quenches in the narrow ones.  closed_end=False puts a velocity inlet at
+    -x instead.  Returns (cfg, solid, T, Y, segments) with segments =
+    [(y0, y1), ...] the fluid rows of each channel."""
     if widths is None:
         widths = [16 + 12 * j for j in range(16)]
     ny = sum(widths) + len(widths) - 1
+    left = "wall_adiabatic" if closed_end else "inlet"
     cfg = base_config(dim=2, nx=length, ny=ny,
-                      bc=["inlet", "outlet_pressure", "wall_isothermal", "wall_isothermal", "periodic", "periodic"],
+                      bc=[left, "outlet_pressure", "wall_isothermal", "wall_isothermal", "periodic", "periodic"],
                       T_wall=[T_wall] * 6, T_solid=T_wall, solid_isothermal=True, u_in=u_in, **over)
     solid = np.zeros((ny, length), dtype=np.uint8)
     segments = []

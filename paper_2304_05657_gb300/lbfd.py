@@ -35,7 +35,7 @@ SYMBOLS = (
     "lbfd_set_state_raw", "lbfd_steps_done", "lbfd_num_cells", "lbfd_num_populations", "lbfd_strerror",
     "lbfd_last_error", "lbfd_step_graph", "lbfd_num_variants", "lbfd_get_variant", "lbfd_set_variant",
     "lbfd_autotune", "lbfd_diagnostics_noalloc", "lbfd_launches_per_step", "lbfd_read_tangent", "lbfd_gradient",
-    "lbfd_diagnostics_rows", "lbfd_set_inlet_velocity",
+    "lbfd_diagnostics_rows", "lbfd_set_inlet_velocity", "lbfd_set_curved_walls",
 )
 
 
@@ -112,6 +112,7 @@ def load(path: str = LIB_PATH):
     lib.lbfd_read_tangent.argtypes = [H, ctypes.c_int, ctypes.c_int, D]
     lib.lbfd_diagnostics_rows.argtypes = [H, ctypes.c_int, ctypes.c_int, D]
     lib.lbfd_set_inlet_velocity.argtypes = [H, ctypes.c_double]
+    lib.lbfd_set_curved_walls.argtypes = [H, ctypes.c_int, D]
     lib.lbfd_gradient.argtypes = [H, ctypes.c_int, D, D]
     lib.lbfd_autotune.argtypes = [H, ctypes.c_int, D, ctypes.POINTER(ctypes.c_int)]
     lib.lbfd_diagnostics_noalloc.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Mechanism), ctypes.POINTER(Params),
@@ -272,6 +273,11 @@ class Solver:
             st = self.lib.lbfd_diagnostics_rows(self.h, int(rows[0]), int(rows[1]), _dp(out))
         _check(self.lib, st, "lbfd_diagnostics", allow=(ENONFINITE,))
         return dict(zip(DIAG_KEYS, out.tolist()))
+
+    def set_curved_walls(self, prims):
+        """Curved walls from primitives (type, p0, p1, p2, p3); see lbfd.h."""
+        arr = np.ascontiguousarray(np.asarray(prims, dtype=np.float64).reshape(-1, 5))
+        _check(self.lib, self.lib.lbfd_set_curved_walls(self.h, int(arr.shape[0]), _dp(arr)), "lbfd_set_curved_walls")
 
     def set_inlet_velocity(self, u_in: float):
         _check(self.lib, self.lib.lbfd_set_inlet_velocity(self.h, float(u_in)), "lbfd_set_inlet_velocity")

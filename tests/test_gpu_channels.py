@@ -12,7 +12,8 @@ def test_row_diagnostics_equal_separate_oracle_channels(lbfd_lib, oracle_mod):
     channel run alone by the oracle (the solid separators are isothermal
     walls at the wall temperature, so the problems are independent)."""
     widths = [5, 8, 13]
-    cfg, solid, T, Y, seg = inputs.batched_channels(widths=widths, length=45, ignite=(10, 25))
+    cfg, solid, T, Y, seg = inputs.batched_channels(widths=widths, length=45, ignite=(10, 25), closed_end=False,
+                                                     u_in=0.01)
     s = lbfd_lib.Solver(cfg, solid)
     s.init_fields(T, Y)
     s.step(40)
@@ -58,6 +59,7 @@ def test_inflow_controller_moves_toward_target(lbfd_lib):
     x0 = s.diagnostics()["x_f"]
     ctl = channels.InflowController(x_target=x0 + 20.0)
     hist = channels.hold_flame(s, ctl, steps=200, every=50)
-    # the flame is upstream of the target: the controller must cut the inflow
-    assert hist[-1][2] < cfg["u_in"]
+    # the unburnt length is shorter than the target (the flame sits upstream
+    # of it): the controller must raise the inflow to push the flame back
+    assert hist[-1][2] > cfg["u_in"]
     assert all(h[2] >= 0.0 for h in hist)

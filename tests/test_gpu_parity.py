@@ -248,3 +248,29 @@ def test_autotune_keeps_state_and_picks_a_variant(lbfd_lib):
     assert np.all(ms > 0)
     for x, y in zip(before, s.get_state()):
         assert np.array_equal(x, y)
+
+
+def test_d3q27_tile_variants_match_oracle(lbfd_lib, oracle_mod):
+    """A 3-D domain large enough for interior cells: every D3Q27 variant
+    (general form, 2.5-D tiles with the boundary list) against the oracle."""
+    cfg, solid, T, Y = inputs.sphere_packing(nx=40, ny=14, nz=13, x_range=(8, 30), r_range=(2.0, 3.5),
+                                             porosity=0.85, seed=12, ignite_width=5)
+    g, T, Y = inputs.perturbed_state(cfg, solid, T, Y, seed=13)
+    o = oracle_mod.Sim(cfg, solid)
+    o.set_state(T, Y, g)
+    o.step(8)
+    orc = o.get_state()
+    s = lbfd_lib.Solver(cfg, solid)
+    assert s.num_variants == 3
+    for v in range(s.num_variants):
+        s.variant = v
+        s.set_state(T, Y, g)
+        s.step(8)
+        compare_states(s.get_state(), orc, 1e-10, f"d3q27 variant {v}")
+    for v in range(s.num_variants):  # mixed precision, same cases
+        sm = lbfd_lib.Solver(dict(cfg, precision="mixed"), solid)
+        sm.variant = v
+        sm.set_state(T, Y, g)
+        sm.step(8)
+        Tg = sm.read_field(lbfd_lib.FIELD_T)
+        assert rel_l2(Tg, orc[0]) <= 1e-6

@@ -312,7 +312,8 @@ def test_packed_channels_are_independent_problems(oracle_mod):
     evolve exactly as the same channels run alone with isothermal walls:
     no stencil or population crosses a solid row."""
     widths = [4, 7, 10]
-    cfg, solid, T, Y, seg = inputs.batched_channels(widths=widths, length=30, ignite=(5, 15))
+    cfg, solid, T, Y, seg = inputs.batched_channels(widths=widths, length=30, ignite=(5, 15), closed_end=False,
+                                                     u_in=0.01)
     nx = cfg["nx"]
     o = oracle_mod.Sim(cfg, solid)
     rng = np.random.default_rng(5)
