@@ -37,6 +37,8 @@ struct lbfd_handle {
     long long nbnd;
     long long* bndf;      // the subset near domain faces (wall-aware 2-D tiles)
     long long nbndf;
+    int* wtiles;          // tiles holding the other boundary cells (2-D)
+    long long nwtiles;
     double* red;          // device reduction scratch
     double* tmp;          // device read-out buffer (ncell doubles)
     cudaStream_t stream;
@@ -138,6 +140,11 @@ void fill_params(const lbfd_handle* h, StepParams<R>& P)
     P.T_solid = (R)p.T_solid;
     P.solid_isothermal = p.solid_isothermal;
     P.poiseuille = p.poiseuille_inlet;
+    for (int f = 0; f < 6; ++f) {
+        const int b = P.bc[f];
+        P.face_solid[f] = (b == LBFD_BC_WALL_ISOTHERMAL && p.solid_isothermal && G.T_wall[f] == p.T_solid) ||
+                          (b == LBFD_BC_WALL_ADIABATIC && !p.solid_isothermal);
+    }
     P.epsY = (R)p.weno_eps;
     P.epsT = (R)(p.weno_eps * p.T_in * p.T_in);
     P.cs = (R)sqrt(cs2);
@@ -208,6 +215,7 @@ void free_handle(lbfd_handle* h)
     if (h->tmp) cudaFree(h->tmp);
     if (h->bnd) cudaFree(h->bnd);
     if (h->bndf) cudaFree(h->bndf);
+    if (h->wtiles) cudaFree(h->wtiles);
     void* curved[] = {h->link_row, h->link_q, h->ghost_row, h->gh_start, h->gh_idx, h->gh_w, h->gval};
     for (void* p : curved)
         if (p) cudaFree(p);
@@ -253,6 +261,8 @@ lbfd::BoundaryLists lists(const lbfd_handle* h)
     const bool curved = h->nghost > 0 || h->Pd.curved;
     b.face = curved ? h->bnd : h->bndf;
     b.nface = curved ? h->nbnd : h->nbndf;
+    b.wall_tiles = h->wtiles;
+    b.nwall_tiles = curved ? 0 : h->nwtiles;
     return b;
 }
 
@@ -353,8 +363,11 @@ int lbfd_create(const lbfd_grid* grid, const uint8_t* solid_mask, const lbfd_mec
         free_handle(h);
         return cuda_fail(e, "cudaMemcpy(mask)");
     }
+    int least_prio = 0;
     if (h->precision != LBFD_TANGENT &&
-        ((e = cudaStreamCreateWithFlags(&h->side.stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        ((e = cudaDeviceGetStreamPriorityRange(&least_prio, &h->side.priority)) != cudaSuccess ||
+         (e = cudaStreamCreateWithPriority(&h->side.stream, cudaStreamNonBlocking, h->side.priority)) !=
+             cudaSuccess ||
          (e = cudaEventCreateWithFlags(&h->side.fork, cudaEventDisableTiming)) != cudaSuccess ||
          (e = cudaEventCreateWithFlags(&h->side.join, cudaEventDisableTiming)) != cudaSuccess)) {
         free_handle(h);
@@ -364,9 +377,11 @@ int lbfd_create(const lbfd_grid* grid, const uint8_t* solid_mask, const lbfd_mec
     h->section = 0.0;
     for (long long c = 0; c < h->ncell; c += h->grid.nx)
         if (!m[c]) h->section += 1.0;
+    std::vector<long long> lists_host[2];
     for (int faces_only = 0; faces_only <= 1; ++faces_only) {
-        std::vector<long long> list;
-        lbfd::boundary_cells(h->dim, h->grid.nx, h->grid.ny, h->grid.nz, m.data(), list, faces_only != 0);
+        std::vector<long long>& list = lists_host[faces_only];
+        lbfd::boundary_cells(h->dim, h->grid.nx, h->grid.ny, h->grid.nz, h->Pd.bc, m.data(), list, faces_only != 0,
+                             h->Pd.face_solid);
         long long** dst = faces_only ? &h->bndf : &h->bnd;
         (faces_only ? h->nbndf : h->nbnd) = (long long)list.size();
         if (list.empty()) continue;
@@ -379,6 +394,19 @@ int lbfd_create(const lbfd_grid* grid, const uint8_t* solid_mask, const lbfd_mec
             cudaSuccess) {
             free_handle(h);
             return cuda_fail(e, "cudaMemcpy(boundary list)");
+        }
+    }
+    if (h->dim == 2) {
+        std::vector<int> tiles;
+        lbfd::wall_tiles(h->grid.nx, h->grid.ny, lists_host[0], lists_host[1], tiles);
+        h->nwtiles = (long long)tiles.size();
+        if (!tiles.empty()) {
+            if ((e = cudaMalloc(&h->wtiles, tiles.size() * sizeof(int))) != cudaSuccess ||
+                (e = cudaMemcpy(h->wtiles, tiles.data(), tiles.size() * sizeof(int), cudaMemcpyHostToDevice)) !=
+                    cudaSuccess) {
+                free_handle(h);
+                return cuda_fail(e, "wall tiles");
+            }
         }
     }
     // initial state: T_in, Y_in, g = 0
@@ -476,7 +504,8 @@ int lbfd_step_graph(lbfd_handle* h, int n)
             return cuda_fail(le, "step launch during capture");
         }
         if (ee != cudaSuccess) return cuda_fail(ee, "cudaStreamEndCapture");
-        cudaError_t ie = cudaGraphInstantiate(&h->graph, g, 0);
+        // honour the kernel nodes' priorities (boundary kernels ahead of the tiles)
+        cudaError_t ie = cudaGraphInstantiate(&h->graph, g, cudaGraphInstantiateFlagUseNodePriority);
         cudaGraphDestroy(g);
         if (ie != cudaSuccess) {
             h->graph = nullptr;
@@ -502,8 +531,11 @@ int lbfd_launches_per_step(const lbfd_handle* h)
 {
     if (!h) return -1;
     const lbfd::BoundaryLists b = lists(h);
-    const long long nb = (h->dim == 2 && h->variant >= 5) ? b.nface : b.nall;
-    return ((h->variant > 0 && nb > 0 && h->precision != LBFD_TANGENT) ? 2 : 1) + (h->nghost > 0 ? 1 : 0);
+    const bool wv = h->dim == 2 && h->variant >= 5 && b.nwall_tiles > 0;
+    const long long nb = wv ? b.nface : b.nall;
+    int n = 1;
+    if (h->variant > 0 && h->precision != LBFD_TANGENT) n += (nb > 0 ? 1 : 0) + (wv ? 1 : 0);
+    return n + (h->nghost > 0 ? 1 : 0);
 }
 
 int lbfd_set_curved_walls(lbfd_handle* h, int n, const double* prims)

@@ -28,7 +28,29 @@ struct StateView {
 struct SideStream {
     cudaStream_t stream;
     cudaEvent_t fork, join;
+    int priority;  // the device's greatest stream priority
 };
+
+// Launch on the side stream at its priority, so that the block scheduler
+// dispatches these blocks ahead of the pending blocks of the (much larger)
+// tile grid on the main stream; in a captured graph the priority is kept
+// as a kernel-node attribute.
+template <typename... Exp, typename... Act>
+cudaError_t launch_prio(void (*kern)(Exp...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, int prio,
+                        Act&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributePriority;
+    attr[0].val.priority = prio;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Act>(args)...);
+}
 
 // Cells the tile kernels leave to the boundary kernel (see boundary_cells):
 // `all` every non-interior fluid cell; `face` only those whose stencil
@@ -39,7 +61,15 @@ struct BoundaryLists {
     long long nall;
     const long long* face;
     long long nface;
+    const int* wall_tiles;  // 2-D tiles of WALL_TX x WALL_TY cells holding cells of all \ face
+    long long nwall_tiles;
 };
+
+// tile shape of the 2-D wall-tile kernel
+constexpr int WALL_TX = 32, WALL_TY = 8;
+// the tiles that hold a cell of `all` not in `face` (host, at create)
+void wall_tiles(int nx, int ny, const std::vector<long long>& all, const std::vector<long long>& face,
+                std::vector<int>& out);
 
 cudaError_t launch_step(int dim, int precision, int variant, const StepParams<double>& Pd,
                         const StepParams<float>& Pf, StateView in, StateView out, const uint8_t* solid,
@@ -53,8 +83,8 @@ cudaError_t launch_step3d_tiled(int precision, int variant, const StepParams<dou
 
 // Fluid cells that are not interior for the tile kernels (host, at create);
 // faces_only (2-D): only cells whose stencil leaves the domain.
-void boundary_cells(int dim, int nx, int ny, int nz, const uint8_t* solid, std::vector<long long>& out,
-                    bool faces_only);
+void boundary_cells(int dim, int nx, int ny, int nz, const int* bc, const uint8_t* solid, std::vector<long long>& out,
+                    bool faces_only, const int* face_solid);
 
 // Diagnostics reduction over the rows y0 <= y < y1 (all x, all z) into the
 // device scratch `red` (RED_WORDS words, zeroed by the launcher); FP64

@@ -30,6 +30,9 @@ struct StepParams {
     int poiseuille;
     R epsY, epsT;
     R cs;            // lattice sound speed 1/sqrt(3)
+    // face f is a wall that acts exactly like the solid cells (same thermal
+    // condition): the wall-aware tiles treat the layer beyond it as solid
+    int face_solid[6];
     // curved walls (lbfd_set_curved_walls); curved == 0: staircase walls
     int curved;
     const int* link_row;    // [ncell] row of link_q, -1 when no link is cut

@@ -42,29 +42,43 @@ static cudaError_t launch_general(const StepParams<R>& P, StateView in, StateVie
 
 template <typename S, typename R, int TX, int TY, bool WALLS>
 static cudaError_t launch_tiled(const StepParams<R>& P, StateView in, StateView out, const uint8_t* solid,
-                                const long long* bnd, long long nbnd, const SideStream& side, cudaStream_t stream)
+                                const BoundaryLists& b, const SideStream& side, cudaStream_t stream)
 {
     constexpr size_t smem = tile_smem_bytes<R, TX, TY>();
-    auto kern = step_kernel_tiled2d<S, R, TX, TY, WALLS>;
+    auto kern = step_kernel_tiled2d<S, R, TX, TY>;
+    constexpr size_t wsmem = tile_smem_bytes<R, WALL_TX, WALL_TY>();
+    auto wkern = step_kernel_tiled2d_walls<S, R, WALL_TX, WALL_TY>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
-    // the cells the tile kernel skips go to the boundary kernel: disjoint
-    // writes, same input state, so it runs concurrently on the side stream
-    const bool fork = nbnd > 0 && side.stream != nullptr;
+    // the interior cells go to the tile kernel; the others, on the side
+    // stream (disjoint writes, same input state), to the wall-tile kernel
+    // (WALLS variants, cells next to in-domain solids) and the boundary
+    // kernel (the rest)
+    const bool walls = WALLS && !P.curved && b.nwall_tiles > 0;
+    const long long* bl = walls ? b.face : b.all;
+    const long long nb = walls ? b.nface : b.nall;
+    const bool fork = (nb > 0 || walls) && side.stream != nullptr;
     cudaError_t e = cudaSuccess;
     if (fork) {
         if ((e = cudaEventRecord(side.fork, stream)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(side.stream, side.fork, 0)) != cudaSuccess) return e;
     }
     cudaStream_t bs = fork ? side.stream : stream;
-    if (nbnd > 0) {
-        const unsigned nb = (unsigned)((nbnd + 127) / 128);
-        step_kernel_boundary<2, S, R><<<nb, 128, 0, bs>>>(P, (const S*)in.g, (S*)out.g, (const S*)in.T, (S*)out.T,
-                                                          (const S*)in.Y, (S*)out.Y, solid, bnd, nbnd);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int prio = fork ? side.priority : 0;
+    if (nb > 0) {  // the longest-latency blocks first
+        const unsigned nbk = (unsigned)((nb + 127) / 128);
+        e = launch_prio(step_kernel_boundary<2, S, R>, dim3(nbk), dim3(128), 0, bs, prio, P, (const S*)in.g,
+                        (S*)out.g, (const S*)in.T, (S*)out.T, (const S*)in.Y, (S*)out.Y, solid, bl, nb);
+        if (e != cudaSuccess) return e;
+    }
+    if (walls) {
+        e = launch_prio(wkern, dim3((unsigned)b.nwall_tiles), dim3(WALL_TX, WALL_TY), wsmem, bs, prio, P,
+                        (const S*)in.g, (S*)out.g, (const S*)in.T, (S*)out.T, (const S*)in.Y, (S*)out.Y, solid,
+                        (const int*)b.wall_tiles);
+        if (e != cudaSuccess) return e;
     }
     kern<<<grid, dim3(TX, TY), smem, stream>>>(P, (const S*)in.g, (S*)out.g, (const S*)in.T, (S*)out.T,
                                                (const S*)in.Y, (S*)out.Y, solid);
@@ -80,26 +94,43 @@ template <typename S, typename R>
 static cudaError_t launch_2d(int variant, const StepParams<R>& P, StateView in, StateView out, const uint8_t* solid,
                              const BoundaryLists& b, const SideStream& side, cudaStream_t stream)
 {
-    // variants 5-8 also update cells next to in-domain solid cells in the
-    // tile kernel, so their boundary list holds only cells near domain faces
-    // (or every non-interior cell once curved walls are set)
-    const long long* bf = b.face;
-    const long long nf = b.nface;
+    // variants 5-8: the same tiles, plus a wall-tile kernel for the cells
+    // next to in-domain solid cells, so that only cells near domain faces
+    // go through the general form
     switch (variant) {
     case 0: return launch_general<2, S, R>(P, in, out, solid, stream);
-    case 1: return launch_tiled<S, R, 32, 8, false>(P, in, out, solid, b.all, b.nall, side, stream);
-    case 2: return launch_tiled<S, R, 32, 4, false>(P, in, out, solid, b.all, b.nall, side, stream);
-    case 3: return launch_tiled<S, R, 64, 4, false>(P, in, out, solid, b.all, b.nall, side, stream);
-    case 4: return launch_tiled<S, R, 32, 16, false>(P, in, out, solid, b.all, b.nall, side, stream);
-    case 5: return launch_tiled<S, R, 32, 8, true>(P, in, out, solid, bf, nf, side, stream);
-    case 6: return launch_tiled<S, R, 32, 4, true>(P, in, out, solid, bf, nf, side, stream);
-    case 7: return launch_tiled<S, R, 64, 4, true>(P, in, out, solid, bf, nf, side, stream);
-    case 8: return launch_tiled<S, R, 32, 16, true>(P, in, out, solid, bf, nf, side, stream);
+    case 1: return launch_tiled<S, R, 32, 8, false>(P, in, out, solid, b, side, stream);
+    case 2: return launch_tiled<S, R, 32, 4, false>(P, in, out, solid, b, side, stream);
+    case 3: return launch_tiled<S, R, 64, 4, false>(P, in, out, solid, b, side, stream);
+    case 4: return launch_tiled<S, R, 32, 16, false>(P, in, out, solid, b, side, stream);
+    case 5: return launch_tiled<S, R, 32, 8, true>(P, in, out, solid, b, side, stream);
+    case 6: return launch_tiled<S, R, 32, 4, true>(P, in, out, solid, b, side, stream);
+    case 7: return launch_tiled<S, R, 64, 4, true>(P, in, out, solid, b, side, stream);
+    case 8: return launch_tiled<S, R, 32, 16, true>(P, in, out, solid, b, side, stream);
     default: return cudaErrorInvalidValue;
     }
 }
 
 int num_variants(int dim) { return dim == 2 ? 9 : 3; }
+
+void wall_tiles(int nx, int ny, const std::vector<long long>& all, const std::vector<long long>& face,
+                std::vector<int>& out)
+{
+    // tiles (WALL_TX x WALL_TY) holding a cell of `all` that is not in `face`
+    out.clear();
+    std::vector<char> in_face;
+    const int gx = (nx + WALL_TX - 1) / WALL_TX, gy = (ny + WALL_TY - 1) / WALL_TY;
+    std::vector<char> mark((size_t)gx * gy, 0);
+    size_t j = 0;
+    for (long long c : all) {  // both lists are sorted by cell index
+        while (j < face.size() && face[j] < c) ++j;
+        if (j < face.size() && face[j] == c) continue;
+        const int x = (int)(c % nx), y = (int)(c / nx);
+        mark[(size_t)(y / WALL_TY) * gx + x / WALL_TX] = 1;
+    }
+    for (size_t t = 0; t < mark.size(); ++t)
+        if (mark[t]) out.push_back((int)t);
+}
 
 cudaError_t launch_step(int dim, int precision, int variant, const StepParams<double>& Pd,
                         const StepParams<float>& Pf, StateView in, StateView out, const uint8_t* solid,
@@ -116,28 +147,41 @@ cudaError_t launch_step(int dim, int precision, int variant, const StepParams<do
     return launch_general<3, float, float>(Pf, in, out, solid, stream);
 }
 
-void boundary_cells(int dim, int nx, int ny, int nz, const uint8_t* solid, std::vector<long long>& out,
-                    bool faces_only)
+void boundary_cells(int dim, int nx, int ny, int nz, const int* bc, const uint8_t* solid, std::vector<long long>& out,
+                    bool faces_only, const int* face_solid)
 {
     out.clear();
+    auto wrap = [](int q, int n, bool periodic, bool* out) {
+        if (q >= 0 && q < n) return q;
+        if (!periodic) {
+            *out = true;
+            return 0;
+        }
+        return ((q % n) + n) % n;
+    };
+    const bool px = bc[0] == 0, py = bc[2] == 0, pz = bc[4] == 0;  // periodic axes
     if (dim == 3) {
         // the 3-D tile kernel's fast-path condition: +-2 along the three axes
-        // and the 26 neighbours are fluid cells inside the domain
-        const long long plane = (long long)nx * ny;
+        // and the 26 neighbours are fluid cells (periodic axes wrapped)
         for (int z = 0; z < nz; ++z)
             for (int y = 0; y < ny; ++y)
                 for (int x = 0; x < nx; ++x) {
-                    const long long c = (long long)x + (long long)nx * y + plane * z;
+                    const long long c = (long long)x + (long long)nx * ((long long)y + (long long)ny * z);
                     if (solid[c]) continue;
-                    bool fast = x >= 2 && x < nx - 2 && y >= 2 && y < ny - 2 && z >= 2 && z < nz - 2;
-                    for (int d = -2; d <= 2 && fast; ++d) {
-                        if (d == 0) continue;
-                        fast = !solid[c + d] && !solid[c + (long long)nx * d] && !solid[c + plane * d];
-                    }
-                    for (int dz = -1; dz <= 1 && fast; ++dz)
-                        for (int dy = -1; dy <= 1 && fast; ++dy)
-                            for (int dx = -1; dx <= 1 && fast; ++dx)
-                                fast = !solid[c + dx + (long long)nx * dy + plane * dz];
+                    bool fast = true;
+                    for (int dz = -2; dz <= 2 && fast; ++dz)
+                        for (int dy = -2; dy <= 2 && fast; ++dy)
+                            for (int dx = -2; dx <= 2 && fast; ++dx) {
+                                const int nzero = (dx != 0) + (dy != 0) + (dz != 0);
+                                const bool axis = nzero <= 1;
+                                const bool near = dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1;
+                                if (!(axis || near)) continue;
+                                bool out = false;
+                                const int qx = wrap(x + dx, nx, px, &out), qy = wrap(y + dy, ny, py, &out),
+                                          qz = wrap(z + dz, nz, pz, &out);
+                                if (out || solid[(long long)qx + (long long)nx * ((long long)qy + (long long)ny * qz)])
+                                    fast = false;
+                            }
                     if (!fast) out.push_back(c);
                 }
         return;
@@ -154,9 +198,18 @@ void boundary_cells(int dim, int nx, int ny, int nz, const uint8_t* solid, std::
                     const bool axis = (dx == 0 || dy == 0);
                     const bool near = (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1);
                     if (!(axis || near)) continue;
-                    const int qx = x + dx, qy = y + dy;
-                    if (qx < 0 || qx >= nx || qy < 0 || qy >= ny) fast = false;
-                    else if (!faces_only && solid[(long long)qx + (long long)nx * qy]) fast = false;
+                    bool outx = false, outy = false;
+                    const int qx = wrap(x + dx, nx, px, &outx), qy = wrap(y + dy, ny, py, &outy);
+                    if (outx || outy) {
+                        // outside: fine for the wall-aware tiles only beyond walls
+                        // that act like the solid cells
+                        const int rx = x + dx, ry = y + dy;
+                        const bool okx = !outx || (face_solid && face_solid[rx < 0 ? 0 : 1]);
+                        const bool oky = !outy || (face_solid && face_solid[ry < 0 ? 2 : 3]);
+                        if (!(faces_only && okx && oky)) fast = false;
+                    } else if (!faces_only && solid[(long long)qx + (long long)nx * qy]) {
+                        fast = false;
+                    }
                 }
             if (!fast) out.push_back(c);
         }

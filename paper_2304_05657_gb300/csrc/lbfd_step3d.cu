@@ -19,9 +19,10 @@ static cudaError_t launch_t3(const StepParams<R>& P, StateView in, StateView out
     }
     if (nbnd > 0) {
         const unsigned nb = (unsigned)((nbnd + 127) / 128);
-        step_kernel_boundary<3, S, R><<<nb, 128, 0, fork ? side.stream : stream>>>(
-            P, (const S*)in.g, (S*)out.g, (const S*)in.T, (S*)out.T, (const S*)in.Y, (S*)out.Y, solid, bnd, nbnd);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        e = launch_prio(step_kernel_boundary<3, S, R>, dim3(nb), dim3(128), 0, fork ? side.stream : stream,
+                        fork ? side.priority : 0, P, (const S*)in.g, (S*)out.g, (const S*)in.T, (S*)out.T,
+                        (const S*)in.Y, (S*)out.Y, solid, bnd, nbnd);
+        if (e != cudaSuccess) return e;
     }
     dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY, (P.nz + ZC - 1) / ZC);
     kern<<<grid, dim3(TX, TY), smem, stream>>>(P, (const S*)in.g, (S*)out.g, (const S*)in.T, (S*)out.T,

@@ -161,67 +161,14 @@ __device__ __forceinline__ int wall_line(const uint8_t* mask, int p0, int st, in
     return ghost;
 }
 
-// one cell next to in-domain solid cells (staircase walls), from the tile
-template <typename S, typename R, int SX, int NPT>
-__device__ __noinline__ void step_cell_walls(const StepParams<R>& P, const TileSmem<R>& sm, int p0, long long c,
-                                             const S* __restrict__ g_in, S* __restrict__ g_out,
-                                             S* __restrict__ T_out, S* __restrict__ Y_out)
-{
-    const long long N = P.N;
-    R g[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {  // Eq. 8, or Eq. 28 from a solid neighbour
-        const bool solid_src = sm.mask[p0 - cx_of(i) - cy_of(i) * SX] != 0;
-        const long long src = solid_src ? c : c - cx_of(i) - (long long)P.nx * cy_of(i);
-        const int plane = solid_src ? opposite<2>(i) : i;
-        g[i] = R(__ldg(&g_in[(long long)plane * N + src]));
-    }
-    const R T0 = sm.T[p0], invW0 = sm.invW[p0], rho0 = sm.rho[p0];
-    R Y0[NSP];
-#pragma unroll
-    for (int k = 0; k < NSP; ++k) Y0[k] = sm.Y[k * NPT + p0];
-    R u[3];
-    {
-        const R inv = fdiv(R(3), rho0);
-        u[0] = ((g[2] + g[5] + g[8]) - (g[0] + g[3] + g[6])) * inv;
-        u[1] = ((g[6] + g[7] + g[8]) - (g[0] + g[1] + g[2])) * inv;
-        u[2] = R(0);
-    }
-    FDAccum<R> acc;
-    acc.conv_T = acc.diff_T = R(0);
-#pragma unroll
-    for (int k = 0; k < NSP; ++k) acc.conv_Y[k] = acc.diff_Y[k] = R(0);
-    acc.grad_rho[2] = R(0);
-    int pts[5];
-    int gh = wall_line(sm.mask, p0, 1, pts);
-    fd_axis_smem_walls<R>(P, sm, NPT, pts, gh, 0, u[0], Y0, invW0, rho0, acc);
-    gh = wall_line(sm.mask, p0, SX, pts);
-    fd_axis_smem_walls<R>(P, sm, NPT, pts, gh, 1, u[1], Y0, invW0, rho0, acc);
-    const R q = arrhenius(P, T0, Y0[P.fuel], Y0[P.oxid]);
-    const R DT = acc.diff_T + P.Q_cp * q;
-    T_out[c] = S(T0 + (DT - acc.conv_T));
-    R lam_Y = R(0);
-#pragma unroll
-    for (int k = 0; k < NSP; ++k) {
-        const R DY = acc.diff_Y[k] + P.yield[k] * q;
-        Y_out[(long long)k * N + c] = S(Y0[k] + (DY - acc.conv_Y[k]));
-        lam_Y += P.inv_Wk[k] * DY;
-    }
-    const R Lam = fdiv(DT, T0) + fdiv(lam_Y, invW0);
-    collide<2, R>(P, g, rho0, u, acc.grad_rho, Lam);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) g_out[(long long)i * N + c] = S(g[i]);
-}
-
-// wall-aware FP32 tiles: at most 64 registers per thread (65536 per SM): the
-// interior path fits, the rare wall path may spill instead of lowering the
-// occupancy of the whole kernel
+// body of the 2-D tile kernels.  WALLS == false: the interior cells of
+// every tile.  WALLS == true: only the cells next to in-domain solid cells
+// (or walls that act like them), in the tiles listed in `tiles`.
 template <typename S, typename R, int TX, int TY, bool WALLS>
-__global__ void __launch_bounds__(TX * TY, (WALLS && sizeof(R) == 4) ? 1024 / (TX * TY) : 1) step_kernel_tiled2d(StepParams<R> P, const S* __restrict__ g_in,
-                                                               S* __restrict__ g_out, const S* __restrict__ T_in,
-                                                               S* __restrict__ T_out, const S* __restrict__ Y_in,
-                                                               S* __restrict__ Y_out,
-                                                               const uint8_t* __restrict__ solid)
+__device__ __forceinline__ void tiled2d_body(const StepParams<R>& P, const S* __restrict__ g_in, S* __restrict__ g_out,
+                                             const S* __restrict__ T_in, S* __restrict__ T_out,
+                                             const S* __restrict__ Y_in, S* __restrict__ Y_out,
+                                             const uint8_t* __restrict__ solid, const int* __restrict__ tiles)
 {
     using G = TileGeom<TX, TY>;
     constexpr int SX = G::SX, NPT = G::NPT;
@@ -234,16 +181,43 @@ __global__ void __launch_bounds__(TX * TY, (WALLS && sizeof(R) == 4) ? 1024 / (T
     sm.rho = sm.invW + NPT;
     sm.mask = reinterpret_cast<uint8_t*>(sm.rho + NPT);
 
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    int bx = blockIdx.x, by = blockIdx.y;
+    if constexpr (WALLS) {
+        const int t = tiles[blockIdx.x];
+        const int gxn = (P.nx + TX - 1) / TX;
+        bx = t % gxn;
+        by = t / gxn;
+    }
+    const int x0 = bx * TX, y0 = by * TY;
     const int tid = threadIdx.x + TX * threadIdx.y;
     const long long N = P.N;
     // stage the tile and its halo (points outside the domain are marked 2
     // and never read by a fast-path cell)
     for (int pt = tid; pt < NPT; pt += TX * TY) {
         const int sx = pt % SX, sy = pt / SX;
-        const int gx = x0 + sx - 2, gy = y0 + sy - 2;
+        int gx = x0 + sx - 2, gy = y0 + sy - 2;
+        // across a periodic face the halo holds the wrapped cells
+        // (at most two periods away: the halo is two cells wide)
+        if (P.bc[0] == BC_PERIODIC) {
+            if (gx < 0) gx += P.nx;
+            if (gx < 0) gx += P.nx;
+            if (gx >= P.nx) gx -= P.nx;
+            if (gx >= P.nx) gx -= P.nx;
+        }
+        if (P.bc[2] == BC_PERIODIC) {
+            if (gy < 0) gy += P.ny;
+            if (gy < 0) gy += P.ny;
+            if (gy >= P.ny) gy -= P.ny;
+            if (gy >= P.ny) gy -= P.ny;
+        }
         if (gx < 0 || gx >= P.nx || gy < 0 || gy >= P.ny) {
-            sm.mask[pt] = 2;
+            uint8_t m = 2;
+            if constexpr (WALLS) {  // beyond walls that act like the solid cells
+                const bool okx = gx >= 0 && gx < P.nx ? true : P.face_solid[gx < 0 ? 0 : 1];
+                const bool oky = gy >= 0 && gy < P.ny ? true : P.face_solid[gy < 0 ? 2 : 3];
+                if (okx && oky) m = 1;
+            }
+            sm.mask[pt] = m;
             continue;
         }
         const long long c = (long long)gx + (long long)P.nx * gy;
@@ -279,29 +253,38 @@ __global__ void __launch_bounds__(TX * TY, (WALLS && sizeof(R) == 4) ? 1024 / (T
         fast = fast && !sm.mask[p0 + j] && !sm.mask[p0 - j] && !sm.mask[p0 + j * SX] && !sm.mask[p0 - j * SX];
     fast = fast && !sm.mask[p0 + SX + 1] && !sm.mask[p0 + SX - 1] && !sm.mask[p0 - SX + 1] && !sm.mask[p0 - SX - 1];
     if constexpr (WALLS) {
-        // next to in-domain solid cells only (no domain face, no curved
-        // walls): staircase bounce-back and mirror ghosts from shared memory
-        if (!fast) {
-            bool walls = !P.curved;
+        // next to in-domain solid cells only (staircase walls); the interior
+        // cells belong to the plain tile kernel, the rest to the boundary list
+        if (fast || P.curved) return;
+        bool walls = true;
 #pragma unroll
-            for (int j = 1; j <= 2; ++j)
-                walls = walls && sm.mask[p0 + j] != 2 && sm.mask[p0 - j] != 2 && sm.mask[p0 + j * SX] != 2 &&
-                        sm.mask[p0 - j * SX] != 2;
-            walls = walls && sm.mask[p0 + SX + 1] != 2 && sm.mask[p0 + SX - 1] != 2 &&
-                    sm.mask[p0 - SX + 1] != 2 && sm.mask[p0 - SX - 1] != 2;
-            if (!walls) return;  // boundary cell: step_kernel_boundary updates it
-            step_cell_walls<S, R, SX, NPT>(P, sm, p0, c, g_in, g_out, T_out, Y_out);
-            return;
-        }
+        for (int j = 1; j <= 2; ++j)
+            walls = walls && sm.mask[p0 + j] != 2 && sm.mask[p0 - j] != 2 && sm.mask[p0 + j * SX] != 2 &&
+                    sm.mask[p0 - j * SX] != 2;
+        walls = walls && sm.mask[p0 + SX + 1] != 2 && sm.mask[p0 + SX - 1] != 2 && sm.mask[p0 - SX + 1] != 2 &&
+                sm.mask[p0 - SX - 1] != 2;
+        if (!walls) return;
     } else {
-        if (!fast) return;  // boundary cell: step_kernel_boundary updates it
+        if (!fast) return;  // boundary cell: another kernel updates it
     }
-    // a1: pull from the neighbours (all interior)
+    // a1: pull from the neighbours (Eq. 8), half-way bounce-back from an
+    // in-domain solid neighbour (Eq. 28) in the wall-aware variants
     R g[9];
+    {
+        // offsets of the x-1, x+1, y-1, y+1 neighbours, wrapped on periodic axes
+        const int oxm = x == 0 ? P.nx - 1 : -1, oxp = x == P.nx - 1 ? 1 - P.nx : 1;
+        const int oym = y == 0 ? (P.ny - 1) * P.nx : -P.nx, oyp = y == P.ny - 1 ? (1 - P.ny) * P.nx : P.nx;
+        const S* gc = g_in + c;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const long long src = c - cx_of(i) - (long long)P.nx * cy_of(i);
-        g[i] = R(__ldg(&g_in[(long long)i * N + src]));
+        for (int i = 0; i < 9; ++i) {
+            const int ox = cx_of(i) > 0 ? oxm : (cx_of(i) < 0 ? oxp : 0);
+            const int oy = cy_of(i) > 0 ? oym : (cy_of(i) < 0 ? oyp : 0);
+            long long off = (long long)i * N + (ox + oy);
+            if constexpr (WALLS) {
+                if (sm.mask[p0 - cx_of(i) - cy_of(i) * SX]) off = (long long)opposite<2>(i) * N;
+            }
+            g[i] = R(__ldg(gc + off));
+        }
     }
     // a2
     const R T0 = sm.T[p0], invW0 = sm.invW[p0], rho0 = sm.rho[p0];
@@ -321,8 +304,16 @@ __global__ void __launch_bounds__(TX * TY, (WALLS && sizeof(R) == 4) ? 1024 / (T
 #pragma unroll
     for (int k = 0; k < NSP; ++k) acc.conv_Y[k] = acc.diff_Y[k] = R(0);
     acc.grad_rho[2] = R(0);
-    fd_axis_smem<R>(P, sm, NPT, p0, 1, 0, u[0], T0, Y0, invW0, rho0, acc);
-    fd_axis_smem<R>(P, sm, NPT, p0, SX, 1, u[1], T0, Y0, invW0, rho0, acc);
+    if constexpr (WALLS) {
+        int pts[5];
+        int gh = wall_line(sm.mask, p0, 1, pts);
+        fd_axis_smem_walls<R>(P, sm, NPT, pts, gh, 0, u[0], Y0, invW0, rho0, acc);
+        gh = wall_line(sm.mask, p0, SX, pts);
+        fd_axis_smem_walls<R>(P, sm, NPT, pts, gh, 1, u[1], Y0, invW0, rho0, acc);
+    } else {
+        fd_axis_smem<R>(P, sm, NPT, p0, 1, 0, u[0], T0, Y0, invW0, rho0, acc);
+        fd_axis_smem<R>(P, sm, NPT, p0, SX, 1, u[1], T0, Y0, invW0, rho0, acc);
+    }
     // a6
     const R q = arrhenius(P, T0, Y0[P.fuel], Y0[P.oxid]);
     const R reac_T = P.Q_cp * q;
@@ -341,6 +332,27 @@ __global__ void __launch_bounds__(TX * TY, (WALLS && sizeof(R) == 4) ? 1024 / (T
     collide<2, R>(P, g, rho0, u, acc.grad_rho, Lam);
 #pragma unroll
     for (int i = 0; i < 9; ++i) g_out[(long long)i * N + c] = S(g[i]);
+}
+
+// FP32: four 256-thread blocks (1024 threads) per SM, i.e. <= 64 registers
+template <typename S, typename R, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY, sizeof(R) == 4 ? 1024 / (TX * TY) : 1) step_kernel_tiled2d(StepParams<R> P, const S* __restrict__ g_in,
+                                                               S* __restrict__ g_out, const S* __restrict__ T_in,
+                                                               S* __restrict__ T_out, const S* __restrict__ Y_in,
+                                                               S* __restrict__ Y_out,
+                                                               const uint8_t* __restrict__ solid)
+{
+    tiled2d_body<S, R, TX, TY, false>(P, g_in, g_out, T_in, T_out, Y_in, Y_out, solid, nullptr);
+}
+
+// the cells next to in-domain solid cells, over the tiles that contain any
+template <typename S, typename R, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY)
+    step_kernel_tiled2d_walls(StepParams<R> P, const S* __restrict__ g_in, S* __restrict__ g_out,
+                              const S* __restrict__ T_in, S* __restrict__ T_out, const S* __restrict__ Y_in,
+                              S* __restrict__ Y_out, const uint8_t* __restrict__ solid, const int* __restrict__ tiles)
+{
+    tiled2d_body<S, R, TX, TY, true>(P, g_in, g_out, T_in, T_out, Y_in, Y_out, solid, tiles);
 }
 
 // The cells the tiled kernel leaves out: general form over a cell list.

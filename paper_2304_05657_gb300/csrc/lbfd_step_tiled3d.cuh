@@ -24,7 +24,8 @@ struct Tile3Geom {
 template <typename R, int TX, int TY>
 __host__ __device__ constexpr size_t tile3_smem_bytes()
 {
-    return sizeof(R) * (size_t)Tile3Geom<TX, TY>::NPT * (3 + 2 * NSP) + (size_t)Tile3Geom<TX, TY>::NPT;
+    // T, Y_k, 1/W, W, rho per point (X_k = Y_k W / W_k is formed when used)
+    return sizeof(R) * (size_t)Tile3Geom<TX, TY>::NPT * (4 + NSP) + (size_t)Tile3Geom<TX, TY>::NPT;
 }
 
 // FD terms along one axis from five explicit shared-memory points
@@ -45,8 +46,10 @@ __device__ __forceinline__ void fd_axis_pts(const StepParams<R>& P, const TileSm
 #pragma unroll
     for (int j = 0; j < 5; ++j) w[j] = sm.invW[pts[j]];
     const R dinvW = fd_d1(w);
-    R Lk[NSP], m[NSP], dm[NSP], dY[NSP];
+    R Lk[NSP], m[NSP], dm[NSP], dY[NSP], Wl[5];
     R sumL = R(0), M = R(0), dM = R(0);
+#pragma unroll
+    for (int j = 0; j < 5; ++j) Wl[j] = sm.X[pts[j]];  // W (the 3-D tile keeps W in the X slot)
 #pragma unroll
     for (int k = 0; k < NSP; ++k) {
 #pragma unroll
@@ -55,7 +58,7 @@ __device__ __forceinline__ void fd_axis_pts(const StepParams<R>& P, const TileSm
         sumL += Lk[k];
         dY[k] = fd_d1(v);
 #pragma unroll
-        for (int j = 0; j < 5; ++j) v[j] = sm.X[k * npt + pts[j]];
+        for (int j = 0; j < 5; ++j) v[j] *= P.inv_Wk[k] * Wl[j];  // X_k = Y_k W / W_k
         const R dX = fd_d1(v), d2X = fd_d2(v);
         m[k] = P.a_diff[k] * invW0 * dX;
         dm[k] = P.a_diff[k] * (invW0 * d2X + dinvW * dX);
@@ -81,13 +84,17 @@ __device__ __forceinline__ void stage_plane(const StepParams<R>& P, const TileSm
     const int tid = threadIdx.x + TX * threadIdx.y;
     for (int q = tid; q < G::NPP; q += TX * TY) {
         const int sx = q % G::SX, sy = q / G::SX;
-        const int gx = x0 + sx - 2, gy = y0 + sy - 2;
+        int gx = x0 + sx - 2, gy = y0 + sy - 2, gz = z;
         const int pt = slot * G::NPP + q;
-        if (gx < 0 || gx >= P.nx || gy < 0 || gy >= P.ny || z < 0 || z >= P.nz) {
+        // across a periodic face the halo holds the wrapped cells
+        if ((gx < 0 || gx >= P.nx) && P.bc[0] == BC_PERIODIC) gx = ((gx % P.nx) + P.nx) % P.nx;
+        if ((gy < 0 || gy >= P.ny) && P.bc[2] == BC_PERIODIC) gy = ((gy % P.ny) + P.ny) % P.ny;
+        if ((gz < 0 || gz >= P.nz) && P.bc[4] == BC_PERIODIC) gz = ((gz % P.nz) + P.nz) % P.nz;
+        if (gx < 0 || gx >= P.nx || gy < 0 || gy >= P.ny || gz < 0 || gz >= P.nz) {
             sm.mask[pt] = 2;
             continue;
         }
-        const long long c = (long long)gx + (long long)P.nx * (gy + (long long)P.ny * z);
+        const long long c = (long long)gx + (long long)P.nx * (gy + (long long)P.ny * gz);
         const uint8_t s = solid[c];
         sm.mask[pt] = s ? 1 : 0;
         if (s) continue;
@@ -99,10 +106,8 @@ __device__ __forceinline__ void stage_plane(const StepParams<R>& P, const TileSm
         const R W = fdiv(R(1), invW);
         sm.T[pt] = T;
 #pragma unroll
-        for (int k = 0; k < NSP; ++k) {
-            sm.Y[k * NPT + pt] = Y[k];
-            sm.X[k * NPT + pt] = Y[k] * P.inv_Wk[k] * W;
-        }
+        for (int k = 0; k < NSP; ++k) sm.Y[k * NPT + pt] = Y[k];
+        sm.X[pt] = W;  // the 3-D tile keeps W in the X slot
         sm.invW[pt] = invW;
         sm.rho[pt] = fdiv(P.T_in * P.invW_in * W, T);
     }
@@ -121,8 +126,8 @@ __global__ void __launch_bounds__(TX * TY) step_kernel_tiled3d(StepParams<R> P, 
     TileSmem<R> sm;
     sm.T = reinterpret_cast<R*>(smem_raw);
     sm.Y = sm.T + NPT;
-    sm.X = sm.Y + NSP * NPT;
-    sm.invW = sm.X + NSP * NPT;
+    sm.X = sm.Y + NSP * NPT;  // one plane: W
+    sm.invW = sm.X + NPT;
     sm.rho = sm.invW + NPT;
     sm.mask = reinterpret_cast<uint8_t*>(sm.rho + NPT);
 
@@ -163,7 +168,11 @@ __global__ void __launch_bounds__(TX * TY) step_kernel_tiled3d(StepParams<R> P, 
             R g[27];
 #pragma unroll
             for (int i = 0; i < 27; ++i) {
-                const long long src = c - cx_of(i) - (long long)P.nx * cy_of(i) - plane * cz_of(i);
+                int xs = x - cx_of(i), ys = y - cy_of(i), zs = z - cz_of(i);  // wrapped on periodic axes
+                xs += xs < 0 ? P.nx : (xs >= P.nx ? -P.nx : 0);
+                ys += ys < 0 ? P.ny : (ys >= P.ny ? -P.ny : 0);
+                zs += zs < 0 ? P.nz : (zs >= P.nz ? -P.nz : 0);
+                const long long src = (long long)xs + (long long)P.nx * ys + plane * zs;
                 g[i] = R(__ldg(&g_in[(long long)i * N + src]));
             }
             const R T0 = sm.T[p0], invW0 = sm.invW[p0], rho0 = sm.rho[p0];
