@@ -184,7 +184,7 @@ int lbfd_step_graph(lbfd_handle* h, int n);
 /* Kernel variants of the step: 0 is the general form (any cell, D2Q9 and
  * D3Q27); in 2-D, 1..4 are shared-memory tiles of 32x8, 32x4, 64x4 and
  * 32x16 interior cells and 5..8 the same tiles plus a second tile kernel
- * (over the 32x8 tiles that need it) for the cells next to in-domain solid
+ * (over the 32x4 tiles that need it) for the cells next to in-domain solid
  * cells (staircase walls, from shared memory); in 3-D, 1..2 are 32x4 columns marching through 16
  * or 32 z-planes with a five-plane shared-memory ring.  The tile variants
  * are followed by the general form over the list of boundary cells

@@ -10,6 +10,7 @@
 #include <type_traits>
 
 #include "lbfd_dual.cuh"
+#include "lbfd_f2.cuh"
 #include "lbfd_params.h"
 
 namespace lbfd {
@@ -94,6 +95,17 @@ __device__ __forceinline__ R inv_molar_mass(const StepParams<R>& P, const R* Y)
     return s;
 }
 
+// Y[k] for a species index known only at run time, without indexing a
+// register array
+template <typename R>
+__device__ __forceinline__ R pick_species(const R* Y, int k)
+{
+    R r = Y[0];
+#pragma unroll
+    for (int j = 1; j < NSP; ++j) r = k == j ? Y[j] : r;
+    return r;
+}
+
 // EOS at constant P_0 (Sec. II.A) with rho(T_in, Y_in) = 1
 template <typename R>
 __device__ __forceinline__ R eos(const StepParams<R>& P, R T, R invW)
@@ -127,12 +139,12 @@ __device__ __forceinline__ R arrhenius(const StepParams<R>& P, R T, R yf, R yo)
 template <typename R>
 __device__ __forceinline__ R fd_d1(const R* v)  // 4th-order central first derivative
 {
-    return (v[0] - v[4] + R(8) * (v[3] - v[1])) * (R(1) / R(12));
+    return (v[0] - v[4] + R(8) * (v[3] - v[1])) * R(scalar_t<R>(1) / scalar_t<R>(12));
 }
 template <typename R>
 __device__ __forceinline__ R fd_d2(const R* v)  // 4th-order central second derivative
 {
-    return (R(16) * (v[1] + v[3]) - (v[0] + v[4]) - R(30) * v[2]) * (R(1) / R(12));
+    return (R(16) * (v[1] + v[3]) - (v[0] + v[4]) - R(30) * v[2]) * R(scalar_t<R>(1) / scalar_t<R>(12));
 }
 template <typename R>
 __device__ __forceinline__ R fd_c2(const R* v)  // centred 2nd order
@@ -330,12 +342,13 @@ __host__ __device__ constexpr int moment_order(int j) { return j % 3 + (j / 3) %
 // orders 0-1 carried, second order split into trace (omega_b) and
 // deviatoric/off-diagonal (omega_s), orders >= 3 at omega_hi.
 // ---------------------------------------------------------------------------
-template <int DIM, typename R>
-__device__ __forceinline__ void collide(const StepParams<R>& P, R* g, R rho, const R* u, const R* grad_rho,
+template <int DIM, typename R, typename PR>
+__device__ __forceinline__ void collide(const StepParams<PR>& P, R* g, R rho, const R* u, const R* grad_rho,
                                         R Lam)
 {
+    using Sc = scalar_t<R>;
     constexpr int Q = DIM == 2 ? 9 : 27;
-    const R cs2 = R(1) / R(3);
+    const R cs2 = R(Sc(1) / Sc(3));
     R sum_g = R(0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) sum_g += g[i];
@@ -346,7 +359,7 @@ __device__ __forceinline__ void collide(const StepParams<R>& P, R* g, R rho, con
     R xi[Q], fe[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const R wi = weight<DIM, R>(i);
+        const R wi = R(weight<DIM, Sc>(i));
         R cu = R(0), cg = R(0);
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
@@ -366,7 +379,7 @@ __device__ __forceinline__ void collide(const StepParams<R>& P, R* g, R rho, con
     to_cumulants<DIM>(g);
     to_cumulants<DIM>(fe);
     // relaxation
-    const R ws = P.omega_s, wb = P.omega_b, wh = P.omega_hi;
+    const R ws = R(P.omega_s), wb = R(P.omega_b), wh = R(P.omega_hi);
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
         const int o = moment_order(j);
@@ -389,7 +402,7 @@ __device__ __forceinline__ void collide(const StepParams<R>& P, R* g, R rho, con
         const R trs = tre + (R(1) - wb) * (tr - tre);
         const R d1s = d1e + (R(1) - ws) * (d1 - d1e);
         const R d2s = d2e + (R(1) - ws) * (d2 - d2e);
-        const R xx = (trs + d1s + d2s) * (R(1) / R(3));
+        const R xx = (trs + d1s + d2s) * R(Sc(1) / Sc(3));
         g[ixx] = xx;
         g[iyy] = xx - d1s;
         g[izz] = xx - d2s;

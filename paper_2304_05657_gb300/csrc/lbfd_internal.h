@@ -66,7 +66,7 @@ struct BoundaryLists {
 };
 
 // tile shape of the 2-D wall-tile kernel
-constexpr int WALL_TX = 32, WALL_TY = 8;
+constexpr int WALL_TX = 32, WALL_TY = 4;
 // the tiles that hold a cell of `all` not in `face` (host, at create)
 void wall_tiles(int nx, int ny, const std::vector<long long>& all, const std::vector<long long>& face,
                 std::vector<int>& out);

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "lbfd_internal.h"
+#include "lbfd_step_pair.cuh"
 #include "lbfd_step_tiled.cuh"
 
 namespace lbfd {
@@ -40,12 +41,16 @@ static cudaError_t launch_general(const StepParams<R>& P, StateView in, StateVie
     return cudaGetLastError();
 }
 
-template <typename S, typename R, int TX, int TY, bool WALLS>
+// PAIR: the interior tiles compute two cells per thread in packed FP32
+// (FP32 storage only; the FP64 form keeps one cell per thread)
+template <typename S, typename R, int TX, int TY, bool WALLS, bool PAIR = false, int MINB = 1>
 static cudaError_t launch_tiled(const StepParams<R>& P, StateView in, StateView out, const uint8_t* solid,
                                 const BoundaryLists& b, const SideStream& side, cudaStream_t stream)
 {
+    constexpr bool pair = PAIR && std::is_same<S, float>::value && std::is_same<R, float>::value;
     constexpr size_t smem = tile_smem_bytes<R, TX, TY>();
     auto kern = step_kernel_tiled2d<S, R, TX, TY>;
+    const dim3 block(pair ? TX / 2 : TX, TY);
     constexpr size_t wsmem = tile_smem_bytes<R, WALL_TX, WALL_TY>();
     auto wkern = step_kernel_tiled2d_walls<S, R, WALL_TX, WALL_TY>;
     if (smem > 48 * 1024) {
@@ -80,8 +85,17 @@ static cudaError_t launch_tiled(const StepParams<R>& P, StateView in, StateView 
                         (const int*)b.wall_tiles);
         if (e != cudaSuccess) return e;
     }
-    kern<<<grid, dim3(TX, TY), smem, stream>>>(P, (const S*)in.g, (S*)out.g, (const S*)in.T, (S*)out.T,
-                                               (const S*)in.Y, (S*)out.Y, solid);
+    if constexpr (pair) {
+        auto pk = step_kernel_pair2d<TX / 2, TY, MINB>;
+        if (smem > 48 * 1024 &&
+            (e = cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+            return e;
+        pk<<<grid, block, smem, stream>>>(P, (const float*)in.g, (float*)out.g, (const float*)in.T, (float*)out.T,
+                                          (const float*)in.Y, (float*)out.Y, solid);
+    } else {
+        kern<<<grid, block, smem, stream>>>(P, (const S*)in.g, (S*)out.g, (const S*)in.T, (S*)out.T,
+                                            (const S*)in.Y, (S*)out.Y, solid);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (fork) {
         if ((e = cudaEventRecord(side.join, side.stream)) != cudaSuccess) return e;
@@ -107,11 +121,17 @@ static cudaError_t launch_2d(int variant, const StepParams<R>& P, StateView in, 
     case 6: return launch_tiled<S, R, 32, 4, true>(P, in, out, solid, b, side, stream);
     case 7: return launch_tiled<S, R, 64, 4, true>(P, in, out, solid, b, side, stream);
     case 8: return launch_tiled<S, R, 32, 16, true>(P, in, out, solid, b, side, stream);
+    // variants 9-12: as 5-8 with two cells per thread in packed FP32, at
+    // 128 registers (9, 10) or 96 (11, 12, five 128-thread blocks per SM)
+    case 9: return launch_tiled<S, R, 32, 8, true, true, 4>(P, in, out, solid, b, side, stream);
+    case 10: return launch_tiled<S, R, 64, 8, true, true, 2>(P, in, out, solid, b, side, stream);
+    case 11: return launch_tiled<S, R, 32, 8, true, true, 5>(P, in, out, solid, b, side, stream);
+    case 12: return launch_tiled<S, R, 64, 4, true, true, 5>(P, in, out, solid, b, side, stream);
     default: return cudaErrorInvalidValue;
     }
 }
 
-int num_variants(int dim) { return dim == 2 ? 9 : 3; }
+int num_variants(int dim) { return dim == 2 ? 13 : 3; }
 
 void wall_tiles(int nx, int ny, const std::vector<long long>& all, const std::vector<long long>& face,
                 std::vector<int>& out)

@@ -376,7 +376,7 @@ __device__ __forceinline__ void cell_step_general(const StepParams<R>& P, const 
         fd_axis<R>(P, a, L.near, Tl, Yl, invWl, rhol, u[a], T0, Y0, invW0, rho0, acc);
     }
     // a6: reaction
-    const R q = arrhenius(P, T0, Y0[P.fuel], Y0[P.oxid]);
+    const R q = arrhenius(P, T0, pick_species(Y0, P.fuel), pick_species(Y0, P.oxid));
     const R reac_T = P.Q_cp * q;
     // a7: Euler update and Lambda from the non-convective rates (Eq. 6)
     const R DT = acc.diff_T + reac_T;

@@ -1,0 +1,152 @@
+// lbfd_step_pair.cuh -- 2-D interior tile kernel that computes two
+// neighbouring cells (x, x+1) per thread with packed FP32 arithmetic (F2):
+// the same staging and the same per-cell arithmetic as step_kernel_tiled2d,
+// instantiated on a pair of cells, so that each packed instruction does the
+// work of two.  The kernel is issue-bound (not HBM-bound), and the packed
+// form halves the floating-point instructions; FD lines along x come from
+// three aligned 8-byte shared loads per field, along y from five.
+//
+// A thread whose two cells are not both interior still computes the pair
+// and stores only the interior one(s); the others belong to the boundary
+// kernels, exactly as in the one-cell-per-thread tiles.
+#pragma once
+#include "lbfd_step_tiled.cuh"
+
+namespace lbfd {
+
+// five-point line of a staged field for the cells at points p0 (even) and
+// p0 + 1: along x from f[p0-2 .. p0+3], along y from rows p0 +- SX, +- 2 SX
+template <bool XLINE, int SX>
+__device__ __forceinline__ void pair_line(const float* f, int p0, F2* v)
+{
+    if constexpr (XLINE) {
+        const float2 a = *reinterpret_cast<const float2*>(f + p0 - 2);
+        const float2 b = *reinterpret_cast<const float2*>(f + p0);
+        const float2 c = *reinterpret_cast<const float2*>(f + p0 + 2);
+        v[0] = F2(a);
+        v[1] = F2(a.y, b.x);
+        v[2] = F2(b);
+        v[3] = F2(b.y, c.x);
+        v[4] = F2(c);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 5; ++j) v[j] = F2(*reinterpret_cast<const float2*>(f + p0 + (j - 2) * SX));
+    }
+}
+
+__device__ __forceinline__ F2 pair_at(const float* f, int p0) { return F2(*reinterpret_cast<const float2*>(f + p0)); }
+
+// store the lanes that are set (predicated stores, no branch)
+__device__ __forceinline__ void pair_store(float* p, const F2& v, bool ok0, bool ok1)
+{
+    if (ok0) p[0] = v.v.x;
+    if (ok1) p[1] = v.v.y;
+}
+
+// TXP x TY threads, a tile of 2 TXP x TY cells, at least MINB blocks per
+// SM (which caps the registers); FP32 storage and arithmetic
+template <int TXP, int TY, int MINB>
+__global__ void __launch_bounds__(TXP * TY, MINB)
+    step_kernel_pair2d(StepParams<float> P, const float* __restrict__ g_in, float* __restrict__ g_out,
+                       const float* __restrict__ T_in, float* __restrict__ T_out, const float* __restrict__ Y_in,
+                       float* __restrict__ Y_out, const uint8_t* __restrict__ solid)
+{
+    constexpr int TX = 2 * TXP;
+    using G = TileGeom<TX, TY>;
+    constexpr int SX = G::SX, NPT = G::NPT;
+    static_assert(SX % 2 == 0 && NPT % 2 == 0, "pairs need 8-byte aligned shared rows");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TileSmem<float> sm;
+    sm.T = reinterpret_cast<float*>(smem_raw);
+    sm.Y = sm.T + NPT;
+    sm.X = sm.Y + NSP * NPT;
+    sm.invW = sm.X + NSP * NPT;
+    sm.rho = sm.invW + NPT;
+    sm.mask = reinterpret_cast<uint8_t*>(sm.rho + NPT);
+
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x = x0 + 2 * threadIdx.x, y = y0 + threadIdx.y;
+    const bool inside = x < P.nx && y < P.ny;
+    const bool has1 = x + 1 < P.nx;
+    const long long c = (long long)x + (long long)P.nx * y;
+    const long long N = P.N;
+
+    // a1: pull from the neighbours (Eq. 8), issued before the staging so
+    // that the loads are in flight meanwhile; a missing lane 1 re-reads
+    // lane 0.  The offsets wrap inside the domain for any in-range cell.
+    F2 g[9];
+    if (inside) {
+        const int x1 = has1 ? x + 1 : x;
+        const int oym = y == 0 ? (P.ny - 1) * P.nx : -P.nx, oyp = y == P.ny - 1 ? (1 - P.ny) * P.nx : P.nx;
+        const int oxm0 = x == 0 ? P.nx - 1 : -1, oxp0 = x == P.nx - 1 ? 1 - P.nx : 1;
+        const int oxm1 = x1 == 0 ? P.nx - 1 : -1, oxp1 = x1 == P.nx - 1 ? 1 - P.nx : 1;
+        const float* gc0 = g_in + c;
+        const float* gc1 = g_in + c + (x1 - x);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int oy = cy_of(i) > 0 ? oym : (cy_of(i) < 0 ? oyp : 0);
+            const int o0 = (cx_of(i) > 0 ? oxm0 : (cx_of(i) < 0 ? oxp0 : 0)) + oy;
+            const int o1 = (cx_of(i) > 0 ? oxm1 : (cx_of(i) < 0 ? oxp1 : 0)) + oy;
+            const float* a0 = gc0 + (long long)i * N + o0;
+            if (cx_of(i) == 0 && has1 && (reinterpret_cast<uintptr_t>(a0) & 7) == 0)
+                g[i] = F2(__ldg(reinterpret_cast<const float2*>(a0)));
+            else
+                g[i] = F2(__ldg(a0), __ldg(gc1 + (long long)i * N + o1));
+        }
+    }
+    stage_tile2d<float, float, TX, TY, false, TXP * TY>(P, sm, x0, y0, threadIdx.x + TXP * threadIdx.y, T_in, Y_in,
+                                                        solid);
+    __syncthreads();
+
+    if (!inside) return;
+    const int p0 = (threadIdx.y + 2) * SX + 2 * threadIdx.x + 2;
+    const bool ok0 = interior_point<SX>(sm.mask, p0);
+    const bool ok1 = has1 && interior_point<SX>(sm.mask, p0 + 1);
+    if (!ok0 && !ok1) return;
+
+    // a2
+    const F2 T0 = pair_at(sm.T, p0), invW0 = pair_at(sm.invW, p0), rho0 = pair_at(sm.rho, p0);
+    F2 Y0[NSP];
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) Y0[k] = pair_at(sm.Y + k * NPT, p0);
+    F2 u[3];
+    {
+        const F2 inv = fdiv(F2(3.f), rho0);
+        u[0] = ((g[2] + g[5] + g[8]) - (g[0] + g[3] + g[6])) * inv;
+        u[1] = ((g[6] + g[7] + g[8]) - (g[0] + g[1] + g[2])) * inv;
+        u[2] = F2(0.f);
+    }
+    // a3-a5
+    FDAccum<F2> acc;
+    acc.conv_T = acc.diff_T = F2(0.f);
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) acc.conv_Y[k] = acc.diff_Y[k] = F2(0.f);
+    acc.grad_rho[2] = F2(0.f);
+    {
+        auto line_x = [&](const float* f, F2* v) { pair_line<true, SX>(f, p0, v); };
+        auto line_y = [&](const float* f, F2* v) { pair_line<false, SX>(f, p0, v); };
+        fd_axis_core<F2>(P, sm, NPT, line_x, 0, u[0], Y0, invW0, rho0, acc);
+        fd_axis_core<F2>(P, sm, NPT, line_y, 1, u[1], Y0, invW0, rho0, acc);
+    }
+    // a6: per lane (the mixed form switches to FP64 above T_fp64)
+    const F2 yf = pick_species(Y0, P.fuel), yo = pick_species(Y0, P.oxid);
+    const F2 q(arrhenius(P, T0.v.x, yf.v.x, yo.v.x), arrhenius(P, T0.v.y, yf.v.y, yo.v.y));
+    const F2 reac_T = F2(P.Q_cp) * q;
+    // a7
+    const F2 DT = acc.diff_T + reac_T;
+    pair_store(T_out + c, T0 + (DT - acc.conv_T), ok0, ok1);
+    F2 lam_Y = F2(0.f);
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) {
+        const F2 DY = acc.diff_Y[k] + F2(P.yield[k]) * q;
+        pair_store(Y_out + (long long)k * N + c, Y0[k] + (DY - acc.conv_Y[k]), ok0, ok1);
+        lam_Y += F2(P.inv_Wk[k]) * DY;
+    }
+    const F2 Lam = fdiv(DT, T0) + fdiv(lam_Y, invW0);
+    // a8-a10
+    collide<2, F2>(P, g, rho0, u, acc.grad_rho, Lam);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) pair_store(g_out + (long long)i * N + c, g[i], ok0, ok1);
+}
+
+}  // namespace lbfd

@@ -38,47 +38,66 @@ __host__ __device__ constexpr size_t tile_smem_bytes()
     return sizeof(R) * (size_t)TileGeom<TX, TY>::NPT * (3 + 2 * NSP) + (size_t)TileGeom<TX, TY>::NPT;
 }
 
+// FD terms along one axis of an interior cell (Eq. 25-27): `line(f, v)`
+// gathers the five points of the staged field f along the axis into v.
+// R is the compute type (float, double, or F2 for a pair of cells), PR the
+// parameters' type.
+template <typename R, typename PR, typename SR, typename Line>
+__device__ __forceinline__ void fd_axis_core(const StepParams<PR>& P, const TileSmem<SR>& sm, int npt, Line line,
+                                             int a, R u_a, const R* Y0, R invW0, R rho0, FDAccum<R>& acc)
+{
+    R v[5], w[5];
+    line(sm.rho, v);
+    const R drho = fd_d1(v);
+    acc.grad_rho[a] = drho;
+    const R drho_r = fdiv(drho, rho0);
+    line(sm.T, v);
+    acc.conv_T += u_a * weno3_deriv_fast(v, u_a, R(P.epsT));
+    acc.diff_T += R(P.alpha) * (fd_d2(v) + drho_r * fd_d1(v));
+    line(sm.invW, w);
+    const R dinvW = fd_d1(w);
+    // diffusion fluxes from the X_k lines first: their sums M, dM enter
+    // every species' correction term
+    R m[NSP], dm[NSP];
+    R M = R(0), dM = R(0);
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) {
+        line(sm.X + k * npt, v);
+        const R dX = fd_d1(v), d2X = fd_d2(v);
+        const R ak = R(P.a_diff[k]);
+        m[k] = ak * invW0 * dX;
+        dm[k] = ak * (invW0 * d2X + dinvW * dX);
+        M += m[k];
+        dM += dm[k];
+    }
+    // then the Y_k lines; the convective correction -Y_k u_a sum_j L_j is
+    // added once the sum is known
+    R sumL = R(0);
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) {
+        line(sm.Y + k * npt, v);
+        const R Lk = weno3_deriv_fast(v, u_a, R(P.epsY));
+        sumL += Lk;
+        const R dY = fd_d1(v);
+        acc.conv_Y[k] += u_a * Lk;
+        acc.diff_Y[k] += dm[k] - dY * M - Y0[k] * dM + (m[k] - Y0[k] * M) * drho_r;
+    }
+    const R us = u_a * sumL;
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) acc.conv_Y[k] -= Y0[k] * us;
+}
+
 // fast-path FD terms along one axis from shared memory; `st` is the point
 // stride of the axis (1 for x, SX for y) and p0 the centre point
 template <typename R>
 __device__ __forceinline__ void fd_axis_smem(const StepParams<R>& P, const TileSmem<R>& sm, int npt, int p0, int st,
                                              int a, R u_a, R T0, const R* Y0, R invW0, R rho0, FDAccum<R>& acc)
 {
-    R v[5], w[5];
+    auto line = [&](const R* f, R* v) {
 #pragma unroll
-    for (int j = 0; j < 5; ++j) v[j] = sm.rho[p0 + (j - 2) * st];
-    const R drho = fd_d1(v);
-    acc.grad_rho[a] = drho;
-    const R drho_r = fdiv(drho, rho0);
-#pragma unroll
-    for (int j = 0; j < 5; ++j) v[j] = sm.T[p0 + (j - 2) * st];
-    acc.conv_T += u_a * weno3_deriv_fast(v, u_a, P.epsT);
-    acc.diff_T += P.alpha * (fd_d2(v) + drho_r * fd_d1(v));
-#pragma unroll
-    for (int j = 0; j < 5; ++j) w[j] = sm.invW[p0 + (j - 2) * st];
-    const R dinvW = fd_d1(w);
-    R Lk[NSP], m[NSP], dm[NSP], dY[NSP];
-    R sumL = R(0), M = R(0), dM = R(0);
-#pragma unroll
-    for (int k = 0; k < NSP; ++k) {
-#pragma unroll
-        for (int j = 0; j < 5; ++j) v[j] = sm.Y[k * npt + p0 + (j - 2) * st];
-        Lk[k] = weno3_deriv_fast(v, u_a, P.epsY);
-        sumL += Lk[k];
-        dY[k] = fd_d1(v);
-#pragma unroll
-        for (int j = 0; j < 5; ++j) v[j] = sm.X[k * npt + p0 + (j - 2) * st];
-        const R dX = fd_d1(v), d2X = fd_d2(v);
-        m[k] = P.a_diff[k] * invW0 * dX;
-        dm[k] = P.a_diff[k] * (invW0 * d2X + dinvW * dX);
-        M += m[k];
-        dM += dm[k];
-    }
-#pragma unroll
-    for (int k = 0; k < NSP; ++k) {
-        acc.conv_Y[k] += u_a * (Lk[k] - Y0[k] * sumL);
-        acc.diff_Y[k] += dm[k] - dY[k] * M - Y0[k] * dM + (m[k] - Y0[k] * M) * drho_r;
-    }
+        for (int j = 0; j < 5; ++j) v[j] = f[p0 + (j - 2) * st];
+    };
+    fd_axis_core<R>(P, sm, npt, line, a, u_a, Y0, invW0, rho0, acc);
 }
 
 // FD terms along one axis for a cell next to in-domain solid cells (staircase
@@ -161,6 +180,109 @@ __device__ __forceinline__ int wall_line(const uint8_t* mask, int p0, int st, in
     return ghost;
 }
 
+// a1 (Eq. 8) for a cell whose 8 neighbours are fluid cells of the domain:
+// plain pull, the x-1, x+1, y-1, y+1 neighbours wrapped on periodic axes
+// (the offsets stay inside the domain for any in-range cell)
+template <typename S, typename R>
+__device__ __forceinline__ void pull_interior(const StepParams<R>& P, const S* __restrict__ g_in, long long c, int x,
+                                              int y, R* g)
+{
+    const int oxm = x == 0 ? P.nx - 1 : -1, oxp = x == P.nx - 1 ? 1 - P.nx : 1;
+    const int oym = y == 0 ? (P.ny - 1) * P.nx : -P.nx, oyp = y == P.ny - 1 ? (1 - P.ny) * P.nx : P.nx;
+    const S* gc = g_in + c;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int ox = cx_of(i) > 0 ? oxm : (cx_of(i) < 0 ? oxp : 0);
+        const int oy = cy_of(i) > 0 ? oym : (cy_of(i) < 0 ? oyp : 0);
+        g[i] = R(__ldg(gc + (long long)i * P.N + (ox + oy)));
+    }
+}
+
+// Stage T, Y_k, X_k, 1/W, rho and the mask of a tile (origin x0, y0) and
+// its 2-cell halo with NTHR threads, this one numbered tid.  All of a
+// thread's global loads are issued before any of them is used, so that
+// their latencies overlap.
+template <typename S, typename R, int TX, int TY, bool WALLS, int NTHR>
+__device__ __forceinline__ void stage_tile2d(const StepParams<R>& P, const TileSmem<R>& sm, int x0, int y0, int tid,
+                                             const S* __restrict__ T_in, const S* __restrict__ Y_in,
+                                             const uint8_t* __restrict__ solid)
+{
+    using G = TileGeom<TX, TY>;
+    constexpr int SX = G::SX, NPT = G::NPT;
+    constexpr int NIT = (NPT + NTHR - 1) / NTHR;
+    const long long N = P.N;
+    long long cell[NIT];  // -1: outside the domain
+    uint8_t s[NIT];
+    R T[NIT], Y[NIT][NSP];
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) {
+        const int pt = tid + it * NTHR;
+        cell[it] = -1;
+        if (pt >= NPT) continue;
+        const int sx = pt % SX, sy = pt / SX;
+        int gx = x0 + sx - 2, gy = y0 + sy - 2;
+        // across a periodic face the halo holds the wrapped cells
+        // (at most two periods away: the halo is two cells wide)
+        if (P.bc[0] == BC_PERIODIC) {
+            if (gx < 0) gx += P.nx;
+            if (gx < 0) gx += P.nx;
+            if (gx >= P.nx) gx -= P.nx;
+            if (gx >= P.nx) gx -= P.nx;
+        }
+        if (P.bc[2] == BC_PERIODIC) {
+            if (gy < 0) gy += P.ny;
+            if (gy < 0) gy += P.ny;
+            if (gy >= P.ny) gy -= P.ny;
+            if (gy >= P.ny) gy -= P.ny;
+        }
+        if (gx < 0 || gx >= P.nx || gy < 0 || gy >= P.ny) {
+            // outside the domain: marked 2 and never read by a fast-path cell
+            uint8_t m = 2;
+            if constexpr (WALLS) {  // beyond walls that act like the solid cells
+                const bool okx = gx >= 0 && gx < P.nx ? true : P.face_solid[gx < 0 ? 0 : 1];
+                const bool oky = gy >= 0 && gy < P.ny ? true : P.face_solid[gy < 0 ? 2 : 3];
+                if (okx && oky) m = 1;
+            }
+            sm.mask[pt] = m;
+            continue;
+        }
+        const long long c = (long long)gx + (long long)P.nx * gy;
+        cell[it] = c;
+        s[it] = solid[c];
+        T[it] = R(T_in[c]);
+#pragma unroll
+        for (int k = 0; k < NSP; ++k) Y[it][k] = R(Y_in[(long long)k * N + c]);
+    }
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) {
+        if (cell[it] < 0) continue;
+        const int pt = tid + it * NTHR;
+        sm.mask[pt] = s[it] ? 1 : 0;
+        if (s[it]) continue;
+        const R invW = inv_molar_mass(P, Y[it]);
+        const R W = fdiv(R(1), invW);
+        sm.T[pt] = T[it];
+#pragma unroll
+        for (int k = 0; k < NSP; ++k) {
+            sm.Y[k * NPT + pt] = Y[it][k];
+            sm.X[k * NPT + pt] = Y[it][k] * P.inv_Wk[k] * W;
+        }
+        sm.invW[pt] = invW;
+        sm.rho[pt] = fdiv(P.T_in * P.invW_in * W, T[it]);
+    }
+}
+
+// the +-2 FD lines and the 8 LB neighbours of point p0 are fluid cells of the domain
+template <int SX>
+__device__ __forceinline__ bool interior_point(const uint8_t* mask, int p0)
+{
+    bool fast = !mask[p0];
+#pragma unroll
+    for (int j = 1; j <= 2; ++j)
+        fast = fast && !mask[p0 + j] && !mask[p0 - j] && !mask[p0 + j * SX] && !mask[p0 - j * SX];
+    return fast && !mask[p0 + SX + 1] && !mask[p0 + SX - 1] && !mask[p0 - SX + 1] && !mask[p0 - SX - 1];
+}
+
 // body of the 2-D tile kernels.  WALLS == false: the interior cells of
 // every tile.  WALLS == true: only the cells next to in-domain solid cells
 // (or walls that act like them), in the tiles listed in `tiles`.
@@ -191,67 +313,23 @@ __device__ __forceinline__ void tiled2d_body(const StepParams<R>& P, const S* __
     const int x0 = bx * TX, y0 = by * TY;
     const int tid = threadIdx.x + TX * threadIdx.y;
     const long long N = P.N;
-    // stage the tile and its halo (points outside the domain are marked 2
-    // and never read by a fast-path cell)
-    for (int pt = tid; pt < NPT; pt += TX * TY) {
-        const int sx = pt % SX, sy = pt / SX;
-        int gx = x0 + sx - 2, gy = y0 + sy - 2;
-        // across a periodic face the halo holds the wrapped cells
-        // (at most two periods away: the halo is two cells wide)
-        if (P.bc[0] == BC_PERIODIC) {
-            if (gx < 0) gx += P.nx;
-            if (gx < 0) gx += P.nx;
-            if (gx >= P.nx) gx -= P.nx;
-            if (gx >= P.nx) gx -= P.nx;
-        }
-        if (P.bc[2] == BC_PERIODIC) {
-            if (gy < 0) gy += P.ny;
-            if (gy < 0) gy += P.ny;
-            if (gy >= P.ny) gy -= P.ny;
-            if (gy >= P.ny) gy -= P.ny;
-        }
-        if (gx < 0 || gx >= P.nx || gy < 0 || gy >= P.ny) {
-            uint8_t m = 2;
-            if constexpr (WALLS) {  // beyond walls that act like the solid cells
-                const bool okx = gx >= 0 && gx < P.nx ? true : P.face_solid[gx < 0 ? 0 : 1];
-                const bool oky = gy >= 0 && gy < P.ny ? true : P.face_solid[gy < 0 ? 2 : 3];
-                if (okx && oky) m = 1;
-            }
-            sm.mask[pt] = m;
-            continue;
-        }
-        const long long c = (long long)gx + (long long)P.nx * gy;
-        const uint8_t s = solid[c];
-        sm.mask[pt] = s ? 1 : 0;
-        if (s) continue;
-        const R T = R(T_in[c]);
-        R Y[NSP];
-#pragma unroll
-        for (int k = 0; k < NSP; ++k) Y[k] = R(Y_in[(long long)k * N + c]);
-        const R invW = inv_molar_mass(P, Y);
-        const R W = fdiv(R(1), invW);
-        sm.T[pt] = T;
-#pragma unroll
-        for (int k = 0; k < NSP; ++k) {
-            sm.Y[k * NPT + pt] = Y[k];
-            sm.X[k * NPT + pt] = Y[k] * P.inv_Wk[k] * W;
-        }
-        sm.invW[pt] = invW;
-        sm.rho[pt] = fdiv(P.T_in * P.invW_in * W, T);
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    const bool inside = x < P.nx && y < P.ny;
+    const long long c = (long long)x + (long long)P.nx * y;
+    R g[9];
+    // a1 for the interior tiles: issued before the staging, so that the
+    // population loads are in flight while the tile is staged
+    if constexpr (!WALLS) {
+        if (inside) pull_interior<S, R>(P, g_in, c, x, y, g);
     }
+    stage_tile2d<S, R, TX, TY, WALLS, TX * TY>(P, sm, x0, y0, tid, T_in, Y_in, solid);
     __syncthreads();
 
-    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
-    if (x >= P.nx || y >= P.ny) return;
+    if (!inside) return;
     const int p0 = (threadIdx.y + 2) * SX + threadIdx.x + 2;
     if (sm.mask[p0]) return;  // solid
-    const long long c = (long long)x + (long long)P.nx * y;
     // fast path: the +-2 lines and the 8 neighbours are fluid cells of the domain
-    bool fast = true;
-#pragma unroll
-    for (int j = 1; j <= 2; ++j)
-        fast = fast && !sm.mask[p0 + j] && !sm.mask[p0 - j] && !sm.mask[p0 + j * SX] && !sm.mask[p0 - j * SX];
-    fast = fast && !sm.mask[p0 + SX + 1] && !sm.mask[p0 + SX - 1] && !sm.mask[p0 - SX + 1] && !sm.mask[p0 - SX - 1];
+    const bool fast = interior_point<SX>(sm.mask, p0);
     if constexpr (WALLS) {
         // next to in-domain solid cells only (staircase walls); the interior
         // cells belong to the plain tile kernel, the rest to the boundary list
@@ -267,11 +345,9 @@ __device__ __forceinline__ void tiled2d_body(const StepParams<R>& P, const S* __
     } else {
         if (!fast) return;  // boundary cell: another kernel updates it
     }
-    // a1: pull from the neighbours (Eq. 8), half-way bounce-back from an
-    // in-domain solid neighbour (Eq. 28) in the wall-aware variants
-    R g[9];
-    {
-        // offsets of the x-1, x+1, y-1, y+1 neighbours, wrapped on periodic axes
+    // a1 for the wall tiles: pull from the neighbours (Eq. 8), half-way
+    // bounce-back from an in-domain solid neighbour (Eq. 28)
+    if constexpr (WALLS) {
         const int oxm = x == 0 ? P.nx - 1 : -1, oxp = x == P.nx - 1 ? 1 - P.nx : 1;
         const int oym = y == 0 ? (P.ny - 1) * P.nx : -P.nx, oyp = y == P.ny - 1 ? (1 - P.ny) * P.nx : P.nx;
         const S* gc = g_in + c;
@@ -280,9 +356,7 @@ __device__ __forceinline__ void tiled2d_body(const StepParams<R>& P, const S* __
             const int ox = cx_of(i) > 0 ? oxm : (cx_of(i) < 0 ? oxp : 0);
             const int oy = cy_of(i) > 0 ? oym : (cy_of(i) < 0 ? oyp : 0);
             long long off = (long long)i * N + (ox + oy);
-            if constexpr (WALLS) {
-                if (sm.mask[p0 - cx_of(i) - cy_of(i) * SX]) off = (long long)opposite<2>(i) * N;
-            }
+            if (sm.mask[p0 - cx_of(i) - cy_of(i) * SX]) off = (long long)opposite<2>(i) * N;
             g[i] = R(__ldg(gc + off));
         }
     }
@@ -315,7 +389,7 @@ __device__ __forceinline__ void tiled2d_body(const StepParams<R>& P, const S* __
         fd_axis_smem<R>(P, sm, NPT, p0, SX, 1, u[1], T0, Y0, invW0, rho0, acc);
     }
     // a6
-    const R q = arrhenius(P, T0, Y0[P.fuel], Y0[P.oxid]);
+    const R q = arrhenius(P, T0, pick_species(Y0, P.fuel), pick_species(Y0, P.oxid));
     const R reac_T = P.Q_cp * q;
     // a7
     const R DT = acc.diff_T + reac_T;

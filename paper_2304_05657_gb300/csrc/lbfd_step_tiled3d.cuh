@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(TX * TY) step_kernel_tiled3d(StepParams<R> P, 
                 fd_axis_pts<R>(P, sm, NPT, py, 1, u[1], Y0, invW0, rho0, acc);
                 fd_axis_pts<R>(P, sm, NPT, pz, 2, u[2], Y0, invW0, rho0, acc);
             }
-            const R q = arrhenius(P, T0, Y0[P.fuel], Y0[P.oxid]);
+            const R q = arrhenius(P, T0, pick_species(Y0, P.fuel), pick_species(Y0, P.oxid));
             const R DT = acc.diff_T + P.Q_cp * q;
             T_out[c] = S(T0 + (DT - acc.conv_T));
             R lam_Y = R(0);
