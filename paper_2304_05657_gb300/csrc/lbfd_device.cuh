@@ -15,6 +15,11 @@
 
 namespace lbfd {
 
+// Fast division: the hardware reciprocal path in FP32 (about 2 ulp, for
+// divisors of normal magnitude), IEEE division in FP64.
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+
 enum { BC_PERIODIC = 0, BC_WALL_ADIABATIC = 1, BC_WALL_ISOTHERMAL = 2, BC_INLET = 3, BC_OUTLET = 4,
        BC_OUTLET_PRESSURE = 5 };
 enum { PT_FLUID = 0, PT_SOLID = 16 };
@@ -110,7 +115,7 @@ __device__ __forceinline__ R pick_species(const R* Y, int k)
 template <typename R>
 __device__ __forceinline__ R eos(const StepParams<R>& P, R T, R invW)
 {
-    return P.T_in * P.invW_in / (T * invW);
+    return fdiv(P.T_in * P.invW_in, T * invW);
 }
 
 // Single-step rate per unit mass of fuel, per step.  The mixed form
@@ -172,10 +177,6 @@ __device__ __forceinline__ R weno3_deriv(const R* v, R u, R eps)
     return weno3_face(v[4], v[3], v[2], eps) - weno3_face(v[3], v[2], v[1], eps);
 }
 
-// Fast division: the hardware reciprocal path in FP32 (about 2 ulp, for
-// divisors of normal magnitude), IEEE division in FP64.
-__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
-__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
 
 // WENO3 derivative without a branch on the sign of u: for u < 0 the line is
 // mirrored and the result negated (the two upwind formulas are mirror

@@ -75,7 +75,7 @@ __device__ __forceinline__ R pull_general(const StepParams<R>& P, int i, const i
                 const int cj = ccomp<DIM>(j, a);
                 if (cj != 0) m += R(cj) * R(g[(long long)j * N + c]);
             }
-            uc[a] = m * R(3) / rho_cell;
+            uc[a] = m * fdiv(R(3), rho_cell);
         }
         R cu = R(0), uu = R(0);
 #pragma unroll
@@ -96,7 +96,7 @@ __device__ __forceinline__ R pull_general(const StepParams<R>& P, int i, const i
             const int cj = ccomp<DIM>(j, a) * ns;
             if (cj != 0) mom += R(cj) * R(g[(long long)j * N + c]);
         }
-        const R un = mom / (rho_cell * (R(1) / R(3)));
+        const R un = fdiv(R(3) * mom, rho_cell);
         int q[3] = {p[0], p[1], p[2]};
         q[a] -= ns;
         R inner = R(g[(long long)i * N + c]);
@@ -284,27 +284,30 @@ __device__ __forceinline__ void fd_axis(const StepParams<R>& P, int a, int near,
 {
     const R drho = fd_d1(rhol);
     acc.grad_rho[a] = drho;
-    const R drho_r = drho / rho0;
+    const R drho_r = fdiv(drho, rho0);
     // temperature: convection without correction, diffusion (Eq. 7)
-    acc.conv_T += u_a * (near ? fd_c2(Tl) : weno3_deriv(Tl, u_a, P.epsT));
+    acc.conv_T += u_a * (near ? fd_c2(Tl) : weno3_deriv_fast(Tl, u_a, P.epsT));
     acc.diff_T += P.alpha * (fd_d2(Tl) + drho_r * fd_d1(Tl));
     // species convection with the correction of Eq. 26
     R Lk[NSP], sumL = R(0);
 #pragma unroll
     for (int k = 0; k < NSP; ++k) {
-        Lk[k] = near ? fd_c2(Yl[k]) : weno3_deriv(Yl[k], u_a, P.epsY);
+        Lk[k] = near ? fd_c2(Yl[k]) : weno3_deriv_fast(Yl[k], u_a, P.epsY);
         sumL += Lk[k];
     }
 #pragma unroll
     for (int k = 0; k < NSP; ++k) acc.conv_Y[k] += u_a * (Lk[k] - Y0[k] * sumL);
     // species diffusion with the correction velocity (Eq. 1-2), expanded
     const R dinvW = fd_d1(invWl);
+    R Wl[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) Wl[j] = fdiv(R(1), invWl[j]);
     R m[NSP], dm[NSP], dY[NSP], M = R(0), dM = R(0);
 #pragma unroll
     for (int k = 0; k < NSP; ++k) {
         R Xl[5];
 #pragma unroll
-        for (int j = 0; j < 5; ++j) Xl[j] = Yl[k][j] * P.inv_Wk[k] / invWl[j];
+        for (int j = 0; j < 5; ++j) Xl[j] = Yl[k][j] * P.inv_Wk[k] * Wl[j];
         const R dX = fd_d1(Xl), d2X = fd_d2(Xl);
         m[k] = P.a_diff[k] * invW0 * dX;
         dm[k] = P.a_diff[k] * (invW0 * d2X + dinvW * dX);
@@ -343,7 +346,7 @@ __device__ __forceinline__ void cell_step_general(const StepParams<R>& P, const 
     // a2: velocity, Eq. 13b
     R u[3] = {R(0), R(0), R(0)};
     {
-        const R inv = R(3) / rho0;
+        const R inv = fdiv(R(3), rho0);
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
             R m = R(0);
@@ -388,7 +391,7 @@ __device__ __forceinline__ void cell_step_general(const StepParams<R>& P, const 
         Y_out[(long long)k * N + c] = S(Y0[k] + (DY - acc.conv_Y[k]));
         lam_Y += P.inv_Wk[k] * DY;
     }
-    const R Lam = DT / T0 + lam_Y / invW0;
+    const R Lam = fdiv(DT, T0) + fdiv(lam_Y, invW0);
     // a8-a9
     collide<DIM, R>(P, g, rho0, u, acc.grad_rho, Lam);
     // a10
