@@ -7,10 +7,12 @@
 // moves data and launches.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <iterator>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -37,6 +39,8 @@ struct lbfd_handle {
     long long nbnd;
     long long* bndf;      // the subset near domain faces (wall-aware 2-D tiles)
     long long nbndf;
+    long long* bndw;      // 3-D: the others (next to in-domain solids only)
+    long long nbndw;
     int* wtiles;          // tiles holding the other boundary cells (2-D)
     long long nwtiles;
     double* red;          // device reduction scratch
@@ -215,6 +219,7 @@ void free_handle(lbfd_handle* h)
     if (h->tmp) cudaFree(h->tmp);
     if (h->bnd) cudaFree(h->bnd);
     if (h->bndf) cudaFree(h->bndf);
+    if (h->bndw) cudaFree(h->bndw);
     if (h->wtiles) cudaFree(h->wtiles);
     void* curved[] = {h->link_row, h->link_q, h->ghost_row, h->gh_start, h->gh_idx, h->gh_w, h->gval};
     for (void* p : curved)
@@ -263,6 +268,14 @@ lbfd::BoundaryLists lists(const lbfd_handle* h)
     b.nface = curved ? h->nbnd : h->nbndf;
     b.wall_tiles = h->wtiles;
     b.nwall_tiles = curved ? 0 : h->nwtiles;
+    b.wall = nullptr;
+    b.nwall = 0;
+    if (h->dim == 3) {  // the general form takes curved walls in both lists
+        b.face = h->bndf;
+        b.nface = h->nbndf;
+        b.wall = h->bndw;
+        b.nwall = h->nbndw;
+    }
     return b;
 }
 
@@ -394,6 +407,20 @@ int lbfd_create(const lbfd_grid* grid, const uint8_t* solid_mask, const lbfd_mec
             cudaSuccess) {
             free_handle(h);
             return cuda_fail(e, "cudaMemcpy(boundary list)");
+        }
+    }
+    if (h->dim == 3) {  // all \ face (both sorted)
+        std::vector<long long> wl;
+        std::set_difference(lists_host[0].begin(), lists_host[0].end(), lists_host[1].begin(), lists_host[1].end(),
+                            std::back_inserter(wl));
+        h->nbndw = (long long)wl.size();
+        if (!wl.empty()) {
+            if ((e = cudaMalloc(&h->bndw, wl.size() * sizeof(long long))) != cudaSuccess ||
+                (e = cudaMemcpy(h->bndw, wl.data(), wl.size() * sizeof(long long), cudaMemcpyHostToDevice)) !=
+                    cudaSuccess) {
+                free_handle(h);
+                return cuda_fail(e, "wall list");
+            }
         }
     }
     if (h->dim == 2) {
@@ -531,10 +558,15 @@ int lbfd_launches_per_step(const lbfd_handle* h)
 {
     if (!h) return -1;
     const lbfd::BoundaryLists b = lists(h);
-    const bool wv = h->dim == 2 && h->variant >= 5 && b.nwall_tiles > 0;
-    const long long nb = wv ? b.nface : b.nall;
     int n = 1;
-    if (h->variant > 0 && h->precision != LBFD_TANGENT) n += (nb > 0 ? 1 : 0) + (wv ? 1 : 0);
+    if (h->variant > 0 && h->precision != LBFD_TANGENT) {
+        if (h->dim == 3) {
+            n += (b.nface > 0 ? 1 : 0) + (b.nwall > 0 ? 1 : 0);
+        } else {
+            const bool wv = h->variant >= 5 && b.nwall_tiles > 0;
+            n += ((wv ? b.nface : b.nall) > 0 ? 1 : 0) + (wv ? 1 : 0);
+        }
+    }
     return n + (h->nghost > 0 ? 1 : 0);
 }
 

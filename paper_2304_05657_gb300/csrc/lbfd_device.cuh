@@ -65,7 +65,9 @@ __device__ __forceinline__ long long cell_of(const StepParams<R>& P, int x, int 
 
 // Classify a point that differs from a fluid cell along one or more axes.
 // Periodic axes wrap; a crossed non-periodic face returns its bc type.
-template <int DIM, typename R>
+// FACES == false: the caller guarantees that no non-periodic face is
+// crossed (cells whose stencils stay inside the domain up to periodic wrap).
+template <int DIM, typename R, bool FACES = true>
 __device__ __forceinline__ int classify(const StepParams<R>& P, int q[3], const uint8_t* __restrict__ solid,
                                         long long* idx, int* face)
 {
@@ -77,10 +79,10 @@ __device__ __forceinline__ int classify(const StepParams<R>& P, int q[3], const 
         if (q[a] < 0) f = 2 * a;
         else if (q[a] >= n) f = 2 * a + 1;
         if (f < 0) continue;
-        if (P.bc[f] == BC_PERIODIC) q[a] = ((q[a] % n) + n) % n;  // extents may be < 3
+        if (!FACES || P.bc[f] == BC_PERIODIC) q[a] = ((q[a] % n) + n) % n;  // extents may be < 3
         else if (wall < 0) wall = f;
     }
-    if (wall >= 0) {
+    if (FACES && wall >= 0) {
         *face = wall;
         return P.bc[wall];
     }

@@ -63,6 +63,8 @@ struct BoundaryLists {
     long long nface;
     const int* wall_tiles;  // 2-D tiles of WALL_TX x WALL_TY cells holding cells of all \ face
     long long nwall_tiles;
+    const long long* wall;  // 3-D: all \ face, cells whose stencils reach no non-periodic face
+    long long nwall;
 };
 
 // tile shape of the 2-D wall-tile kernel
@@ -78,8 +80,8 @@ int num_variants(int dim);
 
 // 3-D tile kernels (variants 1..2 in 3-D), lbfd_step3d.cu
 cudaError_t launch_step3d_tiled(int precision, int variant, const StepParams<double>& Pd, const StepParams<float>& Pf,
-                                StateView in, StateView out, const uint8_t* solid, const long long* bnd,
-                                long long nbnd, const SideStream& side, cudaStream_t stream);
+                                StateView in, StateView out, const uint8_t* solid, const BoundaryLists& b,
+                                const SideStream& side, cudaStream_t stream);
 
 // Fluid cells that are not interior for the tile kernels (host, at create);
 // faces_only (2-D): only cells whose stencil leaves the domain.

@@ -158,7 +158,7 @@ cudaError_t launch_step(int dim, int precision, int variant, const StepParams<do
 {
     if (variant < 0 || variant >= num_variants(dim)) return cudaErrorInvalidValue;
     if (dim == 3 && variant > 0)
-        return launch_step3d_tiled(precision, variant, Pd, Pf, in, out, solid, b.all, b.nall, side, stream);
+        return launch_step3d_tiled(precision, variant, Pd, Pf, in, out, solid, b, side, stream);
     if (precision == 0) {
         if (dim == 2) return launch_2d<double, double>(variant, Pd, in, out, solid, b, side, stream);
         return launch_general<3, double, double>(Pd, in, out, solid, stream);
@@ -182,7 +182,9 @@ void boundary_cells(int dim, int nx, int ny, int nz, const int* bc, const uint8_
     const bool px = bc[0] == 0, py = bc[2] == 0, pz = bc[4] == 0;  // periodic axes
     if (dim == 3) {
         // the 3-D tile kernel's fast-path condition: +-2 along the three axes
-        // and the 26 neighbours are fluid cells (periodic axes wrapped)
+        // and the 26 neighbours are fluid cells (periodic axes wrapped);
+        // faces_only: only the cells whose stencil leaves the domain across
+        // a non-periodic face
         for (int z = 0; z < nz; ++z)
             for (int y = 0; y < ny; ++y)
                 for (int x = 0; x < nx; ++x) {
@@ -199,7 +201,8 @@ void boundary_cells(int dim, int nx, int ny, int nz, const int* bc, const uint8_
                                 bool out = false;
                                 const int qx = wrap(x + dx, nx, px, &out), qy = wrap(y + dy, ny, py, &out),
                                           qz = wrap(z + dz, nz, pz, &out);
-                                if (out || solid[(long long)qx + (long long)nx * ((long long)qy + (long long)ny * qz)])
+                                if (out || (!faces_only &&
+                                            solid[(long long)qx + (long long)nx * ((long long)qy + (long long)ny * qz)]))
                                     fast = false;
                             }
                     if (!fast) out.push_back(c);

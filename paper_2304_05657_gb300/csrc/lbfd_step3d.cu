@@ -4,24 +4,35 @@
 
 namespace lbfd {
 
+// The interior cells go to the tile kernel; on the side stream (same input
+// state, disjoint writes) the general form takes the cells near domain
+// faces (b.face) and, with the face rules compiled out, the cells next to
+// in-domain solids (b.wall).
 template <typename S, typename R, int TX, int TY, int ZC>
 static cudaError_t launch_t3(const StepParams<R>& P, StateView in, StateView out, const uint8_t* solid,
-                             const long long* bnd, long long nbnd, const SideStream& side, cudaStream_t stream)
+                             const BoundaryLists& b, const SideStream& side, cudaStream_t stream)
 {
     constexpr size_t smem = tile3_smem_bytes<R, TX, TY>();
     auto kern = step_kernel_tiled3d<S, R, TX, TY, ZC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const bool fork = nbnd > 0 && side.stream != nullptr;
+    const bool fork = (b.nface > 0 || b.nwall > 0) && side.stream != nullptr;
     if (fork) {
         if ((e = cudaEventRecord(side.fork, stream)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(side.stream, side.fork, 0)) != cudaSuccess) return e;
     }
-    if (nbnd > 0) {
-        const unsigned nb = (unsigned)((nbnd + 127) / 128);
-        e = launch_prio(step_kernel_boundary<3, S, R>, dim3(nb), dim3(128), 0, fork ? side.stream : stream,
-                        fork ? side.priority : 0, P, (const S*)in.g, (S*)out.g, (const S*)in.T, (S*)out.T,
-                        (const S*)in.Y, (S*)out.Y, solid, bnd, nbnd);
+    cudaStream_t bs = fork ? side.stream : stream;
+    const int prio = fork ? side.priority : 0;
+    if (b.nface > 0) {
+        const unsigned nb = (unsigned)((b.nface + 127) / 128);
+        e = launch_prio(step_kernel_boundary<3, S, R, true>, dim3(nb), dim3(128), 0, bs, prio, P, (const S*)in.g,
+                        (S*)out.g, (const S*)in.T, (S*)out.T, (const S*)in.Y, (S*)out.Y, solid, b.face, b.nface);
+        if (e != cudaSuccess) return e;
+    }
+    if (b.nwall > 0) {
+        const unsigned nb = (unsigned)((b.nwall + 127) / 128);
+        e = launch_prio(step_kernel_boundary<3, S, R, false>, dim3(nb), dim3(128), 0, bs, prio, P, (const S*)in.g,
+                        (S*)out.g, (const S*)in.T, (S*)out.T, (const S*)in.Y, (S*)out.Y, solid, b.wall, b.nwall);
         if (e != cudaSuccess) return e;
     }
     dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY, (P.nz + ZC - 1) / ZC);
@@ -37,22 +48,22 @@ static cudaError_t launch_t3(const StepParams<R>& P, StateView in, StateView out
 
 template <typename S, typename R>
 static cudaError_t launch_3d_tiles(int variant, const StepParams<R>& P, StateView in, StateView out,
-                                   const uint8_t* solid, const long long* bnd, long long nbnd, const SideStream& side,
+                                   const uint8_t* solid, const BoundaryLists& b, const SideStream& side,
                                    cudaStream_t stream)
 {
     switch (variant) {
-    case 1: return launch_t3<S, R, 32, 4, 16>(P, in, out, solid, bnd, nbnd, side, stream);
-    case 2: return launch_t3<S, R, 32, 4, 32>(P, in, out, solid, bnd, nbnd, side, stream);
+    case 1: return launch_t3<S, R, 32, 4, 16>(P, in, out, solid, b, side, stream);
+    case 2: return launch_t3<S, R, 32, 4, 32>(P, in, out, solid, b, side, stream);
     default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_step3d_tiled(int precision, int variant, const StepParams<double>& Pd, const StepParams<float>& Pf,
-                                StateView in, StateView out, const uint8_t* solid, const long long* bnd,
-                                long long nbnd, const SideStream& side, cudaStream_t stream)
+                                StateView in, StateView out, const uint8_t* solid, const BoundaryLists& b,
+                                const SideStream& side, cudaStream_t stream)
 {
-    if (precision == 0) return launch_3d_tiles<double, double>(variant, Pd, in, out, solid, bnd, nbnd, side, stream);
-    return launch_3d_tiles<float, float>(variant, Pf, in, out, solid, bnd, nbnd, side, stream);
+    if (precision == 0) return launch_3d_tiles<double, double>(variant, Pd, in, out, solid, b, side, stream);
+    return launch_3d_tiles<float, float>(variant, Pf, in, out, solid, b, side, stream);
 }
 
 }  // namespace lbfd

@@ -19,7 +19,7 @@ namespace lbfd {
 // ---------------------------------------------------------------------------
 // a1: pull one population with the boundary rules
 // ---------------------------------------------------------------------------
-template <int DIM, typename S, typename R>
+template <int DIM, typename S, typename R, bool FACES = true>
 __device__ __forceinline__ R pull_general(const StepParams<R>& P, int i, const int p[3], long long c,
                                           const S* __restrict__ g, const uint8_t* __restrict__ solid,
                                           R rho_cell)
@@ -35,7 +35,7 @@ __device__ __forceinline__ R pull_general(const StepParams<R>& P, int i, const i
         else if (src[a] >= n) f = 2 * a + 1;
         if (f < 0) continue;
         const int t = P.bc[f];
-        if (t == BC_PERIODIC) src[a] = ((src[a] % n) + n) % n;
+        if (!FACES || t == BC_PERIODIC) src[a] = ((src[a] % n) + n) % n;
         else if (t == BC_INLET) { if (inlet < 0) inlet = f; }
         else if (t == BC_OUTLET || t == BC_OUTLET_PRESSURE) { if (outlet < 0) outlet = f; }
         else wall = 1;
@@ -117,7 +117,7 @@ __device__ __forceinline__ R pull_general(const StepParams<R>& P, int i, const i
             int r[3] = {p[0] + ccomp<DIM>(i, 0), p[1] + ccomp<DIM>(i, 1), DIM == 3 ? p[2] + ccomp<DIM>(i, 2) : 0};
             long long ridx = 0;
             int face = -1;
-            if (classify<DIM>(P, r, solid, &ridx, &face) == PT_FLUID)
+            if (classify<DIM, R, FACES>(P, r, solid, &ridx, &face) == PT_FLUID)
                 return R(2) * q * R(g[(long long)ib * N + c]) + (R(1) - R(2) * q) * R(g[(long long)ib * N + ridx]);
             return R(g[(long long)ib * N + c]);
         }
@@ -155,7 +155,7 @@ __device__ __forceinline__ void ghost_mode(const StepParams<R>& P, int type, int
     }
 }
 
-template <int DIM, typename R>
+template <int DIM, typename R, bool FACES = true>
 __device__ __forceinline__ void build_line(const StepParams<R>& P, const int p[3], long long c, int a,
                                            const uint8_t* __restrict__ solid, LineDesc<R>& L)
 {
@@ -173,7 +173,7 @@ __device__ __forceinline__ void build_line(const StepParams<R>& P, const int p[3
             q[a] += side * j;
             long long idx = 0;
             int face = -1;
-            const int t = classify<DIM>(P, q, solid, &idx, &face);
+            const int t = classify<DIM, R, FACES>(P, q, solid, &idx, &face);
             if (t == PT_FLUID) {
                 L.src[2 + side * j] = idx;
                 L.mode[2 + side * j] = G_DIRECT;
@@ -197,7 +197,7 @@ __device__ __forceinline__ void build_line(const StepParams<R>& P, const int p[3
                 q[a] += side * j;
                 long long idx = 0;
                 int face = -1;
-                if (classify<DIM>(P, q, solid, &idx, &face) == PT_SOLID && P.ghost_row[idx] >= 0) {
+                if (classify<DIM, R, FACES>(P, q, solid, &idx, &face) == PT_SOLID && P.ghost_row[idx] >= 0) {
                     L.src[2 + side * j] = P.ghost_row[idx];
                     L.mode[2 + side * j] = G_CURVED;
                     L.TB[2 + side * j] = R(0);
@@ -213,7 +213,7 @@ __device__ __forceinline__ void build_line(const StepParams<R>& P, const int p[3
                 q[a] -= side;
                 long long idx = 0;
                 int face = -1;
-                ms = (classify<DIM>(P, q, solid, &idx, &face) == PT_FLUID) ? idx : c;
+                ms = (classify<DIM, R, FACES>(P, q, solid, &idx, &face) == PT_FLUID) ? idx : c;
             }
             L.src[2 + side * j] = ms;
             L.mode[2 + side * j] = mode;
@@ -321,9 +321,11 @@ __device__ __forceinline__ void fd_axis(const StepParams<R>& P, int a, int near,
 }
 
 // ---------------------------------------------------------------------------
-// The whole coupled update of one fluid cell (general form).
+// The whole coupled update of one fluid cell (general form).  FACES ==
+// false: a cell whose stencils reach no non-periodic domain face (the face
+// rules are compiled out).
 // ---------------------------------------------------------------------------
-template <int DIM, typename S, typename R>
+template <int DIM, typename S, typename R, bool FACES = true>
 __device__ __forceinline__ void cell_step_general(const StepParams<R>& P, const int p[3], long long c,
                                                   const S* __restrict__ g_in, S* __restrict__ g_out,
                                                   const S* __restrict__ T_in, S* __restrict__ T_out,
@@ -342,7 +344,7 @@ __device__ __forceinline__ void cell_step_general(const StepParams<R>& P, const 
     // a1
     R g[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) g[i] = pull_general<DIM, S, R>(P, i, p, c, g_in, solid, rho0);
+    for (int i = 0; i < Q; ++i) g[i] = pull_general<DIM, S, R, FACES>(P, i, p, c, g_in, solid, rho0);
     // a2: velocity, Eq. 13b
     R u[3] = {R(0), R(0), R(0)};
     {
@@ -367,7 +369,7 @@ __device__ __forceinline__ void cell_step_general(const StepParams<R>& P, const 
 #pragma unroll 1
     for (int a = 0; a < DIM; ++a) {
         LineDesc<R> L;
-        build_line<DIM, R>(P, p, c, a, solid, L);
+        build_line<DIM, R, FACES>(P, p, c, a, solid, L);
         R Tl[5], Yl[NSP][5], invWl[5], rhol[5];
 #pragma unroll
         for (int j = 0; j < 5; ++j) {

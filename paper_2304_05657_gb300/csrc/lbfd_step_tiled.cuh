@@ -429,8 +429,9 @@ __global__ void __launch_bounds__(TX * TY)
     tiled2d_body<S, R, TX, TY, true>(P, g_in, g_out, T_in, T_out, Y_in, Y_out, solid, tiles);
 }
 
-// The cells the tiled kernel leaves out: general form over a cell list.
-template <int DIM, typename S, typename R>
+// The cells the tiled kernel leaves out: general form over a cell list
+// (FACES == false: cells whose stencils reach no non-periodic face).
+template <int DIM, typename S, typename R, bool FACES = true>
 __global__ void __launch_bounds__(128) step_kernel_boundary(StepParams<R> P, const S* __restrict__ g_in,
                                                             S* __restrict__ g_out, const S* __restrict__ T_in,
                                                             S* __restrict__ T_out, const S* __restrict__ Y_in,
@@ -445,7 +446,7 @@ __global__ void __launch_bounds__(128) step_kernel_boundary(StepParams<R> P, con
     const long long r = c / P.nx;
     p[1] = (int)(r % P.ny);
     p[2] = (int)(r / P.ny);
-    cell_step_general<DIM, S, R>(P, p, c, g_in, g_out, T_in, T_out, Y_in, Y_out, solid);
+    cell_step_general<DIM, S, R, FACES>(P, p, c, g_in, g_out, T_in, T_out, Y_in, Y_out, solid);
 }
 
 }  // namespace lbfd
