@@ -55,6 +55,9 @@ def workload(name: str, precision: str):
     elif name == "porous128x64x64":
         cfg, solid, T, Y = inputs.sphere_packing(nx=128, ny=64, nz=64, x_range=(16, 112))
         desc = "D3Q27 128x64x64 overlapping spheres r in [8,16], porosity 0.80 (profiling size)"
+    elif name == "porous256x128x128":
+        cfg, solid, T, Y = inputs.sphere_packing(nx=256, ny=128, nz=128, x_range=(32, 224))
+        desc = "D3Q27 256x128x128 overlapping spheres r in [8,16], porosity 0.80 (profiling size)"
     else:
         raise SystemExit(f"unknown workload {name}")
     cfg["precision"] = precision
@@ -75,6 +78,9 @@ def sample_workload(name: str, precision: str, length: int = 96):
         cfg, solid, T, Y = inputs.cylinder_burner(nx=256, ny=128, x_range=(64, 192))
         return cfg, solid, T, Y, "a 256x128 crop of the burner geometry"
     if name == "porous128x64x64":
+        cfg, solid, T, Y = inputs.sphere_packing(nx=32, ny=16, nz=16, x_range=(4, 28), r_range=(2.0, 4.0))
+        return cfg, solid, T, Y, "a 32x16x16 sphere packing"
+    if name == "porous256x128x128":
         cfg, solid, T, Y = inputs.sphere_packing(nx=32, ny=16, nz=16, x_range=(4, 28), r_range=(2.0, 4.0))
         return cfg, solid, T, Y, "a 32x16x16 sphere packing"
     cfg, solid, T, Y = inputs.sphere_packing(nx=32, ny=16, nz=16, x_range=(4, 28), r_range=(2.0, 4.0))
@@ -421,7 +427,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="batched16x1024",
                     choices=["batched16x1024", "channel256x32", "burner2048x512", "porous512x256x256",
-                             "porous128x64x64"])
+                             "porous128x64x64", "porous256x128x128"])
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--baseline-steps", type=int, default=40)

@@ -182,20 +182,27 @@ int lbfd_step(lbfd_handle* h, int n);
 int lbfd_step_graph(lbfd_handle* h, int n);
 
 /* Kernel variants of the step: 0 is the general form (any cell, D2Q9 and
- * D3Q27); in 2-D, 1..4 are shared-memory tiles of 32x8, 32x4, 64x4 and
- * 32x16 interior cells and 5..8 the same tiles plus a second tile kernel
- * (over the 32x4 tiles that need it) for the cells next to in-domain solid
- * cells (staircase walls, from shared memory); in 3-D, 1..2 are 32x4 columns marching through 16
- * or 32 z-planes with a five-plane shared-memory ring.  The tile variants
- * are followed by the general form over the list of boundary cells
- * (computed at create).  All variants compute the same step up to rounding
- * order.  Default: 1 (0 for LBFD_TANGENT, which has the general form only). */
+ * D3Q27).  In 2-D (13 variants), 1..4 are shared-memory tiles of 32x8,
+ * 32x4, 64x4 and 32x16 interior cells; 5..8 the same tiles plus a second
+ * tile kernel (over the 32x4 tiles that need it) for the cells next to
+ * in-domain solid cells (staircase walls, from shared memory); 9..12 as 5..8
+ * with two interior cells per thread in packed FP32 arithmetic (tiles of
+ * 32x8, 64x8, 32x8, 64x4; the FP64 form runs them one cell per thread).
+ * In 3-D (4 variants), 1..2 are 32x4 columns marching through 16 or 32
+ * z-planes with a five-plane shared-memory ring, 3 is 1 with the registers
+ * capped for four blocks per SM.  The cells the tiles leave out go through
+ * the general form over lists computed at create (in 3-D, one list for
+ * cells near domain faces and one, with the face rules compiled out, for
+ * cells next to in-domain solids).  All variants compute the same step up
+ * to rounding order.  Default: 1 (0 for LBFD_TANGENT, which has the
+ * general form only). */
 int lbfd_num_variants(const lbfd_handle* h);
 int lbfd_get_variant(const lbfd_handle* h);
 int lbfd_set_variant(lbfd_handle* h, int variant);
 /* Kernel launches one step makes with the current variant: the tile
- * variants launch the tile kernel and, when the grid has boundary cells,
- * a second kernel over the list of those cells. */
+ * variants launch the tile kernel plus one kernel per non-empty list of
+ * boundary cells (and the wall-tile kernel in 2-D variants 5..12); curved
+ * walls add the ghost-fill kernel. */
 int lbfd_launches_per_step(const lbfd_handle* h);
 
 /* Autotuner: time every variant over `reps` launches on the current state

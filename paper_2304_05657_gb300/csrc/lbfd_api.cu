@@ -376,9 +376,8 @@ int lbfd_create(const lbfd_grid* grid, const uint8_t* solid_mask, const lbfd_mec
         free_handle(h);
         return cuda_fail(e, "cudaMemcpy(mask)");
     }
-    int least_prio = 0;
     if (h->precision != LBFD_TANGENT &&
-        ((e = cudaDeviceGetStreamPriorityRange(&least_prio, &h->side.priority)) != cudaSuccess ||
+        ((e = cudaDeviceGetStreamPriorityRange(&h->side.low, &h->side.priority)) != cudaSuccess ||
          (e = cudaStreamCreateWithPriority(&h->side.stream, cudaStreamNonBlocking, h->side.priority)) !=
              cudaSuccess ||
          (e = cudaEventCreateWithFlags(&h->side.fork, cudaEventDisableTiming)) != cudaSuccess ||

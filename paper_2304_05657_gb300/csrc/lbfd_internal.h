@@ -29,6 +29,7 @@ struct SideStream {
     cudaStream_t stream;
     cudaEvent_t fork, join;
     int priority;  // the device's greatest stream priority
+    int low;       // and its least
 };
 
 // Launch on the side stream at its priority, so that the block scheduler

@@ -80,7 +80,10 @@ static cudaError_t launch_tiled(const StepParams<R>& P, StateView in, StateView 
         if (e != cudaSuccess) return e;
     }
     if (walls) {
-        e = launch_prio(wkern, dim3((unsigned)b.nwall_tiles), dim3(WALL_TX, WALL_TY), wsmem, bs, prio, P,
+        // after the boundary kernel, at the least priority: its blocks fill
+        // the SMs that the tile grid leaves idle in its last wave
+        e = launch_prio(wkern, dim3((unsigned)b.nwall_tiles), dim3(WALL_TX, WALL_TY), wsmem, bs,
+                        fork ? side.low : 0, P,
                         (const S*)in.g, (S*)out.g, (const S*)in.T, (S*)out.T, (const S*)in.Y, (S*)out.Y, solid,
                         (const int*)b.wall_tiles);
         if (e != cudaSuccess) return e;
@@ -131,7 +134,7 @@ static cudaError_t launch_2d(int variant, const StepParams<R>& P, StateView in, 
     }
 }
 
-int num_variants(int dim) { return dim == 2 ? 13 : 3; }
+int num_variants(int dim) { return dim == 2 ? 13 : 4; }
 
 void wall_tiles(int nx, int ny, const std::vector<long long>& all, const std::vector<long long>& face,
                 std::vector<int>& out)

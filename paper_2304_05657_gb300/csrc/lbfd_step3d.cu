@@ -8,12 +8,20 @@ namespace lbfd {
 // state, disjoint writes) the general form takes the cells near domain
 // faces (b.face) and, with the face rules compiled out, the cells next to
 // in-domain solids (b.wall).
-template <typename S, typename R, int TX, int TY, int ZC>
+// the tile kernel instance: MINB > 0 caps its registers for MINB blocks per SM
+template <typename S, typename R, int TX, int TY, int ZC, int MINB>
+static auto tile3_kernel()
+{
+    if constexpr (MINB > 0) return step_kernel_tiled3d_capped<S, R, TX, TY, ZC, MINB>;
+    else return step_kernel_tiled3d<S, R, TX, TY, ZC>;
+}
+
+template <typename S, typename R, int TX, int TY, int ZC, int MINB = 0>
 static cudaError_t launch_t3(const StepParams<R>& P, StateView in, StateView out, const uint8_t* solid,
                              const BoundaryLists& b, const SideStream& side, cudaStream_t stream)
 {
     constexpr size_t smem = tile3_smem_bytes<R, TX, TY>();
-    auto kern = step_kernel_tiled3d<S, R, TX, TY, ZC>;
+    auto kern = tile3_kernel<S, R, TX, TY, ZC, MINB>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const bool fork = (b.nface > 0 || b.nwall > 0) && side.stream != nullptr;
@@ -54,6 +62,8 @@ static cudaError_t launch_3d_tiles(int variant, const StepParams<R>& P, StateVie
     switch (variant) {
     case 1: return launch_t3<S, R, 32, 4, 16>(P, in, out, solid, b, side, stream);
     case 2: return launch_t3<S, R, 32, 4, 32>(P, in, out, solid, b, side, stream);
+    // variant 3: as 1 with the registers capped for four blocks per SM (FP32)
+    case 3: return launch_t3<S, R, 32, 4, 16, sizeof(R) == 4 ? 4 : 0>(P, in, out, solid, b, side, stream);
     default: return cudaErrorInvalidValue;
     }
 }

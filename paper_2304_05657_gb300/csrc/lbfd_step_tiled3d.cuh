@@ -28,16 +28,16 @@ __host__ __device__ constexpr size_t tile3_smem_bytes()
     return sizeof(R) * (size_t)Tile3Geom<TX, TY>::NPT * (4 + NSP) + (size_t)Tile3Geom<TX, TY>::NPT;
 }
 
-// FD terms along one axis from five explicit shared-memory points
+// FD terms along one axis from five explicit shared-memory points (the
+// X_k lines first, as in fd_axis_core); returns d rho / d x_a
 template <typename R>
-__device__ __forceinline__ void fd_axis_pts(const StepParams<R>& P, const TileSmem<R>& sm, int npt, const int* pts,
-                                            int a, R u_a, const R* Y0, R invW0, R rho0, FDAccum<R>& acc)
+__device__ __forceinline__ R fd_axis_pts(const StepParams<R>& P, const TileSmem<R>& sm, int npt, const int* pts,
+                                         R u_a, const R* Y0, R invW0, R rho0, FDAccum<R>& acc)
 {
     R v[5], w[5];
 #pragma unroll
     for (int j = 0; j < 5; ++j) v[j] = sm.rho[pts[j]];
     const R drho = fd_d1(v);
-    acc.grad_rho[a] = drho;
     const R drho_r = fdiv(drho, rho0);
 #pragma unroll
     for (int j = 0; j < 5; ++j) v[j] = sm.T[pts[j]];
@@ -46,30 +46,36 @@ __device__ __forceinline__ void fd_axis_pts(const StepParams<R>& P, const TileSm
 #pragma unroll
     for (int j = 0; j < 5; ++j) w[j] = sm.invW[pts[j]];
     const R dinvW = fd_d1(w);
-    R Lk[NSP], m[NSP], dm[NSP], dY[NSP], Wl[5];
-    R sumL = R(0), M = R(0), dM = R(0);
+    R Wl[5];
 #pragma unroll
     for (int j = 0; j < 5; ++j) Wl[j] = sm.X[pts[j]];  // W (the 3-D tile keeps W in the X slot)
+    R m[NSP], dm[NSP];
+    R M = R(0), dM = R(0);
 #pragma unroll
     for (int k = 0; k < NSP; ++k) {
 #pragma unroll
-        for (int j = 0; j < 5; ++j) v[j] = sm.Y[k * npt + pts[j]];
-        Lk[k] = weno3_deriv_fast(v, u_a, P.epsY);
-        sumL += Lk[k];
-        dY[k] = fd_d1(v);
-#pragma unroll
-        for (int j = 0; j < 5; ++j) v[j] *= P.inv_Wk[k] * Wl[j];  // X_k = Y_k W / W_k
+        for (int j = 0; j < 5; ++j) v[j] = sm.Y[k * npt + pts[j]] * P.inv_Wk[k] * Wl[j];  // X_k = Y_k W / W_k
         const R dX = fd_d1(v), d2X = fd_d2(v);
         m[k] = P.a_diff[k] * invW0 * dX;
         dm[k] = P.a_diff[k] * (invW0 * d2X + dinvW * dX);
         M += m[k];
         dM += dm[k];
     }
+    R sumL = R(0);
 #pragma unroll
     for (int k = 0; k < NSP; ++k) {
-        acc.conv_Y[k] += u_a * (Lk[k] - Y0[k] * sumL);
-        acc.diff_Y[k] += dm[k] - dY[k] * M - Y0[k] * dM + (m[k] - Y0[k] * M) * drho_r;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) v[j] = sm.Y[k * npt + pts[j]];
+        const R Lk = weno3_deriv_fast(v, u_a, P.epsY);
+        sumL += Lk;
+        const R dY = fd_d1(v);
+        acc.conv_Y[k] += u_a * Lk;
+        acc.diff_Y[k] += dm[k] - dY * M - Y0[k] * dM + (m[k] - Y0[k] * M) * drho_r;
     }
+    const R us = u_a * sumL;
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) acc.conv_Y[k] -= Y0[k] * us;
+    return drho;
 }
 
 // stage plane z (grid coordinate) into ring slot `slot`
@@ -81,44 +87,56 @@ __device__ __forceinline__ void stage_plane(const StepParams<R>& P, const TileSm
     using G = Tile3Geom<TX, TY>;
     constexpr int NPT = G::NPT;
     const long long N = P.N;
+    constexpr int NTHR = TX * TY, NIT = (G::NPP + NTHR - 1) / NTHR;
     const int tid = threadIdx.x + TX * threadIdx.y;
-    for (int q = tid; q < G::NPP; q += TX * TY) {
+    // all of this thread's global loads first, then the derived values
+    long long cell[NIT];  // -1: outside the domain
+    uint8_t s[NIT];
+    R T[NIT], Y[NIT][NSP];
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) {
+        const int q = tid + it * NTHR;
+        cell[it] = -1;
+        if (q >= G::NPP) continue;
         const int sx = q % G::SX, sy = q / G::SX;
         int gx = x0 + sx - 2, gy = y0 + sy - 2, gz = z;
-        const int pt = slot * G::NPP + q;
         // across a periodic face the halo holds the wrapped cells
         if ((gx < 0 || gx >= P.nx) && P.bc[0] == BC_PERIODIC) gx = ((gx % P.nx) + P.nx) % P.nx;
         if ((gy < 0 || gy >= P.ny) && P.bc[2] == BC_PERIODIC) gy = ((gy % P.ny) + P.ny) % P.ny;
         if ((gz < 0 || gz >= P.nz) && P.bc[4] == BC_PERIODIC) gz = ((gz % P.nz) + P.nz) % P.nz;
         if (gx < 0 || gx >= P.nx || gy < 0 || gy >= P.ny || gz < 0 || gz >= P.nz) {
-            sm.mask[pt] = 2;
+            sm.mask[slot * G::NPP + q] = 2;
             continue;
         }
         const long long c = (long long)gx + (long long)P.nx * (gy + (long long)P.ny * gz);
-        const uint8_t s = solid[c];
-        sm.mask[pt] = s ? 1 : 0;
-        if (s) continue;
-        const R T = R(T_in[c]);
-        R Y[NSP];
+        cell[it] = c;
+        s[it] = solid[c];
+        T[it] = R(T_in[c]);
 #pragma unroll
-        for (int k = 0; k < NSP; ++k) Y[k] = R(Y_in[(long long)k * N + c]);
-        const R invW = inv_molar_mass(P, Y);
+        for (int k = 0; k < NSP; ++k) Y[it][k] = R(Y_in[(long long)k * N + c]);
+    }
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) {
+        if (cell[it] < 0) continue;
+        const int pt = slot * G::NPP + tid + it * NTHR;
+        sm.mask[pt] = s[it] ? 1 : 0;
+        if (s[it]) continue;
+        const R invW = inv_molar_mass(P, Y[it]);
         const R W = fdiv(R(1), invW);
-        sm.T[pt] = T;
+        sm.T[pt] = T[it];
 #pragma unroll
-        for (int k = 0; k < NSP; ++k) sm.Y[k * NPT + pt] = Y[k];
+        for (int k = 0; k < NSP; ++k) sm.Y[k * NPT + pt] = Y[it][k];
         sm.X[pt] = W;  // the 3-D tile keeps W in the X slot
         sm.invW[pt] = invW;
-        sm.rho[pt] = fdiv(P.T_in * P.invW_in * W, T);
+        sm.rho[pt] = fdiv(P.T_in * P.invW_in * W, T[it]);
     }
 }
 
 template <typename S, typename R, int TX, int TY, int ZC>
-__global__ void __launch_bounds__(TX * TY) step_kernel_tiled3d(StepParams<R> P, const S* __restrict__ g_in,
-                                                               S* __restrict__ g_out, const S* __restrict__ T_in,
-                                                               S* __restrict__ T_out, const S* __restrict__ Y_in,
-                                                               S* __restrict__ Y_out,
-                                                               const uint8_t* __restrict__ solid)
+__device__ __forceinline__ void tiled3d_body(const StepParams<R>& P, const S* __restrict__ g_in,
+                                             S* __restrict__ g_out, const S* __restrict__ T_in,
+                                             S* __restrict__ T_out, const S* __restrict__ Y_in,
+                                             S* __restrict__ Y_out, const uint8_t* __restrict__ solid)
 {
     using G = Tile3Geom<TX, TY>;
     constexpr int SX = G::SX, NPP = G::NPP, NPT = G::NPT;
@@ -140,12 +158,33 @@ __global__ void __launch_bounds__(TX * TY) step_kernel_tiled3d(StepParams<R> P, 
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     const int q0 = (threadIdx.y + 2) * SX + threadIdx.x + 2;  // in-plane point of this thread
     const int zend = zb + ZC < P.nz ? zb + ZC : P.nz;
+    const bool inside = x < P.nx && y < P.ny;
     for (int z = zb; z < zend; ++z) {
+        // a1 issued before the staging of plane z+2, so that the population
+        // loads are in flight meanwhile (pull with periodic wrap; the
+        // offsets stay inside the domain for any in-range cell)
+        const long long c = (long long)x + (long long)P.nx * y + plane * z;
+        R g[27];
+        if (inside) {
+            const int oxm = x == 0 ? P.nx - 1 : -1, oxp = x == P.nx - 1 ? 1 - P.nx : 1;
+            const long long oym = y == 0 ? (long long)(P.ny - 1) * P.nx : -(long long)P.nx;
+            const long long oyp = y == P.ny - 1 ? (long long)(1 - P.ny) * P.nx : (long long)P.nx;
+            const long long ozm = z == 0 ? (P.nz - 1) * plane : -plane;
+            const long long ozp = z == P.nz - 1 ? (1 - P.nz) * plane : plane;
+            const S* gc = g_in + c;
+#pragma unroll
+            for (int i = 0; i < 27; ++i) {
+                const long long o = (cx_of(i) > 0 ? oxm : (cx_of(i) < 0 ? oxp : 0)) +
+                                    (cy_of(i) > 0 ? oym : (cy_of(i) < 0 ? oyp : 0)) +
+                                    (cz_of(i) > 0 ? ozm : (cz_of(i) < 0 ? ozp : 0));
+                g[i] = R(__ldg(gc + (long long)i * N + o));
+            }
+        }
         stage_plane<S, R, TX, TY>(P, sm, slot_of(z + 2), x0, y0, z + 2, T_in, Y_in, solid);
         __syncthreads();
         const int sc = slot_of(z);
         const int p0 = sc * NPP + q0;
-        bool active = x < P.nx && y < P.ny && !sm.mask[p0];
+        bool active = inside && !sm.mask[p0];
         if (active) {
             // interior: +-2 along the three axes and the 26 neighbours
             bool fast = true;
@@ -164,17 +203,6 @@ __global__ void __launch_bounds__(TX * TY) step_kernel_tiled3d(StepParams<R> P, 
             active = fast;
         }
         if (active) {
-            const long long c = (long long)x + (long long)P.nx * y + plane * z;
-            R g[27];
-#pragma unroll
-            for (int i = 0; i < 27; ++i) {
-                int xs = x - cx_of(i), ys = y - cy_of(i), zs = z - cz_of(i);  // wrapped on periodic axes
-                xs += xs < 0 ? P.nx : (xs >= P.nx ? -P.nx : 0);
-                ys += ys < 0 ? P.ny : (ys >= P.ny ? -P.ny : 0);
-                zs += zs < 0 ? P.nz : (zs >= P.nz ? -P.nz : 0);
-                const long long src = (long long)xs + (long long)P.nx * ys + plane * zs;
-                g[i] = R(__ldg(&g_in[(long long)i * N + src]));
-            }
             const R T0 = sm.T[p0], invW0 = sm.invW[p0], rho0 = sm.rho[p0];
             R Y0[NSP];
 #pragma unroll
@@ -197,17 +225,20 @@ __global__ void __launch_bounds__(TX * TY) step_kernel_tiled3d(StepParams<R> P, 
             acc.conv_T = acc.diff_T = R(0);
 #pragma unroll
             for (int k = 0; k < NSP; ++k) acc.conv_Y[k] = acc.diff_Y[k] = R(0);
-            {
-                int px[5], py[5], pz[5];
+            acc.grad_rho[0] = acc.grad_rho[1] = acc.grad_rho[2] = R(0);
+            // the three axes share one copy of the FD code (a rolled loop keeps
+            // the kernel small enough for the instruction cache)
+#pragma unroll 1
+            for (int a = 0; a < 3; ++a) {
+                int pts[5];
 #pragma unroll
-                for (int j = 0; j < 5; ++j) {
-                    px[j] = p0 + (j - 2);
-                    py[j] = p0 + (j - 2) * SX;
-                    pz[j] = slot_of(z + j - 2) * NPP + q0;
-                }
-                fd_axis_pts<R>(P, sm, NPT, px, 0, u[0], Y0, invW0, rho0, acc);
-                fd_axis_pts<R>(P, sm, NPT, py, 1, u[1], Y0, invW0, rho0, acc);
-                fd_axis_pts<R>(P, sm, NPT, pz, 2, u[2], Y0, invW0, rho0, acc);
+                for (int j = 0; j < 5; ++j)
+                    pts[j] = a == 0 ? p0 + (j - 2) : (a == 1 ? p0 + (j - 2) * SX : slot_of(z + j - 2) * NPP + q0);
+                const R u_a = a == 0 ? u[0] : (a == 1 ? u[1] : u[2]);
+                const R drho = fd_axis_pts<R>(P, sm, NPT, pts, u_a, Y0, invW0, rho0, acc);
+                acc.grad_rho[0] = a == 0 ? drho : acc.grad_rho[0];
+                acc.grad_rho[1] = a == 1 ? drho : acc.grad_rho[1];
+                acc.grad_rho[2] = a == 2 ? drho : acc.grad_rho[2];
             }
             const R q = arrhenius(P, T0, pick_species(Y0, P.fuel), pick_species(Y0, P.oxid));
             const R DT = acc.diff_T + P.Q_cp * q;
@@ -226,6 +257,26 @@ __global__ void __launch_bounds__(TX * TY) step_kernel_tiled3d(StepParams<R> P, 
         }
         __syncthreads();  // the slot of z-2 is restaged next iteration
     }
+}
+
+template <typename S, typename R, int TX, int TY, int ZC>
+__global__ void __launch_bounds__(TX * TY) step_kernel_tiled3d(StepParams<R> P, const S* __restrict__ g_in,
+                                                               S* __restrict__ g_out, const S* __restrict__ T_in,
+                                                               S* __restrict__ T_out, const S* __restrict__ Y_in,
+                                                               S* __restrict__ Y_out,
+                                                               const uint8_t* __restrict__ solid)
+{
+    tiled3d_body<S, R, TX, TY, ZC>(P, g_in, g_out, T_in, T_out, Y_in, Y_out, solid);
+}
+
+// the same with the registers capped so that MINB blocks fit on an SM
+template <typename S, typename R, int TX, int TY, int ZC, int MINB>
+__global__ void __launch_bounds__(TX * TY, MINB)
+    step_kernel_tiled3d_capped(StepParams<R> P, const S* __restrict__ g_in, S* __restrict__ g_out,
+                               const S* __restrict__ T_in, S* __restrict__ T_out, const S* __restrict__ Y_in,
+                               S* __restrict__ Y_out, const uint8_t* __restrict__ solid)
+{
+    tiled3d_body<S, R, TX, TY, ZC>(P, g_in, g_out, T_in, T_out, Y_in, Y_out, solid);
 }
 
 }  // namespace lbfd

@@ -288,7 +288,7 @@ def test_d3q27_tile_variants_match_oracle(lbfd_lib, oracle_mod):
     o.step(8)
     orc = o.get_state()
     s = lbfd_lib.Solver(cfg, solid)
-    assert s.num_variants == 3
+    assert s.num_variants == 4
     for v in range(s.num_variants):
         s.variant = v
         s.set_state(T, Y, g)
