@@ -188,9 +188,11 @@ int lbfd_step_graph(lbfd_handle* h, int n);
  * in-domain solid cells (staircase walls, from shared memory); 9..12 as 5..8
  * with two interior cells per thread in packed FP32 arithmetic (tiles of
  * 32x8, 64x8, 32x8, 64x4; the FP64 form runs them one cell per thread).
- * In 3-D (4 variants), 1..2 are 32x4 columns marching through 16 or 32
+ * In 3-D (6 variants), 1..2 are 32x4 columns marching through 16 or 32
  * z-planes with a five-plane shared-memory ring, 3 is 1 with the registers
- * capped for four blocks per SM.  The cells the tiles leave out go through
+ * capped for four blocks per SM, and 4..5 are 1..2 split into an FD tile
+ * kernel (a1-a7, writing Lambda and grad rho to a scratch buffer of four
+ * planes) and a per-cell collision kernel (a8-a10).  The cells the tiles leave out go through
  * the general form over lists computed at create (in 3-D, one list for
  * cells near domain faces and one, with the face rules compiled out, for
  * cells next to in-domain solids).  All variants compute the same step up
@@ -201,8 +203,9 @@ int lbfd_get_variant(const lbfd_handle* h);
 int lbfd_set_variant(lbfd_handle* h, int variant);
 /* Kernel launches one step makes with the current variant: the tile
  * variants launch the tile kernel plus one kernel per non-empty list of
- * boundary cells (and the wall-tile kernel in 2-D variants 5..12); curved
- * walls add the ghost-fill kernel. */
+ * boundary cells (and the wall-tile kernel in 2-D variants 5..12, the
+ * collision kernel in 3-D variants 4..5); curved walls add the ghost-fill
+ * kernel. */
 int lbfd_launches_per_step(const lbfd_handle* h);
 
 /* Autotuner: time every variant over `reps` launches on the current state

@@ -41,6 +41,8 @@ struct lbfd_handle {
     long long nbndf;
     long long* bndw;      // 3-D: the others (next to in-domain solids only)
     long long nbndw;
+    uint8_t* interior;    // 3-D: per cell, 1 = updated by the tile kernels
+    void* aux;            // 3-D: Lambda and grad rho planes of the split variants
     int* wtiles;          // tiles holding the other boundary cells (2-D)
     long long nwtiles;
     double* red;          // device reduction scratch
@@ -220,6 +222,8 @@ void free_handle(lbfd_handle* h)
     if (h->bnd) cudaFree(h->bnd);
     if (h->bndf) cudaFree(h->bndf);
     if (h->bndw) cudaFree(h->bndw);
+    if (h->interior) cudaFree(h->interior);
+    if (h->aux) cudaFree(h->aux);
     if (h->wtiles) cudaFree(h->wtiles);
     void* curved[] = {h->link_row, h->link_q, h->ghost_row, h->gh_start, h->gh_idx, h->gh_w, h->gval};
     for (void* p : curved)
@@ -276,6 +280,8 @@ lbfd::BoundaryLists lists(const lbfd_handle* h)
         b.wall = h->bndw;
         b.nwall = h->nbndw;
     }
+    b.interior = h->interior;
+    b.aux = h->aux;
     return b;
 }
 
@@ -413,6 +419,18 @@ int lbfd_create(const lbfd_grid* grid, const uint8_t* solid_mask, const lbfd_mec
         std::set_difference(lists_host[0].begin(), lists_host[0].end(), lists_host[1].begin(), lists_host[1].end(),
                             std::back_inserter(wl));
         h->nbndw = (long long)wl.size();
+        // per-cell flag of the cells the tile kernels update, and the
+        // Lambda / grad rho planes of the split variants
+        std::vector<uint8_t> inter((size_t)h->ncell, 0);
+        for (long long c = 0; c < h->ncell; ++c) inter[c] = m[c] ? 0 : 1;
+        for (long long c : lists_host[0]) inter[c] = 0;
+        if (h->precision != LBFD_TANGENT &&
+            ((e = cudaMalloc(&h->interior, (size_t)h->ncell)) != cudaSuccess ||
+             (e = cudaMemcpy(h->interior, inter.data(), (size_t)h->ncell, cudaMemcpyHostToDevice)) != cudaSuccess ||
+             (e = cudaMalloc(&h->aux, (size_t)4 * h->stride * h->esz)) != cudaSuccess)) {
+            free_handle(h);
+            return cuda_fail(e, "split-step buffers");
+        }
         if (!wl.empty()) {
             if ((e = cudaMalloc(&h->bndw, wl.size() * sizeof(long long))) != cudaSuccess ||
                 (e = cudaMemcpy(h->bndw, wl.data(), wl.size() * sizeof(long long), cudaMemcpyHostToDevice)) !=
@@ -560,7 +578,7 @@ int lbfd_launches_per_step(const lbfd_handle* h)
     int n = 1;
     if (h->variant > 0 && h->precision != LBFD_TANGENT) {
         if (h->dim == 3) {
-            n += (b.nface > 0 ? 1 : 0) + (b.nwall > 0 ? 1 : 0);
+            n += (b.nface > 0 ? 1 : 0) + (b.nwall > 0 ? 1 : 0) + (h->variant >= 4 ? 1 : 0);
         } else {
             const bool wv = h->variant >= 5 && b.nwall_tiles > 0;
             n += ((wv ? b.nface : b.nall) > 0 ? 1 : 0) + (wv ? 1 : 0);

@@ -66,6 +66,8 @@ struct BoundaryLists {
     long long nwall_tiles;
     const long long* wall;  // 3-D: all \ face, cells whose stencils reach no non-periodic face
     long long nwall;
+    const uint8_t* interior;  // 3-D: 1 for the cells the tile kernels update (per cell)
+    void* aux;                // 3-D: 4 planes of the compute type for the split variants
 };
 
 // tile shape of the 2-D wall-tile kernel

@@ -16,14 +16,19 @@ static auto tile3_kernel()
     else return step_kernel_tiled3d<S, R, TX, TY, ZC>;
 }
 
-template <typename S, typename R, int TX, int TY, int ZC, int MINB = 0>
+// SPLIT: the tile kernel does a1-a7 and a per-cell kernel a8-a10 (two
+// smaller kernels instead of one; Lambda and grad rho pass through aux)
+template <typename S, typename R, int TX, int TY, int ZC, int MINB = 0, bool SPLIT = false>
 static cudaError_t launch_t3(const StepParams<R>& P, StateView in, StateView out, const uint8_t* solid,
                              const BoundaryLists& b, const SideStream& side, cudaStream_t stream)
 {
     constexpr size_t smem = tile3_smem_bytes<R, TX, TY>();
     auto kern = tile3_kernel<S, R, TX, TY, ZC, MINB>();
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto fkern = step_kernel_fd3d<S, R, TX, TY, ZC>;
+    cudaError_t e = SPLIT ? cudaFuncSetAttribute(fkern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                          : cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    if (SPLIT && (b.aux == nullptr || b.interior == nullptr)) return cudaErrorInvalidValue;
     const bool fork = (b.nface > 0 || b.nwall > 0) && side.stream != nullptr;
     if (fork) {
         if ((e = cudaEventRecord(side.fork, stream)) != cudaSuccess) return e;
@@ -44,8 +49,16 @@ static cudaError_t launch_t3(const StepParams<R>& P, StateView in, StateView out
         if (e != cudaSuccess) return e;
     }
     dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY, (P.nz + ZC - 1) / ZC);
-    kern<<<grid, dim3(TX, TY), smem, stream>>>(P, (const S*)in.g, (S*)out.g, (const S*)in.T, (S*)out.T,
-                                               (const S*)in.Y, (S*)out.Y, solid);
+    if constexpr (SPLIT) {
+        fkern<<<grid, dim3(TX, TY), smem, stream>>>(P, (const S*)in.g, (const S*)in.T, (S*)out.T, (const S*)in.Y,
+                                                    (S*)out.Y, solid, (R*)b.aux);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        step_kernel_collide3d<S, R><<<dim3((P.nx + 127) / 128, P.ny, P.nz), 128, 0, stream>>>(
+            P, (const S*)in.g, (S*)out.g, (const S*)in.T, (const S*)in.Y, b.interior, (const R*)b.aux);
+    } else {
+        kern<<<grid, dim3(TX, TY), smem, stream>>>(P, (const S*)in.g, (S*)out.g, (const S*)in.T, (S*)out.T,
+                                                   (const S*)in.Y, (S*)out.Y, solid);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (fork) {
         if ((e = cudaEventRecord(side.join, side.stream)) != cudaSuccess) return e;
@@ -64,6 +77,9 @@ static cudaError_t launch_3d_tiles(int variant, const StepParams<R>& P, StateVie
     case 2: return launch_t3<S, R, 32, 4, 32>(P, in, out, solid, b, side, stream);
     // variant 3: as 1 with the registers capped for four blocks per SM (FP32)
     case 3: return launch_t3<S, R, 32, 4, 16, sizeof(R) == 4 ? 4 : 0>(P, in, out, solid, b, side, stream);
+    // variants 4, 5: as 1, 2 split into an FD tile kernel and a collision kernel
+    case 4: return launch_t3<S, R, 32, 4, 16, 0, true>(P, in, out, solid, b, side, stream);
+    case 5: return launch_t3<S, R, 32, 4, 32, 0, true>(P, in, out, solid, b, side, stream);
     default: return cudaErrorInvalidValue;
     }
 }

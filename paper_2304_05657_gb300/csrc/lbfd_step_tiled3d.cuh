@@ -132,11 +132,14 @@ __device__ __forceinline__ void stage_plane(const StepParams<R>& P, const TileSm
     }
 }
 
-template <typename S, typename R, int TX, int TY, int ZC>
+// SPLIT: steps a1-a7 only; Lambda and grad rho of every interior cell go
+// to aux (four planes) for step_kernel_collide3d, which does a8-a10
+template <typename S, typename R, int TX, int TY, int ZC, bool SPLIT = false>
 __device__ __forceinline__ void tiled3d_body(const StepParams<R>& P, const S* __restrict__ g_in,
                                              S* __restrict__ g_out, const S* __restrict__ T_in,
                                              S* __restrict__ T_out, const S* __restrict__ Y_in,
-                                             S* __restrict__ Y_out, const uint8_t* __restrict__ solid)
+                                             S* __restrict__ Y_out, const uint8_t* __restrict__ solid,
+                                             R* __restrict__ aux = nullptr)
 {
     using G = Tile3Geom<TX, TY>;
     constexpr int SX = G::SX, NPP = G::NPP, NPT = G::NPT;
@@ -251,9 +254,15 @@ __device__ __forceinline__ void tiled3d_body(const StepParams<R>& P, const S* __
                 lam_Y += P.inv_Wk[k] * DY;
             }
             const R Lam = fdiv(DT, T0) + fdiv(lam_Y, invW0);
-            collide<3, R>(P, g, rho0, u, acc.grad_rho, Lam);
+            if constexpr (SPLIT) {
+                aux[c] = Lam;
 #pragma unroll
-            for (int i = 0; i < 27; ++i) g_out[(long long)i * N + c] = S(g[i]);
+                for (int a = 0; a < 3; ++a) aux[(long long)(1 + a) * N + c] = acc.grad_rho[a];
+            } else {
+                collide<3, R>(P, g, rho0, u, acc.grad_rho, Lam);
+#pragma unroll
+                for (int i = 0; i < 27; ++i) g_out[(long long)i * N + c] = S(g[i]);
+            }
         }
         __syncthreads();  // the slot of z-2 is restaged next iteration
     }
@@ -277,6 +286,80 @@ __global__ void __launch_bounds__(TX * TY, MINB)
                                S* __restrict__ Y_out, const uint8_t* __restrict__ solid)
 {
     tiled3d_body<S, R, TX, TY, ZC>(P, g_in, g_out, T_in, T_out, Y_in, Y_out, solid);
+}
+
+// a1-a7 of the interior cells (the FD half of a split step); FP32 held to
+// four 128-thread blocks per SM
+template <typename S, typename R, int TX, int TY, int ZC>
+__global__ void __launch_bounds__(TX * TY, sizeof(R) == 4 ? 512 / (TX * TY) : 1)
+    step_kernel_fd3d(StepParams<R> P, const S* __restrict__ g_in, const S* __restrict__ T_in, S* __restrict__ T_out,
+                     const S* __restrict__ Y_in, S* __restrict__ Y_out, const uint8_t* __restrict__ solid,
+                     R* __restrict__ aux)
+{
+    tiled3d_body<S, R, TX, TY, ZC, true>(P, g_in, nullptr, T_in, T_out, Y_in, Y_out, solid, aux);
+}
+
+// a1, a2 and a8-a10 of the interior cells (the LB half of a split step):
+// the pull and the density are recomputed exactly as in the FD half, Lambda
+// and grad rho read from aux.  One thread per cell, 128 cells of an x-row
+// per block.
+template <typename S, typename R>
+__global__ void __launch_bounds__(128)
+    step_kernel_collide3d(StepParams<R> P, const S* __restrict__ g_in, S* __restrict__ g_out,
+                          const S* __restrict__ T_in, const S* __restrict__ Y_in,
+                          const uint8_t* __restrict__ interior, const R* __restrict__ aux)
+{
+    const int x = blockIdx.x * 128 + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= P.nx) return;
+    const long long N = P.N;
+    const long long plane = (long long)P.nx * P.ny;
+    const long long c = (long long)x + (long long)P.nx * y + plane * z;
+    if (!interior[c]) return;
+    R g[27];
+    {
+        const int oxm = x == 0 ? P.nx - 1 : -1, oxp = x == P.nx - 1 ? 1 - P.nx : 1;
+        const long long oym = y == 0 ? (long long)(P.ny - 1) * P.nx : -(long long)P.nx;
+        const long long oyp = y == P.ny - 1 ? (long long)(1 - P.ny) * P.nx : (long long)P.nx;
+        const long long ozm = z == 0 ? (P.nz - 1) * plane : -plane;
+        const long long ozp = z == P.nz - 1 ? (1 - P.nz) * plane : plane;
+        const S* gc = g_in + c;
+#pragma unroll
+        for (int i = 0; i < 27; ++i) {
+            const long long o = (cx_of(i) > 0 ? oxm : (cx_of(i) < 0 ? oxp : 0)) +
+                                (cy_of(i) > 0 ? oym : (cy_of(i) < 0 ? oyp : 0)) +
+                                (cz_of(i) > 0 ? ozm : (cz_of(i) < 0 ? ozp : 0));
+            g[i] = R(__ldg(gc + (long long)i * N + o));
+        }
+    }
+    // the density as staged by the FD half
+    const R T0 = R(T_in[c]);
+    R Y0[NSP];
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) Y0[k] = R(Y_in[(long long)k * N + c]);
+    const R invW0 = inv_molar_mass(P, Y0);
+    const R W = fdiv(R(1), invW0);
+    const R rho0 = fdiv(P.T_in * P.invW_in * W, T0);
+    R u[3];
+    {
+        const R inv = fdiv(R(3), rho0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            R m = R(0);
+#pragma unroll
+            for (int i = 0; i < 27; ++i) {
+                const int ci = ccomp<3>(i, a);
+                if (ci) m += R(ci) * g[i];
+            }
+            u[a] = m * inv;
+        }
+    }
+    const R Lam = aux[c];
+    R grad[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) grad[a] = aux[(long long)(1 + a) * N + c];
+    collide<3, R>(P, g, rho0, u, grad, Lam);
+#pragma unroll
+    for (int i = 0; i < 27; ++i) g_out[(long long)i * N + c] = S(g[i]);
 }
 
 }  // namespace lbfd

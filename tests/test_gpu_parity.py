@@ -288,7 +288,7 @@ def test_d3q27_tile_variants_match_oracle(lbfd_lib, oracle_mod):
     o.step(8)
     orc = o.get_state()
     s = lbfd_lib.Solver(cfg, solid)
-    assert s.num_variants == 4
+    assert s.num_variants == 6
     for v in range(s.num_variants):
         s.variant = v
         s.set_state(T, Y, g)
@@ -301,3 +301,23 @@ def test_d3q27_tile_variants_match_oracle(lbfd_lib, oracle_mod):
         sm.step(8)
         Tg = sm.read_field(lbfd_lib.FIELD_T)
         assert rel_l2(Tg, orc[0]) <= 1e-6
+
+
+def test_d3q27_split_variants_equal_fused(lbfd_lib):
+    """The split 3-D variants (FD tile kernel, then a collision kernel fed
+    Lambda and grad rho through a scratch buffer) do the fused variants'
+    arithmetic in the same order: bitwise equal states, FP64 and FP32."""
+    cfg, solid, T, Y = inputs.sphere_packing(nx=40, ny=14, nz=13, x_range=(8, 30), r_range=(2.0, 3.5),
+                                             porosity=0.85, seed=12, ignite_width=5)
+    g, T, Y = inputs.perturbed_state(cfg, solid, T, Y, seed=13)
+    for prec in ("fp64", "mixed"):
+        s = lbfd_lib.Solver(dict(cfg, precision=prec), solid)
+        for fused, split in ((1, 4), (2, 5)):
+            st = []
+            for v in (fused, split):
+                s.variant = v
+                s.set_state(T, Y, g)
+                s.step(6)
+                st.append(s.get_state())
+            for a, b in zip(*st):
+                assert np.array_equal(a, b), (prec, fused, split)
