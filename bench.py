@@ -19,6 +19,8 @@ method) on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import glob
+import hashlib
 import json
 import os
 import subprocess
@@ -100,6 +102,35 @@ def peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    """sha256 over the CUDA sources and the C header, in name order."""
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_2304_05657_gb300", "csrc", "*")))
+    files.append(os.path.join(ROOT, "include", "lbfd.h"))
+    for path in files:
+        if path.endswith((".cu", ".cuh", ".h")):
+            h.update(os.path.basename(path).encode())
+            with open(path, "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()
+
+
+def measured_traffic(workload: str, variant: int, precision: str):
+    """DRAM bytes per step (ncu dram__bytes_read.sum + dram__bytes_write.sum
+    over the kernels of one step) recorded in profiles/traffic.json, or None
+    when the record is for other kernel sources, variant or precision."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)[workload]
+    except Exception:
+        return None, None
+    per_variant = rec.get("dram_bytes_per_step", {})
+    if (rec.get("csrc_sha256") != kernel_source_hash() or rec.get("precision") != precision
+            or str(variant) not in per_variant):
+        return None, rec.get("csrc_sha256")
+    return float(per_variant[str(variant)]) * float(rec.get("scale_to_workload", 1.0)), rec.get("csrc_sha256")
 
 
 class ClockSampler:
@@ -383,6 +414,7 @@ def run_ours(args):
     mean_s = float(step_ms.mean()) * 1e-3
     peak, peak_kind = peaks()
     achieved = alg_bytes / mean_s / 1e9
+    traffic, _ = measured_traffic(args.workload, s.variant, precision)
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -394,8 +426,10 @@ def run_ours(args):
                    "kernel_variant": s.variant, "launches_per_step": s.launches_per_step,
                    "autotune_ms_per_variant": [round(float(t), 4) for t in tune_ms]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
-                     "algorithmic_bytes_per_cell": bpc, "kernel": "step_kernel",
+                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+                     "traffic_unit": "DRAM bytes per step (ncu, all kernels of one step)",
+                     "algorithmic_bytes_per_step": alg_bytes, "algorithmic_bytes_per_cell": bpc,
+                     "kernel": "one lbfd_step (the tile kernel with its boundary and wall kernels)",
                      "mean_launch_ms": mean_s * 1e3},
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                 "steps": e2e_steps, "api": "lbfd_set_state_raw + lbfd_step + lbfd_get_state_raw (pinned)"},

@@ -341,10 +341,17 @@ __device__ __forceinline__ void cell_step_general(const StepParams<R>& P, const 
     for (int k = 0; k < NSP; ++k) Y0[k] = R(Y_in[(long long)k * N + c]);
     const R invW0 = inv_molar_mass(P, Y0);
     const R rho0 = eos(P, T0, invW0);
-    // a1
+    // a1: a rolled loop (one copy of the boundary rules keeps this kernel
+    // small enough for the instruction cache; the pulled values pass
+    // through a local array)
     R g[Q];
+    {
+        R gl[Q];
+#pragma unroll 1
+        for (int i = 0; i < Q; ++i) gl[i] = pull_general<DIM, S, R, FACES>(P, i, p, c, g_in, solid, rho0);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) g[i] = pull_general<DIM, S, R, FACES>(P, i, p, c, g_in, solid, rho0);
+        for (int i = 0; i < Q; ++i) g[i] = gl[i];
+    }
     // a2: velocity, Eq. 13b
     R u[3] = {R(0), R(0), R(0)};
     {
@@ -371,7 +378,7 @@ __device__ __forceinline__ void cell_step_general(const StepParams<R>& P, const 
         LineDesc<R> L;
         build_line<DIM, R, FACES>(P, p, c, a, solid, L);
         R Tl[5], Yl[NSP][5], invWl[5], rhol[5];
-#pragma unroll
+#pragma unroll 1
         for (int j = 0; j < 5; ++j) {
             R Yj[NSP];
             line_point<S, R>(P, L, j, T_in, Y_in, Tl[j], Yj, invWl[j], rhol[j]);
