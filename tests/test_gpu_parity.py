@@ -306,7 +306,9 @@ def test_d3q27_tile_variants_match_oracle(lbfd_lib, oracle_mod):
 def test_d3q27_split_variants_equal_fused(lbfd_lib):
     """The split 3-D variants (FD tile kernel, then a collision kernel fed
     Lambda and grad rho through a scratch buffer) do the fused variants'
-    arithmetic in the same order: bitwise equal states, FP64 and FP32."""
+    arithmetic in the same order; only the compiler's choice of fused
+    multiply-adds may differ between the two programs, so the states agree
+    to a few ulp: 1e-12 relative L2 in FP64, 1e-6 in FP32."""
     cfg, solid, T, Y = inputs.sphere_packing(nx=40, ny=14, nz=13, x_range=(8, 30), r_range=(2.0, 3.5),
                                              porosity=0.85, seed=12, ignite_width=5)
     g, T, Y = inputs.perturbed_state(cfg, solid, T, Y, seed=13)
@@ -319,5 +321,5 @@ def test_d3q27_split_variants_equal_fused(lbfd_lib):
                 s.set_state(T, Y, g)
                 s.step(6)
                 st.append(s.get_state())
-            for a, b in zip(*st):
-                assert np.array_equal(a, b), (prec, fused, split)
+            tol = 1e-12 if prec == "fp64" else 1e-6
+            compare_states(st[1], st[0], tol, f"{prec} split {split} vs fused {fused}")
