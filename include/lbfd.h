@@ -218,6 +218,15 @@ int lbfd_autotune(lbfd_handle* h, int reps, double* ms_per_variant, int* best);
  * Synchronises the handle's stream. */
 int lbfd_read_field(lbfd_handle* h, int field, double* out);
 
+/* Copy the whole current state of n listed cells to host FP64
+ * out[n][Q + 1 + 5]: per cell g_0 .. g_{Q-1} (the stored post-collision
+ * populations, Eq. 14), T, Y_0 .. Y_4.  cells: host array of n cell
+ * indices c = x + nx (y + ny z), each in [0, N) (else LBFD_EINVAL, nothing
+ * copied).  Both arrays are caller-owned; the call allocates device scratch
+ * for its duration and synchronises the handle's stream.  Lets a caller
+ * inspect a few cells of a large grid without copying the whole state. */
+int lbfd_read_cells(lbfd_handle* h, const long long* cells, long long n, double* out);
+
 /* Reductions over fluid cells in FP64 (warp shuffles + atomics), out[LBFD_NDIAG]
  * as listed above.  Synchronises; returns LBFD_ENONFINITE (after filling out)
  * when a fluid cell holds a non-finite value. */

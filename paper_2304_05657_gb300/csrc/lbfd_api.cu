@@ -693,6 +693,34 @@ int lbfd_autotune(lbfd_handle* h, int reps, double* ms_per_variant, int* best)
 }
 
 
+int lbfd_read_cells(lbfd_handle* h, const long long* cells, long long n, double* out)
+{
+    if (!h || n < 0 || (n > 0 && (!cells || !out))) return LBFD_EINVAL;
+    if (n == 0) return LBFD_OK;
+    for (long long t = 0; t < n; ++t)
+        if (cells[t] < 0 || cells[t] >= h->ncell) return LBFD_EINVAL;
+    const size_t per = (size_t)h->Q + 1 + lbfd::NSP;
+    long long* dc = nullptr;
+    double* dout = nullptr;
+    cudaError_t e;
+    if ((e = cudaMalloc(&dc, (size_t)n * sizeof(long long))) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&dout, (size_t)n * per * sizeof(double))) != cudaSuccess) {
+        cudaFree(dc);
+        return cuda_fail(e, "cudaMalloc");
+    }
+    if ((e = cudaMemcpyAsync(dc, cells, (size_t)n * sizeof(long long), cudaMemcpyHostToDevice, h->stream)) ==
+            cudaSuccess &&
+        (e = lbfd::launch_cells(h->dim, h->precision, h->Pd, view(h, h->cur), dc, n, dout, h->stream)) ==
+            cudaSuccess &&
+        (e = cudaMemcpyAsync(out, dout, (size_t)n * per * sizeof(double), cudaMemcpyDeviceToHost, h->stream)) ==
+            cudaSuccess)
+        e = cudaStreamSynchronize(h->stream);
+    cudaFree(dc);
+    cudaFree(dout);
+    if (e != cudaSuccess) return cuda_fail(e, "lbfd_read_cells");
+    return LBFD_OK;
+}
+
 int lbfd_read_field(lbfd_handle* h, int field, double* out)
 {
     if (!h || !out) return LBFD_EINVAL;

@@ -100,6 +100,9 @@ cudaError_t launch_diagnostics(int dim, int precision, const StepParams<double>&
 // Derived or raw field of every cell into double out[ncell] (device).
 cudaError_t launch_field(int dim, int precision, const StepParams<double>& Pd, StateView st,
                          const uint8_t* solid, int field, double* out, cudaStream_t stream);
+// gather the whole state of n listed cells into out[n][Q + 1 + NSP] (device)
+cudaError_t launch_cells(int dim, int precision, const StepParams<double>& Pd, StateView st, const long long* cells,
+                         long long n, double* out, cudaStream_t stream);
 
 // Tangent-linear step (precision 2: Dual<double, 4> values, general form,
 // 2-D), tangent read-out and objective gradients (lbfd_tangent.cu).

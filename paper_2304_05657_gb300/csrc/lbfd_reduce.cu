@@ -257,6 +257,40 @@ __global__ void __launch_bounds__(256) field_kernel(StepParams<double> P, const 
     out[c] = v;
 }
 
+// the whole state (g_0..g_{Q-1}, T, Y_0..Y_{NSP-1}) of listed cells
+template <typename S>
+__global__ void __launch_bounds__(256) cells_kernel(long long N, int Q, const S* __restrict__ g,
+                                                    const S* __restrict__ T, const S* __restrict__ Y,
+                                                    const long long* __restrict__ cells, long long n,
+                                                    double* __restrict__ out)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const long long c = cells[t];
+    double* o = out + t * (Q + 1 + NSP);
+    for (int i = 0; i < Q; ++i) o[i] = val(g[(long long)i * N + c]);
+    o[Q] = val(T[c]);
+    for (int k = 0; k < NSP; ++k) o[Q + 1 + k] = val(Y[(long long)k * N + c]);
+}
+
+cudaError_t launch_cells(int dim, int precision, const StepParams<double>& P, StateView st, const long long* cells,
+                         long long n, double* out, cudaStream_t stream)
+{
+    if (n <= 0) return cudaSuccess;
+    const int Q = dim == 2 ? 9 : 27;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    if (precision == 2)
+        cells_kernel<Tan><<<blocks, 256, 0, stream>>>(P.N, Q, (const Tan*)st.g, (const Tan*)st.T, (const Tan*)st.Y,
+                                                      cells, n, out);
+    else if (precision == 0)
+        cells_kernel<double><<<blocks, 256, 0, stream>>>(P.N, Q, (const double*)st.g, (const double*)st.T,
+                                                         (const double*)st.Y, cells, n, out);
+    else
+        cells_kernel<float><<<blocks, 256, 0, stream>>>(P.N, Q, (const float*)st.g, (const float*)st.T,
+                                                        (const float*)st.Y, cells, n, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_field(int dim, int precision, const StepParams<double>& P, StateView st, const uint8_t* solid,
                          int field, double* out, cudaStream_t stream)
 {

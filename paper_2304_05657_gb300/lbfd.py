@@ -35,7 +35,7 @@ SYMBOLS = (
     "lbfd_set_state_raw", "lbfd_steps_done", "lbfd_num_cells", "lbfd_num_populations", "lbfd_strerror",
     "lbfd_last_error", "lbfd_step_graph", "lbfd_num_variants", "lbfd_get_variant", "lbfd_set_variant",
     "lbfd_autotune", "lbfd_diagnostics_noalloc", "lbfd_launches_per_step", "lbfd_read_tangent", "lbfd_gradient",
-    "lbfd_diagnostics_rows", "lbfd_set_inlet_velocity", "lbfd_set_curved_walls",
+    "lbfd_diagnostics_rows", "lbfd_set_inlet_velocity", "lbfd_set_curved_walls", "lbfd_read_cells",
 )
 
 
@@ -92,6 +92,7 @@ def load(path: str = LIB_PATH):
     lib.lbfd_set_state.argtypes = [H, D, D, ctypes.c_void_p]
     lib.lbfd_step.argtypes = [H, ctypes.c_int]
     lib.lbfd_read_field.argtypes = [H, ctypes.c_int, D]
+    lib.lbfd_read_cells.argtypes = [H, ctypes.POINTER(ctypes.c_longlong), ctypes.c_longlong, D]
     lib.lbfd_diagnostics.argtypes = [H, D]
     lib.lbfd_flame_position.argtypes = [H, D, D, D]
     lib.lbfd_state_bytes.restype = ctypes.c_size_t
@@ -255,6 +256,16 @@ class Solver:
     def read_field(self, field: int) -> np.ndarray:
         out = np.empty(self.N)
         _check(self.lib, self.lib.lbfd_read_field(self.h, int(field), _dp(out)), "lbfd_read_field")
+        return out
+
+    def read_cells(self, cells) -> np.ndarray:
+        """The state of the listed cells: float64 [n, Q + 1 + 5] with the
+        columns g_0 .. g_{Q-1}, T, Y_0 .. Y_4."""
+        cells = np.ascontiguousarray(np.asarray(cells, dtype=np.int64).ravel())
+        out = np.empty((cells.size, self.Q + 1 + NSP))
+        st = self.lib.lbfd_read_cells(self.h, cells.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
+                                      int(cells.size), _dp(out))
+        _check(self.lib, st, "lbfd_read_cells")
         return out
 
     def get_state(self):
