@@ -41,7 +41,7 @@ struct lbfd_handle {
     long long nbndf;
     long long* bndw;      // 3-D: the others (next to in-domain solids only)
     long long nbndw;
-    uint8_t* interior;    // 3-D: per cell, 1 = updated by the tile kernels
+    uint8_t* interior;    // per cell, 1 = updated by the interior tile kernels
     void* aux;            // 3-D: Lambda and grad rho planes of the split variants
     int* wtiles;          // tiles holding the other boundary cells (2-D)
     long long nwtiles;
@@ -414,20 +414,26 @@ int lbfd_create(const lbfd_grid* grid, const uint8_t* solid_mask, const lbfd_mec
             return cuda_fail(e, "cudaMemcpy(boundary list)");
         }
     }
+    {
+        // per-cell flag of the cells the tile kernels update (fluid cells
+        // outside the boundary list)
+        std::vector<uint8_t> inter((size_t)h->ncell, 0);
+        for (long long c = 0; c < h->ncell; ++c) inter[c] = m[c] ? 0 : 1;
+        for (long long c : lists_host[0]) inter[c] = 0;
+        if ((e = cudaMalloc(&h->interior, (size_t)h->ncell)) != cudaSuccess ||
+            (e = cudaMemcpy(h->interior, inter.data(), (size_t)h->ncell, cudaMemcpyHostToDevice)) != cudaSuccess) {
+            free_handle(h);
+            return cuda_fail(e, "interior flags");
+        }
+    }
     if (h->dim == 3) {  // all \ face (both sorted)
         std::vector<long long> wl;
         std::set_difference(lists_host[0].begin(), lists_host[0].end(), lists_host[1].begin(), lists_host[1].end(),
                             std::back_inserter(wl));
         h->nbndw = (long long)wl.size();
-        // per-cell flag of the cells the tile kernels update, and the
-        // Lambda / grad rho planes of the split variants
-        std::vector<uint8_t> inter((size_t)h->ncell, 0);
-        for (long long c = 0; c < h->ncell; ++c) inter[c] = m[c] ? 0 : 1;
-        for (long long c : lists_host[0]) inter[c] = 0;
+        // the Lambda / grad rho planes of the split variants
         if (h->precision != LBFD_TANGENT &&
-            ((e = cudaMalloc(&h->interior, (size_t)h->ncell)) != cudaSuccess ||
-             (e = cudaMemcpy(h->interior, inter.data(), (size_t)h->ncell, cudaMemcpyHostToDevice)) != cudaSuccess ||
-             (e = cudaMalloc(&h->aux, (size_t)4 * h->stride * h->esz)) != cudaSuccess)) {
+            (e = cudaMalloc(&h->aux, (size_t)4 * h->stride * h->esz)) != cudaSuccess) {
             free_handle(h);
             return cuda_fail(e, "split-step buffers");
         }

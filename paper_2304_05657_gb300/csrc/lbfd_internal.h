@@ -66,7 +66,7 @@ struct BoundaryLists {
     long long nwall_tiles;
     const long long* wall;  // 3-D: all \ face, cells whose stencils reach no non-periodic face
     long long nwall;
-    const uint8_t* interior;  // 3-D: 1 for the cells the tile kernels update (per cell)
+    const uint8_t* interior;  // per cell, 1 for the cells the interior tile kernels update
     void* aux;                // 3-D: 4 planes of the compute type for the split variants
 };
 

@@ -94,10 +94,10 @@ static cudaError_t launch_tiled(const StepParams<R>& P, StateView in, StateView 
             (e = cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
             return e;
         pk<<<grid, block, smem, stream>>>(P, (const float*)in.g, (float*)out.g, (const float*)in.T, (float*)out.T,
-                                          (const float*)in.Y, (float*)out.Y, solid);
+                                          (const float*)in.Y, (float*)out.Y, b.interior);
     } else {
         kern<<<grid, block, smem, stream>>>(P, (const S*)in.g, (S*)out.g, (const S*)in.T, (S*)out.T,
-                                            (const S*)in.Y, (S*)out.Y, solid);
+                                            (const S*)in.Y, (S*)out.Y, b.interior);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (fork) {

@@ -49,7 +49,7 @@ template <int TXP, int TY, int MINB>
 __global__ void __launch_bounds__(TXP * TY, MINB)
     step_kernel_pair2d(StepParams<float> P, const float* __restrict__ g_in, float* __restrict__ g_out,
                        const float* __restrict__ T_in, float* __restrict__ T_out, const float* __restrict__ Y_in,
-                       float* __restrict__ Y_out, const uint8_t* __restrict__ solid)
+                       float* __restrict__ Y_out, const uint8_t* __restrict__ interior)
 {
     constexpr int TX = 2 * TXP;
     using G = TileGeom<TX, TY>;
@@ -75,7 +75,10 @@ __global__ void __launch_bounds__(TXP * TY, MINB)
     // that the loads are in flight meanwhile; a missing lane 1 re-reads
     // lane 0.  The offsets wrap inside the domain for any in-range cell.
     F2 g[9];
+    bool ok0 = false, ok1 = false;  // the two cells are interior (per-cell class)
     if (inside) {
+        ok0 = interior[c] != 0;
+        ok1 = has1 && interior[c + 1] != 0;
         const int x1 = has1 ? x + 1 : x;
         const int oym = y == 0 ? (P.ny - 1) * P.nx : -P.nx, oyp = y == P.ny - 1 ? (1 - P.ny) * P.nx : P.nx;
         const int oxm0 = x == 0 ? P.nx - 1 : -1, oxp0 = x == P.nx - 1 ? 1 - P.nx : 1;
@@ -95,14 +98,11 @@ __global__ void __launch_bounds__(TXP * TY, MINB)
         }
     }
     stage_tile2d<float, float, TX, TY, false, TXP * TY>(P, sm, x0, y0, threadIdx.x + TXP * threadIdx.y, T_in, Y_in,
-                                                        solid);
+                                                        nullptr);
     __syncthreads();
 
-    if (!inside) return;
+    if (!inside || (!ok0 && !ok1)) return;
     const int p0 = (threadIdx.y + 2) * SX + 2 * threadIdx.x + 2;
-    const bool ok0 = interior_point<SX>(sm.mask, p0);
-    const bool ok1 = has1 && interior_point<SX>(sm.mask, p0 + 1);
-    if (!ok0 && !ok1) return;
 
     // a2
     const F2 T0 = pair_at(sm.T, p0), invW0 = pair_at(sm.invW, p0), rho0 = pair_at(sm.rho, p0);

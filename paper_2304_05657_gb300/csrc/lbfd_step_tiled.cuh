@@ -201,7 +201,9 @@ __device__ __forceinline__ void pull_interior(const StepParams<R>& P, const S* _
 // Stage T, Y_k, X_k, 1/W, rho and the mask of a tile (origin x0, y0) and
 // its 2-cell halo with NTHR threads, this one numbered tid.  All of a
 // thread's global loads are issued before any of them is used, so that
-// their latencies overlap.
+// their latencies overlap.  WALLS == false (interior tiles, whose cells are
+// flagged interior from a per-cell array): no mask; solid points are staged
+// like fluid ones, their values are never read.
 template <typename S, typename R, int TX, int TY, bool WALLS, int NTHR>
 __device__ __forceinline__ void stage_tile2d(const StepParams<R>& P, const TileSmem<R>& sm, int x0, int y0, int tid,
                                              const S* __restrict__ T_in, const S* __restrict__ Y_in,
@@ -242,13 +244,13 @@ __device__ __forceinline__ void stage_tile2d(const StepParams<R>& P, const TileS
                 const bool okx = gx >= 0 && gx < P.nx ? true : P.face_solid[gx < 0 ? 0 : 1];
                 const bool oky = gy >= 0 && gy < P.ny ? true : P.face_solid[gy < 0 ? 2 : 3];
                 if (okx && oky) m = 1;
+                sm.mask[pt] = m;
             }
-            sm.mask[pt] = m;
             continue;
         }
         const long long c = (long long)gx + (long long)P.nx * gy;
         cell[it] = c;
-        s[it] = solid[c];
+        if constexpr (WALLS) s[it] = solid[c];
         T[it] = R(T_in[c]);
 #pragma unroll
         for (int k = 0; k < NSP; ++k) Y[it][k] = R(Y_in[(long long)k * N + c]);
@@ -257,8 +259,10 @@ __device__ __forceinline__ void stage_tile2d(const StepParams<R>& P, const TileS
     for (int it = 0; it < NIT; ++it) {
         if (cell[it] < 0) continue;
         const int pt = tid + it * NTHR;
-        sm.mask[pt] = s[it] ? 1 : 0;
-        if (s[it]) continue;
+        if constexpr (WALLS) {
+            sm.mask[pt] = s[it] ? 1 : 0;
+            if (s[it]) continue;
+        }
         const R invW = inv_molar_mass(P, Y[it]);
         const R W = fdiv(R(1), invW);
         sm.T[pt] = T[it];
@@ -290,7 +294,8 @@ template <typename S, typename R, int TX, int TY, bool WALLS>
 __device__ __forceinline__ void tiled2d_body(const StepParams<R>& P, const S* __restrict__ g_in, S* __restrict__ g_out,
                                              const S* __restrict__ T_in, S* __restrict__ T_out,
                                              const S* __restrict__ Y_in, S* __restrict__ Y_out,
-                                             const uint8_t* __restrict__ solid, const int* __restrict__ tiles)
+                                             const uint8_t* __restrict__ solid, const int* __restrict__ tiles,
+                                             const uint8_t* __restrict__ interior)
 {
     using G = TileGeom<TX, TY>;
     constexpr int SX = G::SX, NPT = G::NPT;
@@ -317,20 +322,25 @@ __device__ __forceinline__ void tiled2d_body(const StepParams<R>& P, const S* __
     const bool inside = x < P.nx && y < P.ny;
     const long long c = (long long)x + (long long)P.nx * y;
     R g[9];
-    // a1 for the interior tiles: issued before the staging, so that the
-    // population loads are in flight while the tile is staged
+    // interior tiles: the cell's class (the +-2 lines and the 8 neighbours
+    // are fluid cells of the domain, precomputed per cell) and a1, issued
+    // before the staging so that the loads are in flight while the tile is
+    // staged
+    bool fast = false;
     if constexpr (!WALLS) {
-        if (inside) pull_interior<S, R>(P, g_in, c, x, y, g);
+        if (inside) {
+            fast = interior[c] != 0;
+            pull_interior<S, R>(P, g_in, c, x, y, g);
+        }
     }
     stage_tile2d<S, R, TX, TY, WALLS, TX * TY>(P, sm, x0, y0, tid, T_in, Y_in, solid);
     __syncthreads();
 
     if (!inside) return;
     const int p0 = (threadIdx.y + 2) * SX + threadIdx.x + 2;
-    if (sm.mask[p0]) return;  // solid
-    // fast path: the +-2 lines and the 8 neighbours are fluid cells of the domain
-    const bool fast = interior_point<SX>(sm.mask, p0);
     if constexpr (WALLS) {
+        if (sm.mask[p0]) return;  // solid
+        fast = interior_point<SX>(sm.mask, p0);
         // next to in-domain solid cells only (staircase walls); the interior
         // cells belong to the plain tile kernel, the rest to the boundary list
         if (fast || P.curved) return;
@@ -343,7 +353,7 @@ __device__ __forceinline__ void tiled2d_body(const StepParams<R>& P, const S* __
                 sm.mask[p0 - SX - 1] != 2;
         if (!walls) return;
     } else {
-        if (!fast) return;  // boundary cell: another kernel updates it
+        if (!fast) return;  // solid, or a boundary cell: another kernel updates it
     }
     // a1 for the wall tiles: pull from the neighbours (Eq. 8), half-way
     // bounce-back from an in-domain solid neighbour (Eq. 28)
@@ -410,13 +420,12 @@ __device__ __forceinline__ void tiled2d_body(const StepParams<R>& P, const S* __
 
 // FP32: four 256-thread blocks (1024 threads) per SM, i.e. <= 64 registers
 template <typename S, typename R, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY, sizeof(R) == 4 ? 1024 / (TX * TY) : 1) step_kernel_tiled2d(StepParams<R> P, const S* __restrict__ g_in,
-                                                               S* __restrict__ g_out, const S* __restrict__ T_in,
-                                                               S* __restrict__ T_out, const S* __restrict__ Y_in,
-                                                               S* __restrict__ Y_out,
-                                                               const uint8_t* __restrict__ solid)
+__global__ void __launch_bounds__(TX * TY, sizeof(R) == 4 ? 1024 / (TX * TY) : 1)
+    step_kernel_tiled2d(StepParams<R> P, const S* __restrict__ g_in, S* __restrict__ g_out,
+                        const S* __restrict__ T_in, S* __restrict__ T_out, const S* __restrict__ Y_in,
+                        S* __restrict__ Y_out, const uint8_t* __restrict__ interior)
 {
-    tiled2d_body<S, R, TX, TY, false>(P, g_in, g_out, T_in, T_out, Y_in, Y_out, solid, nullptr);
+    tiled2d_body<S, R, TX, TY, false>(P, g_in, g_out, T_in, T_out, Y_in, Y_out, nullptr, nullptr, interior);
 }
 
 // the cells next to in-domain solid cells, over the tiles that contain any
@@ -426,7 +435,7 @@ __global__ void __launch_bounds__(TX * TY)
                               const S* __restrict__ T_in, S* __restrict__ T_out, const S* __restrict__ Y_in,
                               S* __restrict__ Y_out, const uint8_t* __restrict__ solid, const int* __restrict__ tiles)
 {
-    tiled2d_body<S, R, TX, TY, true>(P, g_in, g_out, T_in, T_out, Y_in, Y_out, solid, tiles);
+    tiled2d_body<S, R, TX, TY, true>(P, g_in, g_out, T_in, T_out, Y_in, Y_out, solid, tiles, nullptr);
 }
 
 // The cells the tiled kernel leaves out: general form over a cell list
