@@ -28,7 +28,7 @@ static cudaError_t launch_t3(const StepParams<R>& P, StateView in, StateView out
     cudaError_t e = SPLIT ? cudaFuncSetAttribute(fkern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
                           : cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    if (SPLIT && (b.aux == nullptr || b.interior == nullptr)) return cudaErrorInvalidValue;
+    if (b.interior == nullptr || (SPLIT && b.aux == nullptr)) return cudaErrorInvalidValue;
     const bool fork = (b.nface > 0 || b.nwall > 0) && side.stream != nullptr;
     if (fork) {
         if ((e = cudaEventRecord(side.fork, stream)) != cudaSuccess) return e;
@@ -51,13 +51,13 @@ static cudaError_t launch_t3(const StepParams<R>& P, StateView in, StateView out
     dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY, (P.nz + ZC - 1) / ZC);
     if constexpr (SPLIT) {
         fkern<<<grid, dim3(TX, TY), smem, stream>>>(P, (const S*)in.g, (const S*)in.T, (S*)out.T, (const S*)in.Y,
-                                                    (S*)out.Y, solid, (R*)b.aux);
+                                                    (S*)out.Y, b.interior, (R*)b.aux);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         step_kernel_collide3d<S, R><<<dim3((P.nx + 127) / 128, P.ny, P.nz), 128, 0, stream>>>(
             P, (const S*)in.g, (S*)out.g, (const S*)in.T, (const S*)in.Y, b.interior, (const R*)b.aux);
     } else {
         kern<<<grid, dim3(TX, TY), smem, stream>>>(P, (const S*)in.g, (S*)out.g, (const S*)in.T, (S*)out.T,
-                                                   (const S*)in.Y, (S*)out.Y, solid);
+                                                   (const S*)in.Y, (S*)out.Y, b.interior);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (fork) {

@@ -78,11 +78,11 @@ __device__ __forceinline__ R fd_axis_pts(const StepParams<R>& P, const TileSmem<
     return drho;
 }
 
-// stage plane z (grid coordinate) into ring slot `slot`
+// stage plane z (grid coordinate) into ring slot `slot`; solid points are
+// staged like fluid ones (never read: the tile updates interior cells only)
 template <typename S, typename R, int TX, int TY>
 __device__ __forceinline__ void stage_plane(const StepParams<R>& P, const TileSmem<R>& sm, int slot, int x0, int y0,
-                                            int z, const S* __restrict__ T_in, const S* __restrict__ Y_in,
-                                            const uint8_t* __restrict__ solid)
+                                            int z, const S* __restrict__ T_in, const S* __restrict__ Y_in)
 {
     using G = Tile3Geom<TX, TY>;
     constexpr int NPT = G::NPT;
@@ -91,7 +91,6 @@ __device__ __forceinline__ void stage_plane(const StepParams<R>& P, const TileSm
     const int tid = threadIdx.x + TX * threadIdx.y;
     // all of this thread's global loads first, then the derived values
     long long cell[NIT];  // -1: outside the domain
-    uint8_t s[NIT];
     R T[NIT], Y[NIT][NSP];
 #pragma unroll
     for (int it = 0; it < NIT; ++it) {
@@ -104,13 +103,9 @@ __device__ __forceinline__ void stage_plane(const StepParams<R>& P, const TileSm
         if ((gx < 0 || gx >= P.nx) && P.bc[0] == BC_PERIODIC) gx = ((gx % P.nx) + P.nx) % P.nx;
         if ((gy < 0 || gy >= P.ny) && P.bc[2] == BC_PERIODIC) gy = ((gy % P.ny) + P.ny) % P.ny;
         if ((gz < 0 || gz >= P.nz) && P.bc[4] == BC_PERIODIC) gz = ((gz % P.nz) + P.nz) % P.nz;
-        if (gx < 0 || gx >= P.nx || gy < 0 || gy >= P.ny || gz < 0 || gz >= P.nz) {
-            sm.mask[slot * G::NPP + q] = 2;
-            continue;
-        }
+        if (gx < 0 || gx >= P.nx || gy < 0 || gy >= P.ny || gz < 0 || gz >= P.nz) continue;
         const long long c = (long long)gx + (long long)P.nx * (gy + (long long)P.ny * gz);
         cell[it] = c;
-        s[it] = solid[c];
         T[it] = R(T_in[c]);
 #pragma unroll
         for (int k = 0; k < NSP; ++k) Y[it][k] = R(Y_in[(long long)k * N + c]);
@@ -119,8 +114,6 @@ __device__ __forceinline__ void stage_plane(const StepParams<R>& P, const TileSm
     for (int it = 0; it < NIT; ++it) {
         if (cell[it] < 0) continue;
         const int pt = slot * G::NPP + tid + it * NTHR;
-        sm.mask[pt] = s[it] ? 1 : 0;
-        if (s[it]) continue;
         const R invW = inv_molar_mass(P, Y[it]);
         const R W = fdiv(R(1), invW);
         sm.T[pt] = T[it];
@@ -138,7 +131,7 @@ template <typename S, typename R, int TX, int TY, int ZC, bool SPLIT = false>
 __device__ __forceinline__ void tiled3d_body(const StepParams<R>& P, const S* __restrict__ g_in,
                                              S* __restrict__ g_out, const S* __restrict__ T_in,
                                              S* __restrict__ T_out, const S* __restrict__ Y_in,
-                                             S* __restrict__ Y_out, const uint8_t* __restrict__ solid,
+                                             S* __restrict__ Y_out, const uint8_t* __restrict__ interior,
                                              R* __restrict__ aux = nullptr)
 {
     using G = Tile3Geom<TX, TY>;
@@ -157,7 +150,7 @@ __device__ __forceinline__ void tiled3d_body(const StepParams<R>& P, const S* __
     const long long plane = (long long)P.nx * P.ny;
     // ring slot of grid plane z: (z + 5*big) % 5 keeps it non-negative
     auto slot_of = [](int z) { return (z + 10) % 5; };
-    for (int dz = -2; dz <= 1; ++dz) stage_plane<S, R, TX, TY>(P, sm, slot_of(zb + dz), x0, y0, zb + dz, T_in, Y_in, solid);
+    for (int dz = -2; dz <= 1; ++dz) stage_plane<S, R, TX, TY>(P, sm, slot_of(zb + dz), x0, y0, zb + dz, T_in, Y_in);
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     const int q0 = (threadIdx.y + 2) * SX + threadIdx.x + 2;  // in-plane point of this thread
     const int zend = zb + ZC < P.nz ? zb + ZC : P.nz;
@@ -168,7 +161,11 @@ __device__ __forceinline__ void tiled3d_body(const StepParams<R>& P, const S* __
         // offsets stay inside the domain for any in-range cell)
         const long long c = (long long)x + (long long)P.nx * y + plane * z;
         R g[27];
+        // the cell's class (+-2 along the three axes and the 26 neighbours
+        // are fluid cells of the domain), precomputed per cell
+        bool active = false;
         if (inside) {
+            active = interior[c] != 0;
             const int oxm = x == 0 ? P.nx - 1 : -1, oxp = x == P.nx - 1 ? 1 - P.nx : 1;
             const long long oym = y == 0 ? (long long)(P.ny - 1) * P.nx : -(long long)P.nx;
             const long long oyp = y == P.ny - 1 ? (long long)(1 - P.ny) * P.nx : (long long)P.nx;
@@ -183,28 +180,10 @@ __device__ __forceinline__ void tiled3d_body(const StepParams<R>& P, const S* __
                 g[i] = R(__ldg(gc + (long long)i * N + o));
             }
         }
-        stage_plane<S, R, TX, TY>(P, sm, slot_of(z + 2), x0, y0, z + 2, T_in, Y_in, solid);
+        stage_plane<S, R, TX, TY>(P, sm, slot_of(z + 2), x0, y0, z + 2, T_in, Y_in);
         __syncthreads();
         const int sc = slot_of(z);
         const int p0 = sc * NPP + q0;
-        bool active = inside && !sm.mask[p0];
-        if (active) {
-            // interior: +-2 along the three axes and the 26 neighbours
-            bool fast = true;
-#pragma unroll
-            for (int j = 1; j <= 2; ++j)
-                fast = fast && !sm.mask[p0 + j] && !sm.mask[p0 - j] && !sm.mask[p0 + j * SX] &&
-                       !sm.mask[p0 - j * SX] && !sm.mask[slot_of(z + j) * NPP + q0] &&
-                       !sm.mask[slot_of(z - j) * NPP + q0];
-#pragma unroll
-            for (int dz = -1; dz <= 1; ++dz)
-#pragma unroll
-                for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-                    for (int dx = -1; dx <= 1; ++dx)
-                        fast = fast && !sm.mask[slot_of(z + dz) * NPP + q0 + dy * SX + dx];
-            active = fast;
-        }
         if (active) {
             const R T0 = sm.T[p0], invW0 = sm.invW[p0], rho0 = sm.rho[p0];
             R Y0[NSP];
@@ -273,9 +252,9 @@ __global__ void __launch_bounds__(TX * TY) step_kernel_tiled3d(StepParams<R> P, 
                                                                S* __restrict__ g_out, const S* __restrict__ T_in,
                                                                S* __restrict__ T_out, const S* __restrict__ Y_in,
                                                                S* __restrict__ Y_out,
-                                                               const uint8_t* __restrict__ solid)
+                                                               const uint8_t* __restrict__ interior)
 {
-    tiled3d_body<S, R, TX, TY, ZC>(P, g_in, g_out, T_in, T_out, Y_in, Y_out, solid);
+    tiled3d_body<S, R, TX, TY, ZC>(P, g_in, g_out, T_in, T_out, Y_in, Y_out, interior);
 }
 
 // the same with the registers capped so that MINB blocks fit on an SM
@@ -283,9 +262,9 @@ template <typename S, typename R, int TX, int TY, int ZC, int MINB>
 __global__ void __launch_bounds__(TX * TY, MINB)
     step_kernel_tiled3d_capped(StepParams<R> P, const S* __restrict__ g_in, S* __restrict__ g_out,
                                const S* __restrict__ T_in, S* __restrict__ T_out, const S* __restrict__ Y_in,
-                               S* __restrict__ Y_out, const uint8_t* __restrict__ solid)
+                               S* __restrict__ Y_out, const uint8_t* __restrict__ interior)
 {
-    tiled3d_body<S, R, TX, TY, ZC>(P, g_in, g_out, T_in, T_out, Y_in, Y_out, solid);
+    tiled3d_body<S, R, TX, TY, ZC>(P, g_in, g_out, T_in, T_out, Y_in, Y_out, interior);
 }
 
 // a1-a7 of the interior cells (the FD half of a split step); FP32 held to
@@ -293,10 +272,10 @@ __global__ void __launch_bounds__(TX * TY, MINB)
 template <typename S, typename R, int TX, int TY, int ZC>
 __global__ void __launch_bounds__(TX * TY, sizeof(R) == 4 ? 512 / (TX * TY) : 1)
     step_kernel_fd3d(StepParams<R> P, const S* __restrict__ g_in, const S* __restrict__ T_in, S* __restrict__ T_out,
-                     const S* __restrict__ Y_in, S* __restrict__ Y_out, const uint8_t* __restrict__ solid,
+                     const S* __restrict__ Y_in, S* __restrict__ Y_out, const uint8_t* __restrict__ interior,
                      R* __restrict__ aux)
 {
-    tiled3d_body<S, R, TX, TY, ZC, true>(P, g_in, nullptr, T_in, T_out, Y_in, Y_out, solid, aux);
+    tiled3d_body<S, R, TX, TY, ZC, true>(P, g_in, nullptr, T_in, T_out, Y_in, Y_out, interior, aux);
 }
 
 // a1, a2 and a8-a10 of the interior cells (the LB half of a split step):
