@@ -248,21 +248,27 @@ def cpu_baseline(args, precision):
 
 def gradient_rate(args):
     """Gradient steps per second of flame position w.r.t. (ln A, Ta, T_wall,
-    u_in) on the 512x64 cold-wall channel (tangent precision), next to plain
-    FP64 steps per second on the same case; CUDA events on the handle's
-    stream."""
+    u_in) on the 512x64 cold-wall channel: the mixed tangent form (FP32
+    forward, FP64 Arrhenius above T_fp64, FP64 accumulation of the
+    gradient) and the FP64 tangent form, next to plain FP64 (and mixed)
+    steps per second on the same case; CUDA events on the handle's stream."""
     import torch
 
     from paper_2304_05657_gb300 import lbfd
 
     cfg, solid, T, Y = inputs.channel(nx=512, ny=64, walls="isothermal", T_wall=300.0)
     out = {"workload": "D2Q9 channel 512x64, isothermal 300 K walls, objective: flame position",
-           "mode": "tangent-linear (forward), 4 directions, FP64", "steps": args.grad_steps}
+           "mode": "tangent-linear (forward), 4 directions; grad_steps_per_s: FP32 forward with FP64 "
+                   "Arrhenius above 1000 K and FP64 gradient accumulation",
+           "steps": args.grad_steps}
     stream = torch.cuda.current_stream()
-    for prec in ("tangent", "fp64"):
+    grads = {}
+    key = {"tangent_mixed": "grad_steps_per_s", "tangent": "grad_steps_per_s_fp64_tangent",
+           "fp64": "fp64_steps_per_s", "mixed": "mixed_steps_per_s"}
+    for prec in ("tangent_mixed", "tangent", "fp64", "mixed"):
         s = lbfd.Solver(dict(cfg, precision=prec), solid, stream=stream)
         s.init_fields(T, Y)
-        if prec == "fp64":
+        if prec in ("fp64", "mixed"):
             s.autotune(reps=5)
         s.step(5)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -270,12 +276,15 @@ def gradient_rate(args):
         s.step(args.grad_steps)
         e1.record(stream)
         torch.cuda.synchronize()
-        rate = args.grad_steps / (e0.elapsed_time(e1) * 1e-3)
-        out["grad_steps_per_s" if prec == "tangent" else "fp64_steps_per_s"] = rate
-        if prec == "tangent":
+        out[key[prec]] = args.grad_steps / (e0.elapsed_time(e1) * 1e-3)
+        if prec.startswith("tangent"):
             J, g = s.gradient(lbfd.OBJ_FLAME_POSITION)
-            out["dJ_dtheta"] = dict(zip(lbfd.THETA, [float(x) for x in g]))
+            grads[prec] = np.asarray(g, dtype=np.float64)
         s.close()
+    out["dJ_dtheta"] = dict(zip(lbfd.THETA, [float(x) for x in grads["tangent_mixed"]]))
+    out["dJ_dtheta_fp64_tangent"] = dict(zip(lbfd.THETA, [float(x) for x in grads["tangent"]]))
+    out["mixed_vs_fp64_tangent_max_rel"] = float(np.max(np.abs(grads["tangent_mixed"] - grads["tangent"])
+                                                       / np.abs(grads["tangent"])))
     out["grad_vs_fp64_step_time"] = out["fp64_steps_per_s"] / out["grad_steps_per_s"]
     return out
 

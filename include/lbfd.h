@@ -65,6 +65,10 @@ extern "C" {
                           with respect to theta = (ln A, Ta, T_wall, u_in); 2-D only,
                           general-form kernel.  T_wall moves every isothermal wall face
                           and, when solids are isothermal, T_solid together. */
+#define LBFD_TANGENT_MIXED 3 /* as LBFD_TANGENT with FP32 values and derivatives
+                                (FP32 forward), the Arrhenius rate and its derivatives
+                                in FP64 above T_fp64 and the objectives accumulated
+                                in FP64 (lbfd_gradient); no curved walls. */
 
 /* objectives of lbfd_gradient */
 #define LBFD_OBJ_FLAME_POSITION 0 /* x_f [m] as in lbfd_flame_position */

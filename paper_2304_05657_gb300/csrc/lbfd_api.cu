@@ -23,6 +23,7 @@
 using lbfd::StateView;
 using lbfd::StepParams;
 using lbfd::Tan;
+using lbfd::Tanf;
 
 struct lbfd_handle {
     lbfd_grid grid;
@@ -52,7 +53,8 @@ struct lbfd_handle {
     int variant;          // kernel variant (lbfd::launch_step)
     StepParams<double> Pd;
     StepParams<float> Pf;
-    StepParams<lbfd::Tan> Pt;  // tangent precision: parameters with their seeds
+    StepParams<lbfd::Tan> Pt;    // tangent precision: parameters with their seeds
+    StepParams<lbfd::Tanf> Ptf;  // mixed tangent precision
     double section;            // fluid cells of the x = 0 section
     // CUDA graph of `graph_n` steps starting from buffer `graph_parity`
     cudaGraphExec_t graph;
@@ -156,8 +158,11 @@ void fill_params(const lbfd_handle* h, StepParams<R>& P)
     P.cs = (R)sqrt(cs2);
 }
 
-// derivative directions of the tangent precision: (ln A, Ta, T_wall, u_in)
-void seed_tangents(const lbfd_handle* h, StepParams<Tan>& P)
+static bool is_tangent(int precision) { return precision == LBFD_TANGENT || precision == LBFD_TANGENT_MIXED; }
+
+// derivative directions of the tangent precisions: (ln A, Ta, T_wall, u_in)
+template <typename TT>
+void seed_tangents(const lbfd_handle* h, StepParams<TT>& P)
 {
     P.A_lat.d[0] = P.A_lat.v;  // d(A dt)/d(ln A)
     P.Ta.d[1] = 1.0;
@@ -187,8 +192,8 @@ int validate(const lbfd_grid* G, const lbfd_mechanism* M, const lbfd_params* p)
         if (!(M->W[k] > 0.0) || !(M->Le[k] > 0.0)) return LBFD_EINVAL;
     if (!(M->A >= 0.0) || !(M->Ta >= 0.0) || !(M->cp > 0.0) || !std::isfinite(M->Q)) return LBFD_EINVAL;
     if (!(p->T_in > 0.0) || !(p->dt > 0.0) || !(p->Pr > 0.0) || !(p->weno_eps > 0.0)) return LBFD_EINVAL;
-    if (p->precision != LBFD_FP64 && p->precision != LBFD_MIXED && p->precision != LBFD_TANGENT) return LBFD_EINVAL;
-    if (p->precision == LBFD_TANGENT && G->dim != 2) return LBFD_ENOTSUP;
+    if (p->precision != LBFD_FP64 && p->precision != LBFD_MIXED && !is_tangent(p->precision)) return LBFD_EINVAL;
+    if (is_tangent(p->precision) && G->dim != 2) return LBFD_ENOTSUP;
     double ysum = 0.0;
     for (int k = 0; k < lbfd::NSP; ++k) ysum += p->Y_in[k];
     if (fabs(ysum - 1.0) > 1e-6) return LBFD_EINVAL;
@@ -241,9 +246,12 @@ int upload_planes(lbfd_handle* h, int which, int first_plane, int nplanes, const
     } else if (h->precision == LBFD_MIXED) {
         float* d = (float*)stage.data();
         for (size_t i = 0; i < n * nplanes; ++i) d[i] = (float)src[i];
-    } else {  // tangent: the given state carries no derivative
+    } else if (h->precision == LBFD_TANGENT) {  // the given state carries no derivative
         Tan* d = (Tan*)stage.data();
         for (size_t i = 0; i < n * nplanes; ++i) d[i] = Tan(src[i]);
+    } else {
+        Tanf* d = (Tanf*)stage.data();
+        for (size_t i = 0; i < n * nplanes; ++i) d[i] = Tanf(src[i]);
     }
     char* dst = (char*)h->buf[which] + (size_t)first_plane * h->stride * h->esz;
     CK(cudaMemcpy2DAsync(dst, (size_t)h->stride * h->esz, stage.data(), n * h->esz, n * h->esz, nplanes,
@@ -295,13 +303,15 @@ cudaError_t launch_one(lbfd_handle* h, int from, int v, cudaStream_t s)
     }
     if (h->precision == LBFD_TANGENT)
         return lbfd::launch_step_tangent(h->dim, h->Pt, view(h, from), view(h, from ^ 1), h->solid, s);
+    if (h->precision == LBFD_TANGENT_MIXED)
+        return lbfd::launch_step_tangent(h->dim, h->Ptf, view(h, from), view(h, from ^ 1), h->solid, s);
     return lbfd::launch_step(h->dim, h->precision, v, h->Pd, h->Pf, view(h, from), view(h, from ^ 1), h->solid,
                              lists(h), h->side, s);
 }
 
 int num_variants_of(const lbfd_handle* h)
 {
-    return h->precision == LBFD_TANGENT ? 1 : lbfd::num_variants(h->dim);
+    return is_tangent(h->precision) ? 1 : lbfd::num_variants(h->dim);
 }
 
 }  // namespace
@@ -350,10 +360,12 @@ int lbfd_create(const lbfd_grid* grid, const uint8_t* solid_mask, const lbfd_mec
     h->precision = params->precision;
     h->ncell = (long long)h->grid.nx * h->grid.ny * h->grid.nz;
     h->stride = (h->ncell + 63) / 64 * 64;  // 256-byte aligned FP32 planes
-    h->esz = h->precision == LBFD_FP64 ? 8 : (h->precision == LBFD_MIXED ? 4 : sizeof(Tan));
+    h->esz = h->precision == LBFD_FP64 ? 8
+             : h->precision == LBFD_MIXED ? 4
+             : h->precision == LBFD_TANGENT ? sizeof(Tan) : sizeof(Tanf);
     h->planes = (size_t)h->Q + 1 + lbfd::NSP;
     h->stream = nullptr;
-    h->variant = h->precision != LBFD_TANGENT ? 1 : 0;
+    h->variant = is_tangent(h->precision) ? 0 : 1;
     const size_t bytes = h->planes * (size_t)h->stride * h->esz;
     for (int b = 0; b < 2; ++b) {
         e = cudaMalloc(&h->buf[b], bytes);
@@ -374,6 +386,8 @@ int lbfd_create(const lbfd_grid* grid, const uint8_t* solid_mask, const lbfd_mec
     fill_params(h, h->Pf);
     fill_params(h, h->Pt);
     seed_tangents(h, h->Pt);
+    fill_params(h, h->Ptf);
+    seed_tangents(h, h->Ptf);
     // mask
     std::vector<uint8_t> m((size_t)h->ncell, 0);
     if (solid_mask)
@@ -382,7 +396,7 @@ int lbfd_create(const lbfd_grid* grid, const uint8_t* solid_mask, const lbfd_mec
         free_handle(h);
         return cuda_fail(e, "cudaMemcpy(mask)");
     }
-    if (h->precision != LBFD_TANGENT &&
+    if (!is_tangent(h->precision) &&
         ((e = cudaDeviceGetStreamPriorityRange(&h->side.low, &h->side.priority)) != cudaSuccess ||
          (e = cudaStreamCreateWithPriority(&h->side.stream, cudaStreamNonBlocking, h->side.priority)) !=
              cudaSuccess ||
@@ -432,7 +446,7 @@ int lbfd_create(const lbfd_grid* grid, const uint8_t* solid_mask, const lbfd_mec
                             std::back_inserter(wl));
         h->nbndw = (long long)wl.size();
         // the Lambda / grad rho planes of the split variants
-        if (h->precision != LBFD_TANGENT &&
+        if (!is_tangent(h->precision) &&
             (e = cudaMalloc(&h->aux, (size_t)4 * h->stride * h->esz)) != cudaSuccess) {
             free_handle(h);
             return cuda_fail(e, "split-step buffers");
@@ -582,7 +596,7 @@ int lbfd_launches_per_step(const lbfd_handle* h)
     if (!h) return -1;
     const lbfd::BoundaryLists b = lists(h);
     int n = 1;
-    if (h->variant > 0 && h->precision != LBFD_TANGENT) {
+    if (h->variant > 0 && !is_tangent(h->precision)) {
         if (h->dim == 3) {
             n += (b.nface > 0 ? 1 : 0) + (b.nwall > 0 ? 1 : 0) + (h->variant >= 4 ? 1 : 0);
         } else {
@@ -596,6 +610,7 @@ int lbfd_launches_per_step(const lbfd_handle* h)
 int lbfd_set_curved_walls(lbfd_handle* h, int n, const double* prims)
 {
     if (!h || n < 0 || (n > 0 && !prims)) return LBFD_EINVAL;
+    if (h->precision == LBFD_TANGENT_MIXED && n > 0) return LBFD_ENOTSUP;
     for (int k = 0; k < n; ++k) {
         const double* P = prims + 5 * k;
         const int t = (int)P[0];
@@ -618,7 +633,7 @@ int lbfd_set_curved_walls(lbfd_handle* h, int n, const double* prims)
     h->gh_w = nullptr;
     h->gval = nullptr;
     h->nghost = 0;
-    h->Pd.curved = h->Pf.curved = h->Pt.curved = 0;
+    h->Pd.curved = h->Pf.curved = h->Pt.curved = h->Ptf.curved = 0;
     if (h->graph) {
         cudaGraphExecDestroy(h->graph);
         h->graph = nullptr;
@@ -787,6 +802,9 @@ int lbfd_set_inlet_velocity(lbfd_handle* h, double u_in)
     const double seed = h->Pt.u_in.d[3];
     h->Pt.u_in = Tan(u_in);
     h->Pt.u_in.d[3] = seed;
+    const float seedf = h->Ptf.u_in.d[3];
+    h->Ptf.u_in = Tanf(u_in);
+    h->Ptf.u_in.d[3] = seedf;
     if (h->graph) {  // kernel parameters are baked into a captured graph
         cudaGraphExecDestroy(h->graph);
         h->graph = nullptr;
@@ -835,13 +853,14 @@ int lbfd_set_state_raw(lbfd_handle* h, const void* src, size_t bytes)
 
 int lbfd_read_tangent(lbfd_handle* h, int field, int k, double* out)
 {
-    if (!h || !out || h->precision != LBFD_TANGENT || k < 0 || k >= lbfd::NTAN) return LBFD_EINVAL;
+    if (!h || !out || !is_tangent(h->precision) || k < 0 || k >= lbfd::NTAN) return LBFD_EINVAL;
     int plane;
     if (field == LBFD_FIELD_T) plane = h->Q;
     else if (field >= LBFD_FIELD_Y0 && field < LBFD_FIELD_Y0 + lbfd::NSP) plane = h->Q + 1 + (field - LBFD_FIELD_Y0);
     else if (field >= LBFD_FIELD_G0 && field < LBFD_FIELD_G0 + h->Q) plane = field - LBFD_FIELD_G0;
     else return LBFD_EINVAL;
-    CK(lbfd::launch_tangent_field(h->ncell, h->stride, h->buf[h->cur], plane, k, h->tmp, h->stream));
+    CK(lbfd::launch_tangent_field(h->precision == LBFD_TANGENT_MIXED, h->ncell, h->stride, h->buf[h->cur], plane, k,
+                                  h->tmp, h->stream));
     CK(cudaMemcpyAsync(out, h->tmp, (size_t)h->ncell * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return LBFD_OK;
@@ -849,10 +868,14 @@ int lbfd_read_tangent(lbfd_handle* h, int field, int k, double* out)
 
 int lbfd_gradient(lbfd_handle* h, int objective, double* value, double* grad)
 {
-    if (!h || h->precision != LBFD_TANGENT || (objective != LBFD_OBJ_FLAME_POSITION && objective != LBFD_OBJ_HEAT_RELEASE))
+    if (!h || !is_tangent(h->precision) ||
+        (objective != LBFD_OBJ_FLAME_POSITION && objective != LBFD_OBJ_HEAT_RELEASE))
         return LBFD_EINVAL;
     double r[1 + lbfd::NTAN];
-    CK(lbfd::launch_objective(h->Pt, view(h, h->cur), h->solid, objective, h->red, h->stream));
+    if (h->precision == LBFD_TANGENT)
+        CK(lbfd::launch_objective(h->Pt, view(h, h->cur), h->solid, objective, h->red, h->stream));
+    else
+        CK(lbfd::launch_objective(h->Ptf, view(h, h->cur), h->solid, objective, h->red, h->stream));
     CK(cudaMemcpyAsync(r, h->red, sizeof r, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     double scale = 1.0;

@@ -135,6 +135,15 @@ __device__ __forceinline__ R arrhenius(const StepParams<R>& P, R T, R yf, R yo)
         return P.A_lat * yf * yo * expf(-(P.Ta / T));
     } else if constexpr (std::is_same<R, double>::value) {
         return P.A_lat * yf * yo * ::exp(-(P.Ta / T));
+    } else if constexpr (std::is_same<R, Tanf>::value) {
+        if (T > P.T_fp64) {  // FP64 rate and derivatives, as the mixed form
+            Tan A = widen(P.A_lat), Ta = widen(P.Ta);
+            A.v = P.A_lat_d;
+            A.d[0] = P.A_lat_d;  // d(A dt)/d(ln A)
+            Ta.v = P.Ta_d;
+            return narrow(A * widen(yf) * widen(yo) * exp(-(Ta / widen(T))));
+        }
+        return P.A_lat * yf * yo * exp(-(P.Ta / T));
     } else {
         return P.A_lat * yf * yo * exp(-(P.Ta / T));  // the Dual overload
     }

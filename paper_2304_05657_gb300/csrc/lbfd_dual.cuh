@@ -94,7 +94,8 @@ template <typename T, int N>
 __host__ __device__ inline Dual<T, N> exp(const Dual<T, N>& a)
 {
     Dual<T, N> r;
-    r.v = ::exp(a.v);
+    if constexpr (sizeof(T) == 4) r.v = expf(a.v);
+    else r.v = ::exp(a.v);
 #pragma unroll
     for (int k = 0; k < N; ++k) r.d[k] = r.v * a.d[k];
     return r;
@@ -109,8 +110,31 @@ __host__ __device__ inline double val(float x) { return (double)x; }
 template <typename T, int N>
 __host__ __device__ inline double val(const Dual<T, N>& x) { return (double)x.v; }
 
-// tangents with respect to (ln A, Ta, T_wall, u_in)
+// FP64 copy of an FP32 dual number and back (round to nearest)
+template <int N>
+__host__ __device__ inline Dual<double, N> widen(const Dual<float, N>& a)
+{
+    Dual<double, N> r;
+    r.v = a.v;
+#pragma unroll
+    for (int k = 0; k < N; ++k) r.d[k] = a.d[k];
+    return r;
+}
+template <int N>
+__host__ __device__ inline Dual<float, N> narrow(const Dual<double, N>& a)
+{
+    Dual<float, N> r;
+    r.v = (float)a.v;
+#pragma unroll
+    for (int k = 0; k < N; ++k) r.d[k] = (float)a.d[k];
+    return r;
+}
+
+// tangents with respect to (ln A, Ta, T_wall, u_in): FP64, and FP32 (the
+// mixed tangent form: FP32 state and arithmetic, FP64 Arrhenius above
+// T_fp64 and FP64 accumulation of the objectives)
 constexpr int NTAN = 4;
 using Tan = Dual<double, NTAN>;
+using Tanf = Dual<float, NTAN>;
 
 }  // namespace lbfd

@@ -104,13 +104,18 @@ cudaError_t launch_field(int dim, int precision, const StepParams<double>& Pd, S
 cudaError_t launch_cells(int dim, int precision, const StepParams<double>& Pd, StateView st, const long long* cells,
                          long long n, double* out, cudaStream_t stream);
 
-// Tangent-linear step (precision 2: Dual<double, 4> values, general form,
-// 2-D), tangent read-out and objective gradients (lbfd_tangent.cu).
+// Tangent-linear step (precision 2: Dual<double, 4> values; precision 3:
+// Dual<float, 4>; general form, 2-D), tangent read-out and objective
+// gradients (lbfd_tangent.cu).
 cudaError_t launch_step_tangent(int dim, const StepParams<Tan>& P, StateView in, StateView out, const uint8_t* solid,
                                 cudaStream_t stream);
-cudaError_t launch_tangent_field(long long ncell, long long N, const void* state_base, int plane, int k, double* out,
-                                 cudaStream_t stream);
+cudaError_t launch_step_tangent(int dim, const StepParams<Tanf>& P, StateView in, StateView out, const uint8_t* solid,
+                                cudaStream_t stream);
+cudaError_t launch_tangent_field(bool fp32, long long ncell, long long N, const void* state_base, int plane, int k,
+                                 double* out, cudaStream_t stream);
 cudaError_t launch_objective(const StepParams<Tan>& P, StateView st, const uint8_t* solid, int objective, double* red,
+                             cudaStream_t stream);
+cudaError_t launch_objective(const StepParams<Tanf>& P, StateView st, const uint8_t* solid, int objective, double* red,
                              cudaStream_t stream);
 
 // Curved walls (lbfd_geometry.cu): host tables of cut links and ghosts.

@@ -205,6 +205,8 @@ cudaError_t launch_diagnostics(int dim, int precision, const StepParams<double>&
                         : diag_launch<3, double>(P, st, solid, y0, y1, red, stream);
     if (precision == 2)
         return dim == 2 ? diag_launch<2, Tan>(P, st, solid, y0, y1, red, stream) : cudaErrorInvalidValue;
+    if (precision == 3)
+        return dim == 2 ? diag_launch<2, Tanf>(P, st, solid, y0, y1, red, stream) : cudaErrorInvalidValue;
     return dim == 2 ? diag_launch<2, float>(P, st, solid, y0, y1, red, stream)
                     : diag_launch<3, float>(P, st, solid, y0, y1, red, stream);
 }
@@ -282,6 +284,9 @@ cudaError_t launch_cells(int dim, int precision, const StepParams<double>& P, St
     if (precision == 2)
         cells_kernel<Tan><<<blocks, 256, 0, stream>>>(P.N, Q, (const Tan*)st.g, (const Tan*)st.T, (const Tan*)st.Y,
                                                       cells, n, out);
+    else if (precision == 3)
+        cells_kernel<Tanf><<<blocks, 256, 0, stream>>>(P.N, Q, (const Tanf*)st.g, (const Tanf*)st.T,
+                                                       (const Tanf*)st.Y, cells, n, out);
     else if (precision == 0)
         cells_kernel<double><<<blocks, 256, 0, stream>>>(P.N, Q, (const double*)st.g, (const double*)st.T,
                                                          (const double*)st.Y, cells, n, out);
@@ -298,6 +303,12 @@ cudaError_t launch_field(int dim, int precision, const StepParams<double>& P, St
     if (precision == 2) {
         if (dim != 2) return cudaErrorInvalidValue;
         field_kernel<2, Tan><<<blocks, 256, 0, stream>>>(P, (const Tan*)st.g, (const Tan*)st.T, (const Tan*)st.Y,
+                                                          solid, field, out);
+        return cudaGetLastError();
+    }
+    if (precision == 3) {
+        if (dim != 2) return cudaErrorInvalidValue;
+        field_kernel<2, Tanf><<<blocks, 256, 0, stream>>>(P, (const Tanf*)st.g, (const Tanf*)st.T, (const Tanf*)st.Y,
                                                           solid, field, out);
         return cudaGetLastError();
     }

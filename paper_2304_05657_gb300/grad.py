@@ -5,7 +5,9 @@ The forward pass runs the coupled step in the library's tangent precision
 (every state value carries its four derivatives, propagated exactly through
 the discrete step), so the gradient is ready when the forward pass ends;
 backward only scales it by the incoming gradient.  With four parameters
-this needs one pass and no stored trajectory.
+this needs one pass and no stored trajectory.  precision "tangent" is FP64
+throughout; "tangent_mixed" runs the forward pass in FP32 (FP64 Arrhenius
+above T_fp64) and accumulates the objective and its gradient in FP64.
 """
 from __future__ import annotations
 
@@ -35,10 +37,13 @@ def theta_of(cfg: dict):
     return np.array([math.log(cfg["A"]), cfg["Ta"], Tw, cfg["u_in"]])
 
 
-def run_tangent(cfg: dict, solid, T0, Y0, steps: int, objective: int = lbfd.OBJ_FLAME_POSITION, theta=None):
+def run_tangent(cfg: dict, solid, T0, Y0, steps: int, objective: int = lbfd.OBJ_FLAME_POSITION, theta=None,
+                precision: str = "tangent"):
     """J after `steps` steps from (T0, Y0, g = 0) and dJ/dtheta."""
+    if precision not in ("tangent", "tangent_mixed"):
+        raise ValueError(precision)
     c = apply_theta(cfg, theta) if theta is not None else dict(cfg)
-    c["precision"] = "tangent"
+    c["precision"] = precision
     s = lbfd.Solver(c, solid)
     s.init_fields(T0, Y0)
     s.step(steps)
@@ -53,18 +58,20 @@ try:
     class FlameObjective(torch.autograd.Function):
         """J(theta) = flame position (or heat release) after `steps` steps.
 
-        forward(theta[4] float64 tensor, cfg, solid, T0, Y0, steps, objective)."""
+        forward(theta[4] float64 tensor, cfg, solid, T0, Y0, steps, objective,
+        precision)."""
 
         @staticmethod
-        def forward(ctx, theta, cfg, solid, T0, Y0, steps, objective=lbfd.OBJ_FLAME_POSITION):
-            J, g = run_tangent(cfg, solid, T0, Y0, int(steps), int(objective), theta.detach().cpu().numpy())
+        def forward(ctx, theta, cfg, solid, T0, Y0, steps, objective=lbfd.OBJ_FLAME_POSITION, precision="tangent"):
+            J, g = run_tangent(cfg, solid, T0, Y0, int(steps), int(objective), theta.detach().cpu().numpy(),
+                               precision)
             ctx.save_for_backward(torch.as_tensor(g, dtype=theta.dtype, device=theta.device))
             return theta.new_tensor(J)
 
         @staticmethod
         def backward(ctx, grad_out):
             (g,) = ctx.saved_tensors
-            return grad_out * g, None, None, None, None, None, None
+            return grad_out * g, None, None, None, None, None, None, None
 
 except ImportError:  # torch is optional for the C-ABI user
     FlameObjective = None

@@ -19,8 +19,8 @@ LIB_PATH = os.path.join(HERE, "liblbfd.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, EUNSTABLE, ENOTSUP = range(8)
 BC = {"periodic": 0, "wall_adiabatic": 1, "wall_isothermal": 2, "inlet": 3, "outlet": 4, "outlet_pressure": 5}
-FP64, MIXED, TANGENT = 0, 1, 2
-PRECISION = {"fp64": FP64, "mixed": MIXED, "tangent": TANGENT}
+FP64, MIXED, TANGENT, TANGENT_MIXED = 0, 1, 2, 3
+PRECISION = {"fp64": FP64, "mixed": MIXED, "tangent": TANGENT, "tangent_mixed": TANGENT_MIXED}
 OBJ_FLAME_POSITION, OBJ_HEAT_RELEASE = 0, 1
 THETA = ("ln_A", "Ta", "T_wall", "u_in")
 NSP = 5

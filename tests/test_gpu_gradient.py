@@ -68,6 +68,20 @@ def test_tangent_gradient_matches_central_differences(lbfd_lib, oracle_mod, obje
     assert np.all(np.abs(g) > 0)  # every parameter acts on the objective
 
 
+@pytest.mark.parametrize("objective", [lbfd.OBJ_FLAME_POSITION, lbfd.OBJ_HEAT_RELEASE])
+def test_mixed_tangent_gradient_matches_fp64_tangent(lbfd_lib, objective):
+    """FP32 forward pass with FP64 Arrhenius above 1000 K and FP64
+    accumulation of the objective: J within 1e-5 and every component of
+    dJ/dtheta within 2e-3 of the FP64 tangent (FP32 rounding carried over
+    150 steps through the state and its derivatives)."""
+    cfg, solid, T, Y = case()
+    J, g = grad.run_tangent(cfg, solid, T, Y, STEPS, objective)
+    Jm, gm = grad.run_tangent(cfg, solid, T, Y, STEPS, objective, precision="tangent_mixed")
+    assert abs(Jm - J) <= 1e-5 * abs(J), (Jm, J)
+    for k, name in enumerate(lbfd.THETA):
+        assert abs(gm[k] - g[k]) <= 2e-3 * abs(g[k]), (name, gm[k], g[k])
+
+
 def test_tangent_values_match_fp64_kernel(lbfd_lib):
     """The value part of the tangent state is the FP64 step."""
     cfg, solid, T, Y = case()
