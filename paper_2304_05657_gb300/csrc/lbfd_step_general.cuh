@@ -126,6 +126,34 @@ __device__ __forceinline__ R pull_general(const StepParams<R>& P, int i, const i
     return R(g[(long long)i * N + s]);  // Eq. 8
 }
 
+// a1 for a cell whose lattice neighbours are all inside the domain up to
+// periodic wrap and whose walls are staircase: plain pull, half-way
+// bounce-back (Eq. 28) from solid neighbours
+template <int DIM, typename S, typename R>
+__device__ __forceinline__ void pull_walls(const StepParams<R>& P, const int p[3], long long c,
+                                           const S* __restrict__ g, const uint8_t* __restrict__ solid, R* out)
+{
+    constexpr int Q = DIM == 2 ? 9 : 27;
+    const long long N = P.N;
+    const long long plane = (long long)P.nx * P.ny;
+    // offsets to the x-1, x+1, ... neighbours (wrapped on periodic axes)
+    const long long oxm = p[0] == 0 ? P.nx - 1 : -1, oxp = p[0] == P.nx - 1 ? 1 - P.nx : 1;
+    const long long oym = p[1] == 0 ? (long long)(P.ny - 1) * P.nx : -(long long)P.nx;
+    const long long oyp = p[1] == P.ny - 1 ? (long long)(1 - P.ny) * P.nx : (long long)P.nx;
+    long long ozm = 0, ozp = 0;
+    if (DIM == 3) {
+        ozm = p[2] == 0 ? (P.nz - 1) * plane : -plane;
+        ozp = p[2] == P.nz - 1 ? (1 - P.nz) * plane : plane;
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int cx = ccomp<DIM>(i, 0), cy = ccomp<DIM>(i, 1), cz = ccomp<DIM>(i, 2);
+        const long long s = c + (cx > 0 ? oxm : (cx < 0 ? oxp : 0)) + (cy > 0 ? oym : (cy < 0 ? oyp : 0)) +
+                            (cz > 0 ? ozm : (cz < 0 ? ozp : 0));
+        out[i] = solid[s] ? R(g[(long long)opposite<DIM>(i) * N + c]) : R(g[(long long)i * N + s]);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // a3: one FD line through the cell along an axis, with ghost points
 // ---------------------------------------------------------------------------
@@ -345,7 +373,14 @@ __device__ __forceinline__ void cell_step_general(const StepParams<R>& P, const 
     // small enough for the instruction cache; the pulled values pass
     // through a local array)
     R g[Q];
-    {
+    bool pulled = false;
+    if constexpr (!FACES) {  // no face rules: the compact form (staircase walls)
+        if (!P.curved) {
+            pull_walls<DIM, S, R>(P, p, c, g_in, solid, g);
+            pulled = true;
+        }
+    }
+    if (!pulled) {
         R gl[Q];
 #pragma unroll 1
         for (int i = 0; i < Q; ++i) gl[i] = pull_general<DIM, S, R, FACES>(P, i, p, c, g_in, solid, rho0);
