@@ -281,6 +281,24 @@ def gradient_rate(args):
             J, g = s.gradient(lbfd.OBJ_FLAME_POSITION)
             grads[prec] = np.asarray(g, dtype=np.float64)
         s.close()
+    # the discrete adjoint (reverse mode, FP64): forward with checkpoints
+    # every K steps, then the backward sweep with recomputation per segment
+    # (the tangent runs above also started from this initial state and ran
+    # 5 + grad_steps steps: the same map)
+    K = max(1, args.grad_steps // 4)
+    s = lbfd.Solver(dict(cfg, precision="fp64"), solid, stream=stream)
+    s.init_fields(T, Y)
+    s.autotune(reps=5)
+    s.init_fields(T, Y)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, ga = s.adjoint_gradient(5 + args.grad_steps, K)
+    torch.cuda.synchronize()
+    out["adjoint_grad_steps_per_s"] = (5 + args.grad_steps) / (time.perf_counter() - t0)
+    out["adjoint_checkpoint_every"] = K
+    s.close()
+    gt = grads["tangent"]
+    out["adjoint_vs_tangent_max_rel"] = float(np.max(np.abs(np.asarray(ga) - gt) / np.abs(gt)))
     out["dJ_dtheta"] = dict(zip(lbfd.THETA, [float(x) for x in grads["tangent_mixed"]]))
     out["dJ_dtheta_fp64_tangent"] = dict(zip(lbfd.THETA, [float(x) for x in grads["tangent"]]))
     out["mixed_vs_fp64_tangent_max_rel"] = float(np.max(np.abs(grads["tangent_mixed"] - grads["tangent"])

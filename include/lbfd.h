@@ -263,6 +263,24 @@ int lbfd_read_tangent(lbfd_handle* h, int field, int k, double* out);
  * its gradient dJ/dtheta[4].  Either pointer may be NULL.  Synchronises. */
 int lbfd_gradient(lbfd_handle* h, int objective, double* value, double* grad);
 
+/* Discrete adjoint (reverse mode), LBFD_FP64 2-D handles with staircase
+ * walls: advances the state by `steps` steps, keeping a checkpoint of the
+ * state every `checkpoint_every` steps, and returns J = the flame position
+ * x_f [m] after the last step (objective LBFD_OBJ_FLAME_POSITION) and
+ * dJ/dtheta[4], theta = (ln A, Ta, T_wall, u_in), by sweeping the steps
+ * backwards: each segment is recomputed from its checkpoint and the adjoint
+ * of every step, lambda^n = (dF/dx^n)^T lambda^{n+1}, is taken by recording
+ * each fluid cell's step on a reverse-mode tape (the exact transpose of the
+ * derivative of the discrete step, branches taken on the values) and adding
+ * (dF/dtheta)^T lambda^{n+1} to the gradient in FP64.  Device memory for the
+ * call: steps/checkpoint_every + checkpoint_every + 6 state copies plus a
+ * tape of at most 6 GB (28 B x 4096 nodes per cell, cells in chunks), freed
+ * before returning.  Errors: LBFD_EINVAL (arguments),
+ * LBFD_ENOTSUP (other precision, 3-D, curved walls, or a cell whose step
+ * needs more than the tape's 4096 nodes), LBFD_ENOMEM.  Synchronises. */
+int lbfd_adjoint_gradient(lbfd_handle* h, int steps, int checkpoint_every, int objective, double* value,
+                          double* grad);
+
 /* Raw state in storage precision (4 or 8 bytes per value; 40 for tangent):
  * layout g[Q][N], T[N], Y[nsp][N], contiguous; lbfd_state_bytes gives the size.
  * The host buffer may be pageable or pinned; the copy is ordered on the

@@ -812,6 +812,132 @@ int lbfd_set_inlet_velocity(lbfd_handle* h, double u_in)
     return LBFD_OK;
 }
 
+// the view of an FP64 state buffer laid out as the handle's
+static StateView view_of(const lbfd_handle* h, void* base)
+{
+    const size_t plane = (size_t)h->stride * h->esz;
+    StateView v;
+    v.g = base;
+    v.T = (char*)base + plane * h->Q;
+    v.Y = (char*)base + plane * (h->Q + 1);
+    return v;
+}
+
+int lbfd_adjoint_gradient(lbfd_handle* h, int steps, int checkpoint_every, int objective, double* value,
+                          double* grad)
+{
+    if (!h || steps < 1 || checkpoint_every < 1 || objective != LBFD_OBJ_FLAME_POSITION) return LBFD_EINVAL;
+    if (h->precision != LBFD_FP64 || h->dim != 2 || h->nghost > 0 || h->Pd.curved) return LBFD_ENOTSUP;
+    const int K = checkpoint_every < steps ? checkpoint_every : steps;
+    const int nseg = (steps + K - 1) / K;
+    const size_t sbytes = h->planes * (size_t)h->stride * sizeof(double);
+    const long long nel = (long long)h->planes * h->stride;
+    const int planes = (int)h->planes;
+    // tape: at most 6 GB, in chunks of cells
+    lbfd::AdjointWork w;
+    memset(&w, 0, sizeof w);
+    w.maxn = 4096;
+    const size_t node = lbfd::adjoint_node_bytes();
+    long long chunk = (long long)((size_t)6 << 30) / ((long long)w.maxn * (long long)node);
+    chunk = chunk / 64 * 64;
+    const long long need = (h->ncell + 63) / 64 * 64;
+    w.chunk = chunk < need ? chunk : need;
+    const size_t tape = (size_t)w.maxn * w.chunk;
+    char *ck = nullptr, *seg = nullptr;
+    double *lam0 = nullptr, *lam1 = nullptr, *dth = nullptr;
+    std::vector<void*> owned;
+    auto alloc = [&](void** p, size_t bytes) {
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e == cudaSuccess) owned.push_back(*p);
+        return e;
+    };
+    auto release = [&]() {
+        for (void* p : owned) cudaFree(p);
+    };
+    cudaError_t e;
+    if ((e = alloc((void**)&ck, sbytes * nseg)) != cudaSuccess || (e = alloc((void**)&seg, sbytes * K)) != cudaSuccess ||
+        (e = alloc((void**)&lam0, sbytes)) != cudaSuccess || (e = alloc((void**)&lam1, sbytes)) != cudaSuccess ||
+        (e = alloc((void**)&dth, lbfd::NTAN * sizeof(double))) != cudaSuccess ||
+        (e = alloc(&w.rin, nel * lbfd::rev_store_bytes())) != cudaSuccess ||
+        (e = alloc(&w.rout, nel * lbfd::rev_store_bytes())) != cudaSuccess ||
+        (e = alloc((void**)&w.a0, tape * sizeof(double))) != cudaSuccess ||
+        (e = alloc((void**)&w.a1, tape * sizeof(double))) != cudaSuccess ||
+        (e = alloc((void**)&w.adj, tape * sizeof(double))) != cudaSuccess ||
+        (e = alloc((void**)&w.p0, tape * sizeof(int16_t))) != cudaSuccess ||
+        (e = alloc((void**)&w.p1, tape * sizeof(int16_t))) != cudaSuccess ||
+        (e = alloc((void**)&w.flags, 2 * sizeof(int))) != cudaSuccess) {
+        release();
+        cuda_fail(e, "cudaMalloc(adjoint)");
+        return LBFD_ENOMEM;
+    }
+    cudaStream_t s = h->stream;
+#define AK(call)                         \
+    do {                                 \
+        cudaError_t e_ = (call);         \
+        if (e_ != cudaSuccess) {         \
+            release();                   \
+            return cuda_fail(e_, #call); \
+        }                                \
+    } while (0)
+    AK(cudaMemsetAsync(w.flags, 0, 2 * sizeof(int), s));
+    AK(cudaMemsetAsync(dth, 0, lbfd::NTAN * sizeof(double), s));
+    // forward pass from the handle's state, one checkpoint per segment
+    for (int g = 0; g < nseg; ++g) {
+        AK(cudaMemcpyAsync(ck + (size_t)g * sbytes, h->buf[h->cur], sbytes, cudaMemcpyDeviceToDevice, s));
+        const int len = steps - g * K < K ? steps - g * K : K;
+        const int st = lbfd_step(h, len);
+        if (st != LBFD_OK) {
+            release();
+            return st;
+        }
+    }
+    // J and its adjoint: x_f = dx sum_fluid Y_F / (Y_F,in * section)
+    double d[LBFD_NDIAG];
+    const int dst = lbfd_diagnostics(h, d);
+    if (dst != LBFD_OK) {
+        release();
+        return dst;
+    }
+    const double scale = h->section > 0.0 ? h->prm.dx / (h->prm.Y_in[h->mech.fuel] * h->section) : 0.0;
+    {
+        std::vector<double> lam((size_t)nel, 0.0);
+        const size_t off = (size_t)(h->Q + 1 + h->mech.fuel) * h->stride;
+        for (long long c = 0; c < h->ncell; ++c)
+            if (!h->mask_host[c]) lam[off + c] = scale;
+        AK(cudaMemcpyAsync(lam1, lam.data(), sbytes, cudaMemcpyHostToDevice, s));
+        AK(cudaStreamSynchronize(s));
+    }
+    // backward pass: each segment recomputed from its checkpoint
+    const lbfd::BoundaryLists b = lists(h);
+    for (int g = nseg - 1; g >= 0; --g) {
+        const int len = steps - g * K < K ? steps - g * K : K;
+        for (int j = 0; j < len; ++j)  // every slot starts as the checkpoint (solid cells never change)
+            AK(cudaMemcpyAsync(seg + (size_t)j * sbytes, ck + (size_t)g * sbytes, sbytes, cudaMemcpyDeviceToDevice,
+                               s));
+        for (int j = 1; j < len; ++j)
+            AK(lbfd::launch_step(h->dim, 0, h->variant, h->Pd, h->Pf, view_of(h, seg + (size_t)(j - 1) * sbytes),
+                                 view_of(h, seg + (size_t)j * sbytes), h->solid, b, h->side, s));
+        for (int j = len - 1; j >= 0; --j) {
+            AK(cudaMemsetAsync(lam0, 0, sbytes, s));
+            AK(lbfd::launch_adjoint_step(h->dim, h->Pd, planes, (const double*)(seg + (size_t)j * sbytes), h->solid,
+                                         lam1, lam0, dth, w, s));
+            std::swap(lam0, lam1);
+        }
+    }
+    int flags[2];
+    double gr[lbfd::NTAN];
+    AK(cudaMemcpyAsync(flags, w.flags, sizeof flags, cudaMemcpyDeviceToHost, s));
+    AK(cudaMemcpyAsync(gr, dth, sizeof gr, cudaMemcpyDeviceToHost, s));
+    AK(cudaStreamSynchronize(s));
+#undef AK
+    release();
+    if (flags[0]) return LBFD_ENOTSUP;  // a cell's step needs more tape than provided
+    if (value) *value = d[LBFD_DIAG_XF] * h->prm.dx;
+    if (grad)
+        for (int k = 0; k < lbfd::NTAN; ++k) grad[k] = gr[k];
+    return LBFD_OK;
+}
+
 int lbfd_flame_position(lbfd_handle* h, double* x_f, double* mass, double* heat_release)
 {
     double d[LBFD_NDIAG];

@@ -118,6 +118,28 @@ cudaError_t launch_objective(const StepParams<Tan>& P, StateView st, const uint8
 cudaError_t launch_objective(const StepParams<Tanf>& P, StateView st, const uint8_t* solid, int objective, double* red,
                              cudaStream_t stream);
 
+// Discrete adjoint of one FP64 step (lbfd_adjoint.cu): scratch of the
+// reverse-mode tape, node k of thread t at k * chunk + t.
+struct AdjointWork {
+    void* rin;   // the input state as tape input (planes * N elements)
+    void* rout;  // the recorded outputs
+    double* a0;
+    double* a1;
+    int16_t* p0;
+    int16_t* p1;
+    double* adj;
+    int maxn;         // nodes per thread
+    long long chunk;  // threads (cells) per launch, a multiple of 64
+    int* flags;       // [0] tape overflow, [1] most nodes a thread used
+};
+size_t adjoint_node_bytes();
+size_t rev_store_bytes();
+// lam (zeroed by the caller) += (dF/dx)^T lam_next, dtheta += (dF/dtheta)^T
+// lam_next for the step F taken from `state` (planes of N doubles)
+cudaError_t launch_adjoint_step(int dim, const StepParams<double>& Pd, int planes, const double* state,
+                                const uint8_t* solid, const double* lam_next, double* lam, double* dtheta,
+                                const AdjointWork& w, cudaStream_t stream);
+
 // Curved walls (lbfd_geometry.cu): host tables of cut links and ghosts.
 struct CurvedTables {
     std::vector<int> link_row;        // [ncell]

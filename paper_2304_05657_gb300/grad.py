@@ -8,6 +8,9 @@ backward only scales it by the incoming gradient.  With four parameters
 this needs one pass and no stored trajectory.  precision "tangent" is FP64
 throughout; "tangent_mixed" runs the forward pass in FP32 (FP64 Arrhenius
 above T_fp64) and accumulates the objective and its gradient in FP64.
+precision "adjoint" computes the same gradient of the flame position in
+reverse mode (the discrete adjoint, FP64, checkpoints every
+`checkpoint_every` steps and recomputation of each segment).
 """
 from __future__ import annotations
 
@@ -38,8 +41,10 @@ def theta_of(cfg: dict):
 
 
 def run_tangent(cfg: dict, solid, T0, Y0, steps: int, objective: int = lbfd.OBJ_FLAME_POSITION, theta=None,
-                precision: str = "tangent"):
+                precision: str = "tangent", checkpoint_every: int = 200):
     """J after `steps` steps from (T0, Y0, g = 0) and dJ/dtheta."""
+    if precision == "adjoint":
+        return run_adjoint(cfg, solid, T0, Y0, steps, objective, theta, checkpoint_every)
     if precision not in ("tangent", "tangent_mixed"):
         raise ValueError(precision)
     c = apply_theta(cfg, theta) if theta is not None else dict(cfg)
@@ -48,6 +53,18 @@ def run_tangent(cfg: dict, solid, T0, Y0, steps: int, objective: int = lbfd.OBJ_
     s.init_fields(T0, Y0)
     s.step(steps)
     J, g = s.gradient(objective)
+    s.close()
+    return J, g
+
+
+def run_adjoint(cfg: dict, solid, T0, Y0, steps: int, objective: int = lbfd.OBJ_FLAME_POSITION, theta=None,
+                checkpoint_every: int = 200):
+    """The same (J, dJ/dtheta) by the discrete adjoint (FP64)."""
+    c = apply_theta(cfg, theta) if theta is not None else dict(cfg)
+    c["precision"] = "fp64"
+    s = lbfd.Solver(c, solid)
+    s.init_fields(T0, Y0)
+    J, g = s.adjoint_gradient(steps, checkpoint_every, objective)
     s.close()
     return J, g
 

@@ -36,6 +36,7 @@ SYMBOLS = (
     "lbfd_last_error", "lbfd_step_graph", "lbfd_num_variants", "lbfd_get_variant", "lbfd_set_variant",
     "lbfd_autotune", "lbfd_diagnostics_noalloc", "lbfd_launches_per_step", "lbfd_read_tangent", "lbfd_gradient",
     "lbfd_diagnostics_rows", "lbfd_set_inlet_velocity", "lbfd_set_curved_walls", "lbfd_read_cells",
+    "lbfd_adjoint_gradient",
 )
 
 
@@ -115,6 +116,7 @@ def load(path: str = LIB_PATH):
     lib.lbfd_set_inlet_velocity.argtypes = [H, ctypes.c_double]
     lib.lbfd_set_curved_walls.argtypes = [H, ctypes.c_int, D]
     lib.lbfd_gradient.argtypes = [H, ctypes.c_int, D, D]
+    lib.lbfd_adjoint_gradient.argtypes = [H, ctypes.c_int, ctypes.c_int, ctypes.c_int, D, D]
     lib.lbfd_autotune.argtypes = [H, ctypes.c_int, D, ctypes.POINTER(ctypes.c_int)]
     lib.lbfd_diagnostics_noalloc.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Mechanism), ctypes.POINTER(Params),
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong,
@@ -239,6 +241,16 @@ class Solver:
         val = np.zeros(1)
         grad = np.zeros(4)
         _check(self.lib, self.lib.lbfd_gradient(self.h, int(objective), _dp(val), _dp(grad)), "lbfd_gradient")
+        return float(val[0]), grad
+
+    def adjoint_gradient(self, steps: int, checkpoint_every: int = 200, objective: int = OBJ_FLAME_POSITION):
+        """Advance `steps` steps and return (J, dJ/dtheta) by the discrete
+        adjoint with checkpoints every `checkpoint_every` steps (FP64)."""
+        val = np.zeros(1)
+        grad = np.zeros(4)
+        st = self.lib.lbfd_adjoint_gradient(self.h, int(steps), int(checkpoint_every), int(objective), _dp(val),
+                                            _dp(grad))
+        _check(self.lib, st, "lbfd_adjoint_gradient")
         return float(val[0]), grad
 
     @property
