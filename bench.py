@@ -345,11 +345,11 @@ def run_ours(args):
     import torch
 
     world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
 
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2304_05657_gb300 import build as libbuild
     from paper_2304_05657_gb300 import lbfd
 

@@ -249,6 +249,27 @@ def test_mixed_variants_match_oracle(lbfd_lib, oracle_mod, name):
         assert np.abs(gg - go).max() <= 1e-4 * scale, (name, v, np.abs(gg - go).max() / scale)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "tangent", "tangent_mixed"])
+def test_read_cells_equals_read_field(lbfd_lib, precision):
+    """lbfd_read_cells returns, per listed cell, g_0..g_{Q-1}, T, Y_k as
+    lbfd_read_field does; invalid indices are rejected without a copy."""
+    cfg, solid, T, Y, g = case_batched()
+    s = lbfd_lib.Solver(dict(cfg, precision=precision), solid)
+    s.set_state(T, Y, g)
+    s.step(3)
+    Tg, Yg, gg = s.get_state()
+    rng = np.random.Generator(np.random.PCG64(5))
+    cells = rng.integers(0, solid.size, size=57)
+    rows = s.read_cells(cells)
+    assert rows.shape == (57, s.Q + 6)
+    assert np.array_equal(rows[:, :s.Q], gg[:, cells].T)
+    assert np.array_equal(rows[:, s.Q], Tg[cells])
+    assert np.array_equal(rows[:, s.Q + 1:], Yg[:, cells].T)
+    assert s.read_cells([]).shape == (0, s.Q + 6)
+    with pytest.raises(lbfd_lib.LbfdError):
+        s.read_cells([0, solid.size])
+
+
 def test_graph_launch_equals_single_launches(lbfd_lib):
     cfg, solid, T, Y, g = case_batched()
     a = lbfd_lib.Solver(cfg, solid)
