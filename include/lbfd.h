@@ -188,7 +188,7 @@ int lbfd_step_graph(lbfd_handle* h, int n);
 /* Kernel variants of the step: 0 is the general form (any cell, D2Q9 and
  * D3Q27).  In 2-D (13 variants), 1..4 are shared-memory tiles of 32x8,
  * 32x4, 64x4 and 32x16 interior cells; 5..8 the same tiles plus a second
- * tile kernel (over the 32x4 tiles that need it) for the cells next to
+ * tile kernel (over the 64x2 tiles that need it) for the cells next to
  * in-domain solid cells (staircase walls, from shared memory); 9..12 as 5..8
  * with two interior cells per thread in packed FP32 arithmetic (tiles of
  * 32x8, 64x8, 32x8, 64x4; the FP64 form runs them one cell per thread).

@@ -71,7 +71,7 @@ struct BoundaryLists {
 };
 
 // tile shape of the 2-D wall-tile kernel
-constexpr int WALL_TX = 32, WALL_TY = 4;
+constexpr int WALL_TX = 64, WALL_TY = 2;
 // the tiles that hold a cell of `all` not in `face` (host, at create)
 void wall_tiles(int nx, int ny, const std::vector<long long>& all, const std::vector<long long>& face,
                 std::vector<int>& out);
