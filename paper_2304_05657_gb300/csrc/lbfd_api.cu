@@ -1,10 +1,11 @@
 // lbfd_api.cu -- host side of the C ABI declared in include/lbfd.h.
 //
 // The handle owns a double-buffered device state (populations and scalar
-// fields in SoA planes), the solid mask, a small reduction scratch and a
-// read-out buffer.  All arithmetic of a step runs in the kernels of
-// lbfd_step.cu; this file validates, converts parameters to lattice units,
-// moves data and launches.
+// fields in SoA planes), the solid mask, the per-cell interior flags and
+// boundary lists, a small reduction scratch and a read-out buffer.  All
+// arithmetic of a step runs in the kernels; this file validates, converts
+// parameters to lattice units, moves data, launches, and drives the
+// checkpointed backward sweep of the discrete adjoint.
 #include <cuda_runtime.h>
 
 #include <algorithm>

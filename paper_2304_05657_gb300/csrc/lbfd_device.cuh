@@ -2,7 +2,8 @@
 // lattice constants, boundary classification, pull streaming with boundary
 // rules, FD line gathering with ghost nodes, FD operators, and the cumulant
 // collision.  Written for sm_103a; templated on the compute type R (double
-// for the FP64 form, float for the mixed form).
+// for the FP64 form, float for the mixed form, F2 for two cells in packed
+// FP32, dual numbers for the tangent forms, Rev for the adjoint).
 //
 // Method: Hosseini & Thevenin, arXiv 2304.05657, Sec. II-III.
 #pragma once

@@ -2,9 +2,11 @@
 //
 // Variant 0 is the general form (one thread per cell, every access through
 // the boundary classification; D2Q9 and D3Q27).  Variants 1.. are 2-D
-// shared-memory tiles of different shapes (lbfd_step_tiled.cuh); the
-// autotuner picks among them by timing.  All variants compute the same
-// step; they differ only in rounding order.
+// shared-memory tiles of different shapes, with or without the wall-tile
+// kernel, one or two cells per thread (lbfd_step_tiled.cuh,
+// lbfd_step_pair.cuh; 3-D: lbfd_step3d.cu); the autotuner picks among them
+// by timing.  All variants compute the same step; they differ only in
+// rounding order.  Also: the host-side classification of boundary cells.
 #include <vector>
 
 #include "lbfd_internal.h"

@@ -3,12 +3,15 @@
 // A block owns a TX x TY tile of cells.  It stages T, Y_k and the derived
 // point values 1/W, X_k and rho of the tile plus a 2-cell halo in shared
 // memory (each derived value is computed once per point instead of once per
-// stencil use).  Cells whose +-2 FD lines and LB neighbours are all fluid
-// cells inside the domain take the fast path: FD stencils from shared
-// memory, populations pulled straight from global memory (coalesced, one
-// plane at a time).  Every other cell (walls, solids, inlet, outlet,
-// periodic wrap) is left to step_kernel_boundary, which runs the general
-// form of lbfd_step_general.cuh over a precomputed list of those cells.
+// stencil use; across periodic faces the halo holds the wrapped cells).
+// Interior cells (+-2 FD lines and the 8 LB neighbours are fluid cells of
+// the domain; a per-cell flag computed at create) take the fast path: FD
+// stencils from shared memory, populations pulled straight from global
+// memory (coalesced, one plane at a time).  The wall-tile kernel updates
+// the cells next to in-domain solid cells over the listed tiles, from the
+// same staging plus the mask; step_kernel_boundary runs the general form
+// of lbfd_step_general.cuh over the list of the remaining cells (near
+// inlet, outlet and wall faces).
 #pragma once
 #include "lbfd_step_general.cuh"
 

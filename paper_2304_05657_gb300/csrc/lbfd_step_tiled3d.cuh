@@ -3,10 +3,11 @@
 // A block of TX x TY threads owns a TX x TY column of cells and marches it
 // through ZC consecutive z-planes.  Shared memory holds a ring of five
 // z-planes (z-2 .. z+2) of the tile plus its 2-cell x/y halo, with T, Y_k
-// and the derived 1/W, X_k, rho of every point; each plane is loaded once
-// per column pass.  Interior cells (every +-2 axis neighbour and all 26 LB
-// neighbours are fluid cells inside the domain) take the fast path; the
-// others are left to step_kernel_boundary over the precomputed cell list.
+// and the derived W, 1/W, rho of every point (X_k = Y_k W / W_k is formed
+// when used); each plane is loaded once per column pass.  Interior cells
+// (every +-2 axis neighbour and all 26 LB neighbours are fluid cells of the
+// domain; a per-cell flag computed at create) are updated here; the others
+// go to step_kernel_boundary over the face and wall lists.
 #pragma once
 #include "lbfd_step_tiled.cuh"
 
