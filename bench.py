@@ -133,6 +133,22 @@ def measured_traffic(workload: str, variant: int, precision: str):
     return float(per_variant[str(variant)]) * float(rec.get("scale_to_workload", 1.0)), rec.get("csrc_sha256")
 
 
+def measured_instructions(workload: str, variant: int, precision: str):
+    """Warp instructions per step (ncu smsp__inst_executed.sum over the
+    kernels of one step) from profiles/traffic.json, under the same rules
+    as measured_traffic."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)[workload]
+    except Exception:
+        return None
+    per_variant = rec.get("warp_instructions_per_step", {})
+    if (rec.get("csrc_sha256") != kernel_source_hash() or rec.get("precision") != precision
+            or str(variant) not in per_variant):
+        return None
+    return float(per_variant[str(variant)]) * float(rec.get("scale_to_workload", 1.0))
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during a region."""
 
@@ -442,6 +458,18 @@ def run_ours(args):
     peak, peak_kind = peaks()
     achieved = alg_bytes / mean_s / 1e9
     traffic, _ = measured_traffic(args.workload, s.variant, precision)
+    # the bound that the counters show: instruction issue.  Peak = one warp
+    # instruction per cycle per SM sub-partition (4 per SM) at the SM clock
+    # sampled during the timed region.
+    insts = measured_instructions(args.workload, s.variant, precision)
+    issue = None
+    if insts is not None:
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
+        peak_ips = sms * 4 * mhz * 1e6
+        issue = {"warp_instructions_per_step": insts, "achieved_warp_inst_per_s": insts / mean_s,
+                 "peak_warp_inst_per_s": peak_ips, "frac": insts / mean_s / peak_ips,
+                 "note": "instructions of every kernel of the step (ncu), over the event-timed step"}
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -457,7 +485,7 @@ def run_ours(args):
                      "traffic_unit": "DRAM bytes per step (ncu, all kernels of one step)",
                      "algorithmic_bytes_per_step": alg_bytes, "algorithmic_bytes_per_cell": bpc,
                      "kernel": "one lbfd_step (the tile kernel with its boundary and wall kernels)",
-                     "mean_launch_ms": mean_s * 1e3},
+                     "mean_launch_ms": mean_s * 1e3, "issue": issue},
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                 "steps": e2e_steps, "api": "lbfd_set_state_raw + lbfd_step + lbfd_get_state_raw (pinned)"},
         "gpu_launches": args.steps * s.launches_per_step,
