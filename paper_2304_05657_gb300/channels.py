@@ -64,22 +64,25 @@ def quenching_width(widths, burning) -> float:
 @dataclass
 class InflowController:
     """Proportional-integral control of the inlet velocity on the flame
-    position: if the flame drifts downstream (x_f above the target) the
-    inflow slows down, and vice versa.  At steady state u_in equals the
-    flame speed."""
+    position, in incremental form: u_k = u_{k-1} + kp (e_k - e_{k-1}) +
+    ki e_k with e = x_target - x_f.  If the flame drifts downstream (x_f
+    above the target) the inflow slows down, and vice versa.  The flame
+    position integrates u_in - S_F, so this PI loop settles with x_f at the
+    target and u_in equal to the flame speed."""
 
     x_target: float          # unburnt length to hold [cells]
-    kp: float = 2e-4         # per cell of error
-    ki: float = 2e-6         # per cell of error and per update
+    kp: float = 1e-3         # per cell of error change
+    ki: float = 2e-5         # per cell of error and per update
     u_min: float = 0.0
     u_max: float = 0.1
-    integral: float = 0.0
+    last_err: float | None = None
 
     def update(self, solver, rows=None) -> float:
         xf = solver.diagnostics(rows=rows)["x_f"]
         err = self.x_target - xf  # > 0: flame too close to the inlet -> more inflow
-        self.integral += err
-        u = solver.cfg["u_in"] + self.kp * err + self.ki * self.integral
+        de = 0.0 if self.last_err is None else err - self.last_err
+        self.last_err = err
+        u = solver.cfg["u_in"] + self.kp * de + self.ki * err
         u = float(min(max(u, self.u_min), self.u_max))
         solver.set_inlet_velocity(u)
         return u
