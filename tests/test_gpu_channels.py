@@ -69,3 +69,30 @@ def test_inflow_controller_holds_the_flame(lbfd_lib):
     us = [h[2] for h in hist[-20:]]
     assert max(us) - min(us) < 5e-5, us
     assert all(0.0 <= h[2] <= 0.1 for h in hist)
+
+
+def test_batched_channels_show_a_quenching_width(lbfd_lib):
+    """The benchmark's 16 channels (widths 16..196, isothermal 300 K walls,
+    mixed precision) after 20 000 steps: the narrow channels quench and the
+    wide ones burn, with one transition (a quenching width, Sec. IV.A), and
+    among the burning channels the flame speed S_F = u_in - dx_f/dt grows
+    with the width (the widest at least twice the narrowest burning one)."""
+    cfg, solid, T, Y, seg = inputs.batched_channels()
+    s = lbfd_lib.Solver(dict(cfg, precision="mixed"), solid)
+    s.init_fields(T, Y)
+    tr = channels.FlameSpeedTracker(segments=seg)
+    for n in range(0, 20001, 1000):
+        if n:
+            s.step_graph(1000)
+        tr.record(s, n)
+    burning = tr.burning()
+    widths = [y1 - y0 for y0, y1 in seg]
+    first = int(np.argmax(burning))
+    assert 3 <= first <= len(widths) - 3, burning  # some quench, some burn
+    assert not burning[:first].any() and burning[first:].all(), burning  # one transition
+    qw = channels.quenching_width(widths, burning)
+    assert qw == widths[first]
+    S_F = tr.flame_speed(window=5)
+    burn = S_F[first:]
+    assert np.all(burn[1:] > 0.0)
+    assert burn[-1] >= 2.0 * burn[0]
