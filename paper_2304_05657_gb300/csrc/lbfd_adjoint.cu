@@ -96,6 +96,7 @@ static StepParams<Rev> rev_params(const StepParams<double>& D)
         P.inv_Wk[k] = Rev(D.inv_Wk[k]);
         P.yield[k] = Rev(D.yield[k]);
         P.a_diff[k] = Rev(D.a_diff[k]);
+        P.a12[k] = Rev(D.a12[k]);
         P.Y_in[k] = Rev(D.Y_in[k]);
     }
     P.fuel = D.fuel;
@@ -110,6 +111,7 @@ static StepParams<Rev> rev_params(const StepParams<double>& D)
     P.omega_b = Rev(D.omega_b);
     P.omega_hi = Rev(D.omega_hi);
     P.alpha = Rev(D.alpha);
+    P.alpha12 = Rev(D.alpha12);
     P.u_in = Rev(D.u_in);
     P.T_in = Rev(D.T_in);
     P.invW_in = Rev(D.invW_in);

@@ -127,6 +127,7 @@ void fill_params(const lbfd_handle* h, StepParams<R>& P)
         P.inv_Wk[k] = (R)(1.0 / M.W[k]);
         P.yield[k] = (R)(M.nu_stoich[k] * M.W[k] / yF);
         P.a_diff[k] = (R)(alpha / M.Le[k] * M.W[k]);
+        P.a12[k] = (R)(alpha / M.Le[k] / 12.0);
         P.Y_in[k] = (R)p.Y_in[k];
     }
     P.fuel = M.fuel;
@@ -142,6 +143,7 @@ void fill_params(const lbfd_handle* h, StepParams<R>& P)
     P.omega_b = (R)(p.omega_bulk > 0.0 ? p.omega_bulk : omega_s);
     P.omega_hi = (R)p.omega_hi;
     P.alpha = (R)alpha;
+    P.alpha12 = (R)(alpha / 12.0);
     P.u_in = (R)p.u_in;
     P.T_in = (R)p.T_in;
     P.invW_in = (R)invW_in;

@@ -163,6 +163,17 @@ __device__ __forceinline__ R fd_d2(const R* v)  // 4th-order central second deri
 {
     return (R(16) * (v[1] + v[3]) - (v[0] + v[4]) - R(30) * v[2]) * R(scalar_t<R>(1) / scalar_t<R>(12));
 }
+// the same stencils times 12 (the tiles fold 1/12 into their coefficients)
+template <typename R>
+__device__ __forceinline__ R fd_D1(const R* v)
+{
+    return v[0] - v[4] + R(8) * (v[3] - v[1]);
+}
+template <typename R>
+__device__ __forceinline__ R fd_D2(const R* v)
+{
+    return R(16) * (v[1] + v[3]) - (v[0] + v[4]) - R(30) * v[2];
+}
 template <typename R>
 __device__ __forceinline__ R fd_c2(const R* v)  // centred 2nd order
 {

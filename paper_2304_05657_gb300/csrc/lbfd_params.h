@@ -16,6 +16,8 @@ struct StepParams {
     R inv_Wk[NSP];   // 1/W_k
     R yield[NSP];    // nu_k W_k / (-nu_F W_F)
     R a_diff[NSP];   // D_k W_k, D_k = alpha / Le_k
+    R a12[NSP];      // a_diff / (12 W_k): the tiles' diffusion on Y_k W with 12x stencils
+    R alpha12;       // alpha / 12
     int fuel, oxid;
     R A_lat;         // A * dt (per step)
     R Ta;            // activation temperature [K]

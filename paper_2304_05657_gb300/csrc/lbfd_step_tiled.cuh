@@ -56,18 +56,19 @@ __device__ __forceinline__ void fd_axis_core(const StepParams<PR>& P, const Tile
     const R drho_r = fdiv(drho, rho0);
     line(sm.T, v);
     acc.conv_T += u_a * weno3_deriv_fast(v, u_a, R(P.epsT));
-    acc.diff_T += R(P.alpha) * (fd_d2(v) + drho_r * fd_d1(v));
+    acc.diff_T += R(P.alpha12) * (fd_D2(v) + drho_r * fd_D1(v));  // 12x stencils, alpha / 12
     line(sm.invW, w);
     const R dinvW = fd_d1(w);
-    // diffusion fluxes from the X_k lines first: their sums M, dM enter
-    // every species' correction term
+    // diffusion fluxes from the staged Y_k W lines first (X_k = Y_k W / W_k;
+    // 1/W_k and 1/12 are folded into a12): their sums M, dM enter every
+    // species' correction term
     R m[NSP], dm[NSP];
     R M = R(0), dM = R(0);
 #pragma unroll
     for (int k = 0; k < NSP; ++k) {
         line(sm.X + k * npt, v);
-        const R dX = fd_d1(v), d2X = fd_d2(v);
-        const R ak = R(P.a_diff[k]);
+        const R dX = fd_D1(v), d2X = fd_D2(v);
+        const R ak = R(P.a12[k]);
         m[k] = ak * invW0 * dX;
         dm[k] = ak * (invW0 * d2X + dinvW * dX);
         M += m[k];
@@ -143,10 +144,10 @@ __device__ __forceinline__ void fd_axis_smem_walls(const StepParams<R>& P, const
         sumL += Lk[k];
         dY[k] = fd_d1(v);
 #pragma unroll
-        for (int j = 0; j < 5; ++j) v[j] = sm.X[k * npt + pts[j]];
-        const R dX = fd_d1(v), d2X = fd_d2(v);
-        m[k] = P.a_diff[k] * invW0 * dX;
-        dm[k] = P.a_diff[k] * (invW0 * d2X + dinvW * dX);
+        for (int j = 0; j < 5; ++j) v[j] = sm.X[k * npt + pts[j]];  // Y_k W
+        const R dX = fd_D1(v), d2X = fd_D2(v);
+        m[k] = P.a12[k] * invW0 * dX;
+        dm[k] = P.a12[k] * (invW0 * d2X + dinvW * dX);
         M += m[k];
         dM += dm[k];
     }
@@ -272,7 +273,7 @@ __device__ __forceinline__ void stage_tile2d(const StepParams<R>& P, const TileS
 #pragma unroll
         for (int k = 0; k < NSP; ++k) {
             sm.Y[k * NPT + pt] = Y[it][k];
-            sm.X[k * NPT + pt] = Y[it][k] * P.inv_Wk[k] * W;
+            sm.X[k * NPT + pt] = Y[it][k] * W;  // X_k W_k (1/W_k folded into a12)
         }
         sm.invW[pt] = invW;
         sm.rho[pt] = fdiv(P.T_in * P.invW_in * W, T[it]);

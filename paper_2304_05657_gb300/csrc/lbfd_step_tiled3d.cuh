@@ -43,7 +43,7 @@ __device__ __forceinline__ R fd_axis_pts(const StepParams<R>& P, const TileSmem<
 #pragma unroll
     for (int j = 0; j < 5; ++j) v[j] = sm.T[pts[j]];
     acc.conv_T += u_a * weno3_deriv_fast(v, u_a, P.epsT);
-    acc.diff_T += P.alpha * (fd_d2(v) + drho_r * fd_d1(v));
+    acc.diff_T += P.alpha12 * (fd_D2(v) + drho_r * fd_D1(v));  // 12x stencils, alpha / 12
 #pragma unroll
     for (int j = 0; j < 5; ++j) w[j] = sm.invW[pts[j]];
     const R dinvW = fd_d1(w);
@@ -55,10 +55,10 @@ __device__ __forceinline__ R fd_axis_pts(const StepParams<R>& P, const TileSmem<
 #pragma unroll
     for (int k = 0; k < NSP; ++k) {
 #pragma unroll
-        for (int j = 0; j < 5; ++j) v[j] = sm.Y[k * npt + pts[j]] * P.inv_Wk[k] * Wl[j];  // X_k = Y_k W / W_k
-        const R dX = fd_d1(v), d2X = fd_d2(v);
-        m[k] = P.a_diff[k] * invW0 * dX;
-        dm[k] = P.a_diff[k] * (invW0 * d2X + dinvW * dX);
+        for (int j = 0; j < 5; ++j) v[j] = sm.Y[k * npt + pts[j]] * Wl[j];  // X_k W_k (1/W_k and 1/12 in a12)
+        const R dX = fd_D1(v), d2X = fd_D2(v);
+        m[k] = P.a12[k] * invW0 * dX;
+        dm[k] = P.a12[k] * (invW0 * d2X + dinvW * dX);
         M += m[k];
         dM += dm[k];
     }
