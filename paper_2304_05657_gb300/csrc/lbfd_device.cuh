@@ -360,6 +360,62 @@ __device__ __forceinline__ void from_cumulants(R* m)
 
 __host__ __device__ constexpr int moment_order(int j) { return j % 3 + (j / 3) % 3 + j / 9; }
 
+// Cumulants of orders >= 2 of g^eq / (rho cs^2) (Eq. 10, 12, 21, 22) in
+// closed form.  On the product-weight lattices (D2Q9, D3Q27) the central
+// moments of the discrete second-order equilibrium are polynomials in
+// e = P_h / (rho cs^2) - 1 and the velocity; taking them through Eq. 22
+// gives the expressions below (a, b, c = u_x^2, u_y^2, u_z^2), the same
+// numbers as transforming the Q values, up to rounding.  Orders 0 and 1 are
+// not relaxed and are left unset.
+template <int DIM, typename R>
+__device__ __forceinline__ void eq_cumulants(R* fe, R e, const R* u)
+{
+    using Sc = scalar_t<R>;
+    const R third = R(Sc(1) / Sc(3)), ninth = R(Sc(1) / Sc(9));
+    const R ux = u[0], uy = u[1];
+    const R a = ux * ux, b = uy * uy;
+    const R Ph = e + R(1), Ph3 = Ph * third, e3 = e * third, E2 = e * e;
+    const R s1 = R(3) + e - R(3) * E2, s2 = E2 * third, s3 = (E2 + e) * ninth;
+    // second order: kappa_aa = e u_a^2 + Ph/3, kappa_ab = e u_a u_b
+    // third: kappa_aab = -u_b (Ph u_a^2 + e/3); fourth: c_aabb = u_a^2 u_b^2 s1 - s2 (u_a^2 + u_b^2) - s3
+    fe[LBFD_M(2, 0, 0)] = e * a + Ph3;
+    fe[LBFD_M(0, 2, 0)] = e * b + Ph3;
+    fe[LBFD_M(1, 1, 0)] = e * ux * uy;
+    fe[LBFD_M(2, 1, 0)] = -(uy * (Ph * a + e3));
+    fe[LBFD_M(1, 2, 0)] = -(ux * (Ph * b + e3));
+    fe[LBFD_M(2, 2, 0)] = a * b * s1 - s2 * (a + b) - s3;
+    if constexpr (DIM == 3) {
+        const R uz = u[2];
+        const R c = uz * uz;
+        fe[LBFD_M(0, 0, 2)] = e * c + Ph3;
+        fe[LBFD_M(1, 0, 1)] = e * ux * uz;
+        fe[LBFD_M(0, 1, 1)] = e * uy * uz;
+        fe[LBFD_M(2, 0, 1)] = -(uz * (Ph * a + e3));
+        fe[LBFD_M(0, 2, 1)] = -(uz * (Ph * b + e3));
+        fe[LBFD_M(1, 0, 2)] = -(ux * (Ph * c + e3));
+        fe[LBFD_M(0, 1, 2)] = -(uy * (Ph * c + e3));
+        fe[LBFD_M(1, 1, 1)] = -(Ph * ux * uy * uz);
+        fe[LBFD_M(2, 0, 2)] = a * c * s1 - s2 * (a + c) - s3;
+        fe[LBFD_M(0, 2, 2)] = b * c * s1 - s2 * (b + c) - s3;
+        // fourth, c_aabc = u_b u_c (u_a^2 s1 - s2)
+        fe[LBFD_M(2, 1, 1)] = uy * uz * (a * s1 - s2);
+        fe[LBFD_M(1, 2, 1)] = ux * uz * (b * s1 - s2);
+        fe[LBFD_M(1, 1, 2)] = ux * uy * (c * s1 - s2);
+        // fifth, c_abbcc = u_a (u_b^2 u_c^2 t1 + (u_b^2 + u_c^2) t2 + t3)
+        const R t1 = R(-6) + R(9) * e + R(10) * E2;
+        const R t2 = (e + R(4) * E2) * third, t3 = (e + R(2) * E2) * ninth;
+        fe[LBFD_M(1, 2, 2)] = ux * (b * c * t1 + (b + c) * t2 + t3);
+        fe[LBFD_M(2, 1, 2)] = uy * (a * c * t1 + (a + c) * t2 + t3);
+        fe[LBFD_M(2, 2, 1)] = uz * (a * b * t1 + (a + b) * t2 + t3);
+        // sixth, in the elementary symmetric polynomials of a, b, c
+        const R E3 = E2 * e;
+        const R sg1 = a + b + c, sg2 = a * b + a * c + b * c, sg3 = a * b * c;
+        fe[LBFD_M(2, 2, 2)] = sg3 * (R(30) * E3 - R(25) * E2 - R(64) * e)
+            + sg2 * (R(2) * E3 - (R(5) * E2 + R(7) * e) * third) + sg1 * (R(2) * E3 - E2) * ninth
+            + (R(2) * E3 * third + E2 + e * third) * ninth;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Collision of one cell (Eq. 9, 10, 12-15, 19, 21-24): g (post-streaming)
 // is replaced by g*.  Relaxation toward the cumulants of g^eq/(rho cs^2);
@@ -394,14 +450,12 @@ __device__ __forceinline__ void collide(const StepParams<PR>& P, R* g, R rho, co
         // f^eq / rho, Eq. 10
         const R feq_r = wi * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);
         xi[i] = cs2 * (feq_r - wi) * cg + wi * rcs2 * Lam;  // Eq. 9
-        // g^eq / (rho cs2) = w (P_h/(rho cs2) - 1) + f^eq/rho, Eq. 12
-        fe[i] = wi * (P_h * inv_rcs2 - R(1)) + feq_r;
         g[i] = (g[i] + R(0.5) * xi[i]) * inv_rcs2;  // Eq. 19
     }
     central_forward<DIM>(g, u);
-    central_forward<DIM>(fe, u);
     to_cumulants<DIM>(g);
-    to_cumulants<DIM>(fe);
+    // the target: cumulants of g^eq / (rho cs2) = w (P_h/(rho cs2) - 1) + f^eq/rho (Eq. 12)
+    eq_cumulants<DIM>(fe, P_h * inv_rcs2 - R(1), u);
     // relaxation
     const R ws = R(P.omega_s), wb = R(P.omega_b), wh = R(P.omega_hi);
 #pragma unroll
