@@ -112,6 +112,7 @@ static StepParams<Rev> rev_params(const StepParams<double>& D)
     P.omega_hi = Rev(D.omega_hi);
     P.alpha = Rev(D.alpha);
     P.alpha12 = Rev(D.alpha12);
+    P.lam_yield = Rev(D.lam_yield);
     P.u_in = Rev(D.u_in);
     P.T_in = Rev(D.T_in);
     P.invW_in = Rev(D.invW_in);

@@ -144,6 +144,11 @@ void fill_params(const lbfd_handle* h, StepParams<R>& P)
     P.omega_hi = (R)p.omega_hi;
     P.alpha = (R)alpha;
     P.alpha12 = (R)(alpha / 12.0);
+    {
+        double ly = 0.0;
+        for (int k = 0; k < lbfd::NSP; ++k) ly += M.nu_stoich[k] / yF;  // yield_k / W_k
+        P.lam_yield = (R)ly;
+    }
     P.u_in = (R)p.u_in;
     P.T_in = (R)p.T_in;
     P.invW_in = (R)invW_in;

@@ -18,6 +18,7 @@ struct StepParams {
     R a_diff[NSP];   // D_k W_k, D_k = alpha / Le_k
     R a12[NSP];      // a_diff / (12 W_k): the tiles' diffusion on Y_k W with 12x stencils
     R alpha12;       // alpha / 12
+    R lam_yield;     // sum_k yield_k / W_k (the reaction's share of Lambda's species sum)
     int fuel, oxid;
     R A_lat;         // A * dt (per step)
     R Ta;            // activation temperature [K]

@@ -92,10 +92,11 @@ static cudaError_t launch_tiled(const StepParams<R>& P, StateView in, StateView 
     }
     if constexpr (pair) {
         auto pk = step_kernel_pair2d<TX / 2, TY, MINB>;
-        if (smem > 48 * 1024 &&
-            (e = cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        constexpr size_t psmem = pair_smem_bytes<TX, TY>();
+        if (psmem > 48 * 1024 &&
+            (e = cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem)) != cudaSuccess)
             return e;
-        pk<<<grid, block, smem, stream>>>(P, (const float*)in.g, (float*)out.g, (const float*)in.T, (float*)out.T,
+        pk<<<grid, block, psmem, stream>>>(P, (const float*)in.g, (float*)out.g, (const float*)in.T, (float*)out.T,
                                           (const float*)in.Y, (float*)out.Y, b.interior);
     } else {
         kern<<<grid, block, smem, stream>>>(P, (const S*)in.g, (S*)out.g, (const S*)in.T, (S*)out.T,

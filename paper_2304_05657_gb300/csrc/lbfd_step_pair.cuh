@@ -36,6 +36,29 @@ __device__ __forceinline__ void pair_line(const float* f, int p0, F2* v)
 
 __device__ __forceinline__ F2 pair_at(const float* f, int p0) { return F2(*reinterpret_cast<const float2*>(f + p0)); }
 
+// asynchronous global -> shared copy of B bytes (cp.async; both addresses
+// aligned to B), completed by cp_async_wait_all in the issuing thread
+template <int B>
+__device__ __forceinline__ void cp_async(void* dst, const void* src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(src), "n"(B) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// shared memory of the pair kernel: the staged tile, then (16-byte aligned)
+// the pulled populations of its cells, [i][2 * thread + lane]
+template <int TX, int TY>
+__host__ __device__ constexpr size_t pair_pull_offset()
+{
+    return (tile_smem_bytes<float, TX, TY>() + 15) / 16 * 16;
+}
+template <int TX, int TY>
+__host__ __device__ constexpr size_t pair_smem_bytes()
+{
+    return pair_pull_offset<TX, TY>() + sizeof(float) * 9 * TX * TY;
+}
+
 // store the lanes that are set (predicated stores, no branch)
 __device__ __forceinline__ void pair_store(float* p, const F2& v, bool ok0, bool ok1)
 {
@@ -71,10 +94,14 @@ __global__ void __launch_bounds__(TXP * TY, MINB)
     const long long c = (long long)x + (long long)P.nx * y;
     const long long N = P.N;
 
-    // a1: pull from the neighbours (Eq. 8), issued before the staging so
-    // that the loads are in flight meanwhile; a missing lane 1 re-reads
-    // lane 0.  The offsets wrap inside the domain for any in-range cell.
-    F2 g[9];
+    // a1: pull from the neighbours (Eq. 8) straight into shared memory
+    // (cp.async), issued before the staging so that the copies are in flight
+    // meanwhile and hold no registers through the FD part; a missing lane 1
+    // re-reads lane 0.  The offsets wrap inside the domain for any in-range
+    // cell.
+    constexpr int NT = TXP * TY;
+    const int tid = threadIdx.x + TXP * threadIdx.y;
+    float* gs = reinterpret_cast<float*>(smem_raw + pair_pull_offset<TX, TY>()) + 2 * tid;
     bool ok0 = false, ok1 = false;  // the two cells are interior (per-cell class)
     if (inside) {
         ok0 = interior[c] != 0;
@@ -91,18 +118,24 @@ __global__ void __launch_bounds__(TXP * TY, MINB)
             const int o0 = (cx_of(i) > 0 ? oxm0 : (cx_of(i) < 0 ? oxp0 : 0)) + oy;
             const int o1 = (cx_of(i) > 0 ? oxm1 : (cx_of(i) < 0 ? oxp1 : 0)) + oy;
             const float* a0 = gc0 + (long long)i * N + o0;
-            if (cx_of(i) == 0 && has1 && (reinterpret_cast<uintptr_t>(a0) & 7) == 0)
-                g[i] = F2(__ldg(reinterpret_cast<const float2*>(a0)));
-            else
-                g[i] = F2(__ldg(a0), __ldg(gc1 + (long long)i * N + o1));
+            float* d = gs + i * 2 * NT;
+            if (cx_of(i) == 0 && has1 && (reinterpret_cast<uintptr_t>(a0) & 7) == 0) {
+                cp_async<8>(d, a0);
+            } else {
+                cp_async<4>(d, a0);
+                cp_async<4>(d + 1, gc1 + (long long)i * N + o1);
+            }
         }
     }
-    stage_tile2d<float, float, TX, TY, false, TXP * TY>(P, sm, x0, y0, threadIdx.x + TXP * threadIdx.y, T_in, Y_in,
-                                                        nullptr);
+    stage_tile2d<float, float, TX, TY, false, NT>(P, sm, x0, y0, tid, T_in, Y_in, nullptr);
+    cp_async_wait_all();
     __syncthreads();
 
     if (!inside || (!ok0 && !ok1)) return;
     const int p0 = (threadIdx.y + 2) * SX + 2 * threadIdx.x + 2;
+    F2 g[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) g[i] = F2(*reinterpret_cast<const float2*>(gs + i * 2 * NT));
 
     // a2
     const F2 T0 = pair_at(sm.T, p0), invW0 = pair_at(sm.invW, p0), rho0 = pair_at(sm.rho, p0);
@@ -117,11 +150,8 @@ __global__ void __launch_bounds__(TXP * TY, MINB)
         u[2] = F2(0.f);
     }
     // a3-a5
-    FDAccum<F2> acc;
-    acc.conv_T = acc.diff_T = F2(0.f);
-#pragma unroll
-    for (int k = 0; k < NSP; ++k) acc.conv_Y[k] = acc.diff_Y[k] = F2(0.f);
-    acc.grad_rho[2] = F2(0.f);
+    TileAccum<F2> acc;
+    acc.clear();
     {
         auto line_x = [&](const float* f, F2* v) { pair_line<true, SX>(f, p0, v); };
         auto line_y = [&](const float* f, F2* v) { pair_line<false, SX>(f, p0, v); };
@@ -135,15 +165,16 @@ __global__ void __launch_bounds__(TXP * TY, MINB)
     // a7
     const F2 DT = acc.diff_T + reac_T;
     pair_store(T_out + c, T0 + (DT - acc.conv_T), ok0, ok1);
-    F2 lam_Y = F2(0.f);
 #pragma unroll
-    for (int k = 0; k < NSP; ++k) {
-        const F2 DY = acc.diff_Y[k] + F2(P.yield[k]) * q;
-        pair_store(Y_out + (long long)k * N + c, Y0[k] + (DY - acc.conv_Y[k]), ok0, ok1);
-        lam_Y += F2(P.inv_Wk[k]) * DY;
-    }
+    for (int k = 0; k < NSP; ++k)
+        pair_store(Y_out + (long long)k * N + c, Y0[k] + (acc.rhs_Y[k] + F2(P.yield[k]) * q), ok0, ok1);
+    const F2 lam_Y = acc.lamY + F2(P.lam_yield) * q;
     const F2 Lam = fdiv(DT, T0) + fdiv(lam_Y, invW0);
-    // a8-a10
+    // a8-a10, on the populations read again from shared memory (the compiler
+    // barrier keeps them out of registers during the FD part)
+    asm volatile("" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 9; ++i) g[i] = F2(*reinterpret_cast<const float2*>(gs + i * 2 * NT));
     collide<2, F2>(P, g, rho0, u, acc.grad_rho, Lam);
 #pragma unroll
     for (int i = 0; i < 9; ++i) pair_store(g_out + (long long)i * N + c, g[i], ok0, ok1);

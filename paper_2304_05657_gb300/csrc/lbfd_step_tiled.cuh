@@ -41,13 +41,33 @@ __host__ __device__ constexpr size_t tile_smem_bytes()
     return sizeof(R) * (size_t)TileGeom<TX, TY>::NPT * (3 + 2 * NSP) + (size_t)TileGeom<TX, TY>::NPT;
 }
 
+// FD sums of the tile kernels: T's convective and non-convective parts,
+// and for the species the net rate rhs_Y = sum over axes of (diffusion -
+// convection) plus lamY = sum_k (diffusion of Y_k) / W_k, the FD part of
+// Lambda's species sum (Eq. 6), which is all that Lambda needs of them
+template <typename R>
+struct TileAccum {
+    R conv_T, diff_T;
+    R rhs_Y[NSP];
+    R lamY;
+    R grad_rho[3];
+    __device__ __forceinline__ void clear()
+    {
+        conv_T = diff_T = lamY = R(0);
+#pragma unroll
+        for (int k = 0; k < NSP; ++k) rhs_Y[k] = R(0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) grad_rho[a] = R(0);
+    }
+};
+
 // FD terms along one axis of an interior cell (Eq. 25-27): `line(f, v)`
 // gathers the five points of the staged field f along the axis into v.
 // R is the compute type (float, double, or F2 for a pair of cells), PR the
 // parameters' type.
 template <typename R, typename PR, typename SR, typename Line>
 __device__ __forceinline__ void fd_axis_core(const StepParams<PR>& P, const TileSmem<SR>& sm, int npt, Line line,
-                                             int a, R u_a, const R* Y0, R invW0, R rho0, FDAccum<R>& acc)
+                                             int a, R u_a, const R* Y0, R invW0, R rho0, TileAccum<R>& acc)
 {
     R v[5], w[5];
     line(sm.rho, v);
@@ -83,19 +103,20 @@ __device__ __forceinline__ void fd_axis_core(const StepParams<PR>& P, const Tile
         const R Lk = weno3_deriv_fast(v, u_a, R(P.epsY));
         sumL += Lk;
         const R dY = fd_d1(v);
-        acc.conv_Y[k] += u_a * Lk;
-        acc.diff_Y[k] += dm[k] - dY * M - Y0[k] * dM + (m[k] - Y0[k] * M) * drho_r;
+        const R dk = dm[k] - dY * M - Y0[k] * dM + (m[k] - Y0[k] * M) * drho_r;
+        acc.rhs_Y[k] += dk - u_a * Lk;
+        acc.lamY += R(P.inv_Wk[k]) * dk;
     }
     const R us = u_a * sumL;
 #pragma unroll
-    for (int k = 0; k < NSP; ++k) acc.conv_Y[k] -= Y0[k] * us;
+    for (int k = 0; k < NSP; ++k) acc.rhs_Y[k] += Y0[k] * us;
 }
 
 // fast-path FD terms along one axis from shared memory; `st` is the point
 // stride of the axis (1 for x, SX for y) and p0 the centre point
 template <typename R>
 __device__ __forceinline__ void fd_axis_smem(const StepParams<R>& P, const TileSmem<R>& sm, int npt, int p0, int st,
-                                             int a, R u_a, R T0, const R* Y0, R invW0, R rho0, FDAccum<R>& acc)
+                                             int a, R u_a, R T0, const R* Y0, R invW0, R rho0, TileAccum<R>& acc)
 {
     auto line = [&](const R* f, R* v) {
 #pragma unroll
@@ -111,7 +132,7 @@ __device__ __forceinline__ void fd_axis_smem(const StepParams<R>& P, const TileS
 template <typename R>
 __device__ __forceinline__ void fd_axis_smem_walls(const StepParams<R>& P, const TileSmem<R>& sm, int npt,
                                                    const int* pts, int ghost, int a, R u_a, const R* Y0, R invW0,
-                                                   R rho0, FDAccum<R>& acc)
+                                                   R rho0, TileAccum<R>& acc)
 {
     const bool iso = P.solid_isothermal;
     const R TB = P.T_solid;
@@ -153,8 +174,9 @@ __device__ __forceinline__ void fd_axis_smem_walls(const StepParams<R>& P, const
     }
 #pragma unroll
     for (int k = 0; k < NSP; ++k) {
-        acc.conv_Y[k] += u_a * (Lk[k] - Y0[k] * sumL);
-        acc.diff_Y[k] += dm[k] - dY[k] * M - Y0[k] * dM + (m[k] - Y0[k] * M) * drho_r;
+        const R dk = dm[k] - dY[k] * M - Y0[k] * dM + (m[k] - Y0[k] * M) * drho_r;
+        acc.rhs_Y[k] += dk - u_a * (Lk[k] - Y0[k] * sumL);
+        acc.lamY += P.inv_Wk[k] * dk;
     }
 }
 
@@ -387,11 +409,8 @@ __device__ __forceinline__ void tiled2d_body(const StepParams<R>& P, const S* __
         u[2] = R(0);
     }
     // a3-a5
-    FDAccum<R> acc;
-    acc.conv_T = acc.diff_T = R(0);
-#pragma unroll
-    for (int k = 0; k < NSP; ++k) acc.conv_Y[k] = acc.diff_Y[k] = R(0);
-    acc.grad_rho[2] = R(0);
+    TileAccum<R> acc;
+    acc.clear();
     if constexpr (WALLS) {
         int pts[5];
         int gh = wall_line(sm.mask, p0, 1, pts);
@@ -408,13 +427,9 @@ __device__ __forceinline__ void tiled2d_body(const StepParams<R>& P, const S* __
     // a7
     const R DT = acc.diff_T + reac_T;
     T_out[c] = S(T0 + (DT - acc.conv_T));
-    R lam_Y = R(0);
 #pragma unroll
-    for (int k = 0; k < NSP; ++k) {
-        const R DY = acc.diff_Y[k] + P.yield[k] * q;
-        Y_out[(long long)k * N + c] = S(Y0[k] + (DY - acc.conv_Y[k]));
-        lam_Y += P.inv_Wk[k] * DY;
-    }
+    for (int k = 0; k < NSP; ++k) Y_out[(long long)k * N + c] = S(Y0[k] + (acc.rhs_Y[k] + P.yield[k] * q));
+    const R lam_Y = acc.lamY + P.lam_yield * q;
     const R Lam = fdiv(DT, T0) + fdiv(lam_Y, invW0);
     // a8-a10
     collide<2, R>(P, g, rho0, u, acc.grad_rho, Lam);

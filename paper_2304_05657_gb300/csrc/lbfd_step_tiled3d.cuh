@@ -33,7 +33,7 @@ __host__ __device__ constexpr size_t tile3_smem_bytes()
 // X_k lines first, as in fd_axis_core); returns d rho / d x_a
 template <typename R>
 __device__ __forceinline__ R fd_axis_pts(const StepParams<R>& P, const TileSmem<R>& sm, int npt, const int* pts,
-                                         R u_a, const R* Y0, R invW0, R rho0, FDAccum<R>& acc)
+                                         R u_a, const R* Y0, R invW0, R rho0, TileAccum<R>& acc)
 {
     R v[5], w[5];
 #pragma unroll
@@ -70,12 +70,13 @@ __device__ __forceinline__ R fd_axis_pts(const StepParams<R>& P, const TileSmem<
         const R Lk = weno3_deriv_fast(v, u_a, P.epsY);
         sumL += Lk;
         const R dY = fd_d1(v);
-        acc.conv_Y[k] += u_a * Lk;
-        acc.diff_Y[k] += dm[k] - dY * M - Y0[k] * dM + (m[k] - Y0[k] * M) * drho_r;
+        const R dk = dm[k] - dY * M - Y0[k] * dM + (m[k] - Y0[k] * M) * drho_r;
+        acc.rhs_Y[k] += dk - u_a * Lk;
+        acc.lamY += P.inv_Wk[k] * dk;
     }
     const R us = u_a * sumL;
 #pragma unroll
-    for (int k = 0; k < NSP; ++k) acc.conv_Y[k] -= Y0[k] * us;
+    for (int k = 0; k < NSP; ++k) acc.rhs_Y[k] += Y0[k] * us;
     return drho;
 }
 
@@ -204,11 +205,8 @@ __device__ __forceinline__ void tiled3d_body(const StepParams<R>& P, const S* __
                     u[a] = m * inv;
                 }
             }
-            FDAccum<R> acc;
-            acc.conv_T = acc.diff_T = R(0);
-#pragma unroll
-            for (int k = 0; k < NSP; ++k) acc.conv_Y[k] = acc.diff_Y[k] = R(0);
-            acc.grad_rho[0] = acc.grad_rho[1] = acc.grad_rho[2] = R(0);
+            TileAccum<R> acc;
+            acc.clear();
             // the three axes share one copy of the FD code (a rolled loop keeps
             // the kernel small enough for the instruction cache)
 #pragma unroll 1
@@ -226,13 +224,9 @@ __device__ __forceinline__ void tiled3d_body(const StepParams<R>& P, const S* __
             const R q = arrhenius(P, T0, pick_species(Y0, P.fuel), pick_species(Y0, P.oxid));
             const R DT = acc.diff_T + P.Q_cp * q;
             T_out[c] = S(T0 + (DT - acc.conv_T));
-            R lam_Y = R(0);
 #pragma unroll
-            for (int k = 0; k < NSP; ++k) {
-                const R DY = acc.diff_Y[k] + P.yield[k] * q;
-                Y_out[(long long)k * N + c] = S(Y0[k] + (DY - acc.conv_Y[k]));
-                lam_Y += P.inv_Wk[k] * DY;
-            }
+            for (int k = 0; k < NSP; ++k) Y_out[(long long)k * N + c] = S(Y0[k] + (acc.rhs_Y[k] + P.yield[k] * q));
+            const R lam_Y = acc.lamY + P.lam_yield * q;
             const R Lam = fdiv(DT, T0) + fdiv(lam_Y, invW0);
             if constexpr (SPLIT) {
                 aux[c] = Lam;
