@@ -191,7 +191,8 @@ int lbfd_step_graph(lbfd_handle* h, int n);
  * tile kernel (over the 64x2 tiles that need it) for the cells next to
  * in-domain solid cells (staircase walls, from shared memory); 9..12 as 5..8
  * with two interior cells per thread in packed FP32 arithmetic (tiles of
- * 32x8, 64x8, 32x8, 64x4; the FP64 form runs them one cell per thread).
+ * 32x8, 64x8, 32x8, 64x4 at 4, 2, 5 and 5 blocks per SM; the FP64 form runs
+ * them one cell per thread).
  * In 3-D (6 variants), 1..2 are 32x4 columns marching through 16 or 32
  * z-planes with a five-plane shared-memory ring, 3 is 1 with the registers
  * capped for four blocks per SM, and 4..5 are 1..2 split into an FD tile

@@ -128,7 +128,8 @@ static cudaError_t launch_2d(int variant, const StepParams<R>& P, StateView in, 
     case 7: return launch_tiled<S, R, 64, 4, true>(P, in, out, solid, b, side, stream);
     case 8: return launch_tiled<S, R, 32, 16, true>(P, in, out, solid, b, side, stream);
     // variants 9-12: as 5-8 with two cells per thread in packed FP32, at
-    // 128 registers (9, 10) or 96 (11, 12, five 128-thread blocks per SM)
+    // 128 registers (9, 10) or 96 (11, 12, five 128-thread blocks per SM;
+    // six blocks at 80 registers spill and are slower)
     case 9: return launch_tiled<S, R, 32, 8, true, true, 4>(P, in, out, solid, b, side, stream);
     case 10: return launch_tiled<S, R, 64, 8, true, true, 2>(P, in, out, solid, b, side, stream);
     case 11: return launch_tiled<S, R, 32, 8, true, true, 5>(P, in, out, solid, b, side, stream);

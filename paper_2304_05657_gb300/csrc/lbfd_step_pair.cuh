@@ -156,8 +156,16 @@ __global__ void __launch_bounds__(TXP * TY, MINB)
         auto line_x = [&](const float* f, F2* v) { pair_line<true, SX>(f, p0, v); };
         auto line_y = [&](const float* f, F2* v) { pair_line<false, SX>(f, p0, v); };
         fd_axis_core<F2>(P, sm, NPT, line_x, 0, u[0], Y0, invW0, rho0, acc);
+        // the point values are read again from shared memory for each use
+        // (the compiler barrier keeps them out of registers in between)
+        asm volatile("" ::: "memory");
+#pragma unroll
+        for (int k = 0; k < NSP; ++k) Y0[k] = pair_at(sm.Y + k * NPT, p0);
         fd_axis_core<F2>(P, sm, NPT, line_y, 1, u[1], Y0, invW0, rho0, acc);
     }
+    asm volatile("" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) Y0[k] = pair_at(sm.Y + k * NPT, p0);
     // a6: per lane (the mixed form switches to FP64 above T_fp64)
     const F2 yf = pick_species(Y0, P.fuel), yo = pick_species(Y0, P.oxid);
     const F2 q(arrhenius(P, T0.v.x, yf.v.x, yo.v.x), arrhenius(P, T0.v.y, yf.v.y, yo.v.y));
