@@ -59,11 +59,80 @@ __host__ __device__ constexpr size_t pair_smem_bytes()
     return pair_pull_offset<TX, TY>() + sizeof(float) * 9 * TX * TY;
 }
 
-// store the lanes that are set (predicated stores, no branch)
-__device__ __forceinline__ void pair_store(float* p, const F2& v, bool ok0, bool ok1)
+// store the lanes that are set: one 8-byte store when both are and p is
+// 8-byte aligned (vec), else per lane
+__device__ __forceinline__ void pair_store(float* p, const F2& v, bool ok0, bool ok1, bool vec)
 {
-    if (ok0) p[0] = v.v.x;
-    if (ok1) p[1] = v.v.y;
+    if (vec) {
+        *reinterpret_cast<float2*>(p) = v.v;
+    } else {
+        if (ok0) p[0] = v.v.x;
+        if (ok1) p[1] = v.v.y;
+    }
+}
+
+// Staging of the pair kernel's tile, two x-neighbouring points per thread
+// in packed FP32 (the same values as stage_tile2d): with nx even, the two
+// points of a pair (staged x even) are both inside the domain or both
+// outside it, wrap together across a periodic x face and sit at an even
+// cell index, so that each field moves as one 8-byte load and one 8-byte
+// shared store.  Odd nx takes stage_tile2d.
+template <int TX, int TY, int NTHR>
+__device__ __forceinline__ void stage_tile2d_pairs(const StepParams<float>& P, const TileSmem<float>& sm, int x0,
+                                                   int y0, int tid, const float* __restrict__ T_in,
+                                                   const float* __restrict__ Y_in)
+{
+    using G = TileGeom<TX, TY>;
+    constexpr int SX = G::SX, NPT = G::NPT, NPP = NPT / 2;
+    constexpr int NIT = (NPP + NTHR - 1) / NTHR;
+    const long long N = P.N;
+    long long cell[NIT];  // -1: outside the domain
+    F2 T[NIT], Y[NIT][NSP];
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) {
+        const int pp = tid + it * NTHR;
+        cell[it] = -1;
+        if (pp >= NPP) continue;
+        const int pt = 2 * pp;
+        const int sx = pt % SX, sy = pt / SX;
+        int gx = x0 + sx - 2, gy = y0 + sy - 2;
+        if (P.bc[0] == BC_PERIODIC) {
+            if (gx < 0) gx += P.nx;
+            if (gx < 0) gx += P.nx;
+            if (gx >= P.nx) gx -= P.nx;
+            if (gx >= P.nx) gx -= P.nx;
+        }
+        if (P.bc[2] == BC_PERIODIC) {
+            if (gy < 0) gy += P.ny;
+            if (gy < 0) gy += P.ny;
+            if (gy >= P.ny) gy -= P.ny;
+            if (gy >= P.ny) gy -= P.ny;
+        }
+        if (gx < 0 || gx >= P.nx || gy < 0 || gy >= P.ny) continue;
+        const long long c = (long long)gx + (long long)P.nx * gy;
+        cell[it] = c;
+        T[it] = F2(*reinterpret_cast<const float2*>(T_in + c));
+#pragma unroll
+        for (int k = 0; k < NSP; ++k) Y[it][k] = F2(*reinterpret_cast<const float2*>(Y_in + (long long)k * N + c));
+    }
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) {
+        if (cell[it] < 0) continue;
+        const int pt = 2 * (tid + it * NTHR);
+        F2 invW = F2(0.f);
+#pragma unroll
+        for (int k = 0; k < NSP; ++k) invW += Y[it][k] * F2(P.inv_Wk[k]);
+        const F2 W = fdiv(F2(1.f), invW);
+        auto put = [&](float* f, const F2& v) { *reinterpret_cast<float2*>(f + pt) = v.v; };
+        put(sm.T, T[it]);
+#pragma unroll
+        for (int k = 0; k < NSP; ++k) {
+            put(sm.Y + k * NPT, Y[it][k]);
+            put(sm.X + k * NPT, Y[it][k] * W);  // X_k W_k (1/W_k folded into a12)
+        }
+        put(sm.invW, invW);
+        put(sm.rho, fdiv(F2(P.T_in * P.invW_in) * W, T[it]));
+    }
 }
 
 // TXP x TY threads, a tile of 2 TXP x TY cells, at least MINB blocks per
@@ -127,7 +196,10 @@ __global__ void __launch_bounds__(TXP * TY, MINB)
             }
         }
     }
-    stage_tile2d<float, float, TX, TY, false, NT>(P, sm, x0, y0, tid, T_in, Y_in, nullptr);
+    if ((P.nx & 1) == 0)
+        stage_tile2d_pairs<TX, TY, NT>(P, sm, x0, y0, tid, T_in, Y_in);
+    else
+        stage_tile2d<float, float, TX, TY, false, NT>(P, sm, x0, y0, tid, T_in, Y_in, nullptr);
     cp_async_wait_all();
     __syncthreads();
 
@@ -172,10 +244,11 @@ __global__ void __launch_bounds__(TXP * TY, MINB)
     const F2 reac_T = F2(P.Q_cp) * q;
     // a7
     const F2 DT = acc.diff_T + reac_T;
-    pair_store(T_out + c, T0 + (DT - acc.conv_T), ok0, ok1);
+    const bool vec = ok0 && ok1 && (c & 1) == 0;
+    pair_store(T_out + c, T0 + (DT - acc.conv_T), ok0, ok1, vec);
 #pragma unroll
     for (int k = 0; k < NSP; ++k)
-        pair_store(Y_out + (long long)k * N + c, Y0[k] + (acc.rhs_Y[k] + F2(P.yield[k]) * q), ok0, ok1);
+        pair_store(Y_out + (long long)k * N + c, Y0[k] + (acc.rhs_Y[k] + F2(P.yield[k]) * q), ok0, ok1, vec);
     const F2 lam_Y = acc.lamY + F2(P.lam_yield) * q;
     const F2 Lam = fdiv(DT, T0) + fdiv(lam_Y, invW0);
     // a8-a10, on the populations read again from shared memory (the compiler
@@ -185,7 +258,7 @@ __global__ void __launch_bounds__(TXP * TY, MINB)
     for (int i = 0; i < 9; ++i) g[i] = F2(*reinterpret_cast<const float2*>(gs + i * 2 * NT));
     collide<2, F2>(P, g, rho0, u, acc.grad_rho, Lam);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) pair_store(g_out + (long long)i * N + c, g[i], ok0, ok1);
+    for (int i = 0; i < 9; ++i) pair_store(g_out + (long long)i * N + c, g[i], ok0, ok1, vec);
 }
 
 }  // namespace lbfd

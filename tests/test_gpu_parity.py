@@ -65,17 +65,23 @@ def case_channel_isothermal_poiseuille():
     return cfg, solid, T, Y, g
 
 
-def case_periodic_obstacles():
-    rng = np.random.Generator(np.random.PCG64(3))
-    cfg = inputs.base_config(dim=2, nx=67, ny=29, bc=["periodic"] * 6, u_in=0.0)
-    solid = np.zeros((29, 67), dtype=np.uint8)
+def case_periodic_obstacles(nx=67, ny=29, seed=3):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    cfg = inputs.base_config(dim=2, nx=nx, ny=ny, bc=["periodic"] * 6, u_in=0.0)
+    solid = np.zeros((ny, nx), dtype=np.uint8)
     for _ in range(6):  # blocks of 1..4 cells, incl. one-cell-thin walls
-        x, y = rng.integers(0, 67), rng.integers(0, 29)
+        x, y = rng.integers(0, nx), rng.integers(0, ny)
         solid[y:y + rng.integers(1, 5), x:x + rng.integers(1, 5)] = 1
     solid[10, 5:40] = 1  # a thin wall with fluid on both sides
     T, Y = inputs.ignition_fields(cfg, solid, 20, 35)
-    g, T, Y = inputs.perturbed_state(cfg, solid, T, Y, seed=4)
+    g, T, Y = inputs.perturbed_state(cfg, solid, T, Y, seed=seed + 1)
     return cfg, solid, T, Y, g
+
+
+def case_periodic_obstacles_even():
+    """Even nx: the packed-pair kernels stage and store two cells at a
+    time, and their halo wraps across both periodic faces."""
+    return case_periodic_obstacles(nx=66, ny=28, seed=13)
 
 
 def case_obstacles_adiabatic_solid():
@@ -106,6 +112,7 @@ CASES_2D = {
     "channel_adiabatic": case_channel_adiabatic,
     "channel_isothermal_poiseuille": case_channel_isothermal_poiseuille,
     "periodic_obstacles": case_periodic_obstacles,
+    "periodic_obstacles_even": case_periodic_obstacles_even,
     "obstacles_adiabatic_solid": case_obstacles_adiabatic_solid,
     "batched": case_batched,
 }
