@@ -36,7 +36,11 @@ def build(force: bool = False) -> str:
         tmp = _LIB + f".{os.getpid()}.tmp"
         cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c99", "-fPIC",
                "-shared", "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+        # OpenMP only threads orc_step over grid rows (for timing on all host
+        # cores); without it the oracle is the same single-threaded code
+        r = subprocess.run(cmd[:1] + ["-fopenmp"] + cmd[1:], capture_output=True)
+        if r.returncode != 0:
+            subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
         return _LIB
 
@@ -79,6 +83,8 @@ def _load():
         lib.orc_get_state.argtypes = [P, D, D, D]
         lib.orc_step.argtypes = [P, ctypes.c_int]
         lib.orc_step_slab.argtypes = [P, ctypes.c_int, ctypes.c_int]
+        lib.orc_set_threads.argtypes = [ctypes.c_int]
+        lib.orc_openmp.restype = ctypes.c_int
         lib.orc_set_geometry.argtypes = [P, ctypes.c_int, D]
         lib.orc_num_ghosts.restype = ctypes.c_long
         lib.orc_num_ghosts.argtypes = [P]
@@ -244,6 +250,17 @@ class Sim:
         keys = ("x_f", "mass", "heat_release", "fuel_consumption", "T_max", "x_hrr_max",
                 "n_nonfinite", "n_fluid")
         return dict(zip(keys, out.tolist()))
+
+
+def set_threads(n: int) -> int:
+    """Threads of every later step (1 unless changed; the result does not
+    depend on it).  Returns the count in effect: 1 when the library was
+    built without OpenMP."""
+    lib = _load()
+    if not lib.orc_openmp():
+        n = 1
+    lib.orc_set_threads(int(n))
+    return max(1, int(n))
 
 
 def cumulants(dim: int, Pi):

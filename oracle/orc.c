@@ -1142,26 +1142,48 @@ void orc_get_state(const orc_sim *S, double *T, double *Y, double *g)
     if (g) memcpy(g, S->g, sizeof(double) * (size_t)S->Q * N);
 }
 
+/* Threads of orc_step (OpenMP over grid rows when the library is built
+ * with -fopenmp; 1 by default).  Every cell's update reads state n only and
+ * writes its own outputs, so the result does not depend on the count; the
+ * threaded form exists to time the oracle on all host cores. */
+static int orc_nthreads = 1;
+
+void orc_set_threads(int n) { orc_nthreads = n > 0 ? n : 1; }
+
+int orc_openmp(void)
+{
+#ifdef _OPENMP
+    return 1;
+#else
+    return 0;
+#endif
+}
+
 /* Advance n coupled steps.  Solid cells keep their state. */
 void orc_step(orc_sim *S, int n)
 {
     long N = S->N;
-    double gin[27], gst[27], Yn[ORC_MAXSP], Tn;
+    int rows = S->s.ny * S->s.nz;
     for (int it = 0; it < n; ++it) {
         memcpy(S->gn, S->g, sizeof(double) * (size_t)S->Q * N);
         memcpy(S->Tn, S->T, sizeof(double) * (size_t)N);
         memcpy(S->Yn, S->Y, sizeof(double) * (size_t)S->nsp * N);
-        for (int z = 0; z < S->s.nz; ++z)
-            for (int y = 0; y < S->s.ny; ++y)
-                for (int x = 0; x < S->s.nx; ++x) {
-                    int p[3] = {x, y, z};
-                    long c = cell_index(S, p);
-                    if (S->solid[c]) continue;
-                    cell_update(S, p, c, gin, NULL, &Tn, Yn, gst);
-                    S->Tn[c] = Tn;
-                    for (int k = 0; k < S->nsp; ++k) S->Yn[(long)k * N + c] = Yn[k];
-                    for (int i = 0; i < S->Q; ++i) S->gn[(long)i * N + c] = gst[i];
-                }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(orc_nthreads)
+#endif
+        for (int row = 0; row < rows; ++row) {
+            double gin[27], gst[27], Yn[ORC_MAXSP], Tn;
+            int y = row % S->s.ny, z = row / S->s.ny;
+            for (int x = 0; x < S->s.nx; ++x) {
+                int p[3] = {x, y, z};
+                long c = cell_index(S, p);
+                if (S->solid[c]) continue;
+                cell_update(S, p, c, gin, NULL, &Tn, Yn, gst);
+                S->Tn[c] = Tn;
+                for (int k = 0; k < S->nsp; ++k) S->Yn[(long)k * N + c] = Yn[k];
+                for (int i = 0; i < S->Q; ++i) S->gn[(long)i * N + c] = gst[i];
+            }
+        }
         double *t;
         t = S->g; S->g = S->gn; S->gn = t;
         t = S->T; S->T = S->Tn; S->Tn = t;
