@@ -135,3 +135,24 @@ def test_autograd_function_backward(lbfd_lib):
     assert abs(J.item() - J2) <= 1e-14 * abs(J2)
     assert np.allclose(theta.grad.numpy(), 2.0 * g, rtol=1e-14, atol=0)
     assert math.isfinite(J.item())
+
+
+def test_adjoint_matches_the_cpu_adjoint_and_central_differences(lbfd_lib):
+    """The GPU discrete adjoint (reverse-mode tape of the CUDA step) against
+    the FP64 CPU adjoint of the oracle (reverse accumulation through an
+    independent restatement of the step): both are the transpose of the
+    derivative of the same discrete map, so they agree to rounding, 1e-8
+    relative per component; and directly against central differences of
+    the FP64 GPU step, 1e-4."""
+    from oracle import adjoint
+
+    cfg, solid, T, Y = case()
+    Jg, gg = grad.run_tangent(cfg, solid, T, Y, STEPS, precision="adjoint", checkpoint_every=50)
+    Jc, gc = adjoint.adjoint_gradient(cfg, solid, T, Y, STEPS, checkpoint_every=50)
+    assert abs(Jg - Jc) <= 1e-12 * abs(Jc), (Jg, Jc)
+    for k, name in enumerate(lbfd.THETA):
+        assert abs(gg[k] - gc[k]) <= 1e-8 * abs(gc[k]), (name, gg[k], gc[k])
+    theta = grad.theta_of(cfg)
+    fd = central_fd(lambda t: J_gpu(cfg, solid, T, Y, t, lbfd.OBJ_FLAME_POSITION), theta)
+    for k, name in enumerate(lbfd.THETA):
+        assert abs(gg[k] - fd[k]) <= 1e-4 * abs(fd[k]), (name, gg[k], fd[k])
