@@ -185,6 +185,28 @@ int lbfd_step(lbfd_handle* h, int n);
  * stream of its own and synchronises it before returning. */
 int lbfd_step_graph(lbfd_handle* h, int n);
 
+/* Advance n coupled steps in ONE persistent launch (2-D, LBFD_FP64 or
+ * LBFD_MIXED, staircase walls): a cooperative launch of as many blocks as
+ * are resident on the device at once; every step the blocks share out the
+ * interior tiles, the tiles of cells next to in-domain solids and the
+ * cells near domain faces (the per-cell arithmetic of kernel variant 6),
+ * then meet at a grid-wide barrier before the buffers swap roles.  Batches
+ * of channels packed into one masked domain (separated by solid rows)
+ * advance together in this one launch.  Every barrier wait is bounded by
+ * lbfd_set_wait_limit (default 2 s): a block that waits longer records it
+ * and returns, the others follow within the same step, and the call returns
+ * LBFD_ETIMEOUT with the step in lbfd_last_error(); the state is then
+ * undefined (set it again before stepping) and the handle stays usable.
+ * Synchronises the handle's stream (it reads the barrier's status).
+ * Errors: EINVAL, ENOTSUP (3-D, tangent precisions, curved walls), ENOMEM,
+ * ECUDA, ETIMEOUT. */
+int lbfd_step_persistent(lbfd_handle* h, int n);
+
+/* Bound of every grid-wide wait of lbfd_step_persistent, in nanoseconds.
+ * ns <= 0: no block waits at all, so every barrier that is not met at once
+ * fails (exercises the LBFD_ETIMEOUT path without a fault). */
+int lbfd_set_wait_limit(lbfd_handle* h, long long ns);
+
 /* Kernel variants of the step: 0 is the general form (any cell, D2Q9 and
  * D3Q27).  In 2-D (13 variants), 1..4 are shared-memory tiles of 32x8,
  * 32x4, 64x4 and 32x16 interior cells; 5..8 the same tiles plus a second

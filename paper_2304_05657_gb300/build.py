@@ -17,7 +17,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbfd.so")
 SOURCES = ["lbfd_api.cu", "lbfd_step.cu", "lbfd_step3d.cu", "lbfd_reduce.cu", "lbfd_tangent.cu",
-           "lbfd_geometry.cu", "lbfd_adjoint.cu"]
+           "lbfd_geometry.cu", "lbfd_adjoint.cu", "lbfd_persistent.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", CSRC, "-I", INCLUDE]

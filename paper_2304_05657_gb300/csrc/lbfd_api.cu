@@ -72,6 +72,9 @@ struct lbfd_handle {
     double* gh_w;
     void* gval;
     long long nghost;
+    // persistent step: barrier words and the bound of each grid-wide wait
+    lbfd::PersistentWait* pwait;
+    long long wait_limit_ns;
 };
 
 namespace {
@@ -238,6 +241,7 @@ void free_handle(lbfd_handle* h)
     if (h->interior) cudaFree(h->interior);
     if (h->aux) cudaFree(h->aux);
     if (h->wtiles) cudaFree(h->wtiles);
+    if (h->pwait) cudaFree(h->pwait);
     void* curved[] = {h->link_row, h->link_q, h->ghost_row, h->gh_start, h->gh_idx, h->gh_w, h->gval};
     for (void* p : curved)
         if (p) cudaFree(p);
@@ -374,6 +378,7 @@ int lbfd_create(const lbfd_grid* grid, const uint8_t* solid_mask, const lbfd_mec
     h->planes = (size_t)h->Q + 1 + lbfd::NSP;
     h->stream = nullptr;
     h->variant = is_tangent(h->precision) ? 0 : 1;
+    h->wait_limit_ns = 2000000000LL;  // 2 s per grid-wide wait of the persistent step
     const size_t bytes = h->planes * (size_t)h->stride * h->esz;
     for (int b = 0; b < 2; ++b) {
         e = cudaMalloc(&h->buf[b], bytes);
@@ -590,6 +595,42 @@ int lbfd_step_graph(lbfd_handle* h, int n)
     }
     CK(cudaGraphLaunch(h->graph, s));
     if (s != h->stream) CK(cudaStreamSynchronize(s));
+    h->cur ^= (n & 1);
+    h->steps += n;
+    return LBFD_OK;
+}
+
+int lbfd_set_wait_limit(lbfd_handle* h, long long ns)
+{
+    if (!h) return LBFD_EINVAL;
+    h->wait_limit_ns = ns;
+    return LBFD_OK;
+}
+
+int lbfd_step_persistent(lbfd_handle* h, int n)
+{
+    if (!h || n < 0) return LBFD_EINVAL;
+    if (h->dim != 2 || is_tangent(h->precision) || h->nghost > 0 || h->Pd.curved) return LBFD_ENOTSUP;
+    if (n == 0) return LBFD_OK;
+    if (!h->pwait) {
+        if (cudaMalloc((void**)&h->pwait, sizeof(lbfd::PersistentWait)) != cudaSuccess) {
+            h->pwait = nullptr;
+            return LBFD_ENOMEM;
+        }
+    }
+    int blocks = 0;
+    cudaError_t e = lbfd::launch_step_persistent(h->precision, h->Pd, h->Pf, view(h, h->cur), view(h, h->cur ^ 1), n,
+                                                 h->solid, lists(h), h->pwait, h->wait_limit_ns, h->stream, &blocks);
+    if (e != cudaSuccess) return cuda_fail(e, "persistent step launch");
+    lbfd::PersistentWait w{};
+    CK(cudaMemcpyAsync(&w, h->pwait, sizeof w, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (w.error) {
+        snprintf(g_last_error, sizeof g_last_error,
+                 "persistent step: a grid-wide wait gave up at step %d of %d (%d blocks, limit %lld ns)", w.step, n,
+                 blocks, h->wait_limit_ns);
+        return LBFD_ETIMEOUT;
+    }
     h->cur ^= (n & 1);
     h->steps += n;
     return LBFD_OK;

@@ -69,7 +69,7 @@ __device__ __forceinline__ long long cell_of(const StepParams<R>& P, int x, int 
 // FACES == false: the caller guarantees that no non-periodic face is
 // crossed (cells whose stencils stay inside the domain up to periodic wrap).
 template <int DIM, typename R, bool FACES = true>
-__device__ __forceinline__ int classify(const StepParams<R>& P, int q[3], const uint8_t* __restrict__ solid,
+__device__ __forceinline__ int classify(const StepParams<R>& P, int q[3], const uint8_t* LBFD_RESTRICT solid,
                                         long long* idx, int* face)
 {
     int wall = -1;

@@ -157,6 +157,23 @@ cudaError_t launch_ghost_fill(int precision, const StepParams<double>& Pd, const
                               const StepParams<Tan>& Pt, StateView in, const long long* start, const long long* nb,
                               const double* w, long long nghost, cudaStream_t stream);
 
+// Grid-wide barrier words of the persistent step (device memory, zeroed
+// before each launch): arrival count, generation, a failure flag and the
+// first step (1-based) whose barrier gave up.
+struct PersistentWait {
+    unsigned count;
+    unsigned gen;
+    int error;
+    int step;
+    unsigned next[2];  // work-item counters of even and odd steps
+};
+// n 2-D steps in one cooperative launch (lbfd_persistent.cu), alternating
+// a -> b -> a ...; *blocks gets the grid size.  limit_ns bounds every
+// barrier wait (<= 0: no waiting at all).
+cudaError_t launch_step_persistent(int precision, const StepParams<double>& Pd, const StepParams<float>& Pf,
+                                   StateView a, StateView b, int n, const uint8_t* solid, const BoundaryLists& bl,
+                                   PersistentWait* w, long long limit_ns, cudaStream_t stream, int* blocks);
+
 // Number of words of the reduction scratch.
 constexpr int RED_WORDS = 16;
 

@@ -2,6 +2,17 @@
 // already converted to the compute type R and to lattice units.
 #pragma once
 
+// Read-only hints of the step's state loads.  A kernel that writes the
+// state buffers and reads them back within one launch (the persistent
+// step) defines both before including the step headers: no restrict
+// qualifier and plain loads, so that no load takes the non-coherent path.
+#ifndef LBFD_RESTRICT
+#define LBFD_RESTRICT __restrict__
+#endif
+#ifndef LBFD_LDG
+#define LBFD_LDG(p) __ldg(p)
+#endif
+
 namespace lbfd {
 
 constexpr int NSP = 5;  // species count the kernels are built for

@@ -21,7 +21,7 @@ namespace lbfd {
 // ---------------------------------------------------------------------------
 template <int DIM, typename S, typename R, bool FACES = true>
 __device__ __forceinline__ R pull_general(const StepParams<R>& P, int i, const int p[3], long long c,
-                                          const S* __restrict__ g, const uint8_t* __restrict__ solid,
+                                          const S* LBFD_RESTRICT g, const uint8_t* LBFD_RESTRICT solid,
                                           R rho_cell)
 {
     const long long N = P.N;
@@ -131,7 +131,7 @@ __device__ __forceinline__ R pull_general(const StepParams<R>& P, int i, const i
 // bounce-back (Eq. 28) from solid neighbours
 template <int DIM, typename S, typename R>
 __device__ __forceinline__ void pull_walls(const StepParams<R>& P, const int p[3], long long c,
-                                           const S* __restrict__ g, const uint8_t* __restrict__ solid, R* out)
+                                           const S* LBFD_RESTRICT g, const uint8_t* LBFD_RESTRICT solid, R* out)
 {
     constexpr int Q = DIM == 2 ? 9 : 27;
     const long long N = P.N;
@@ -185,7 +185,7 @@ __device__ __forceinline__ void ghost_mode(const StepParams<R>& P, int type, int
 
 template <int DIM, typename R, bool FACES = true>
 __device__ __forceinline__ void build_line(const StepParams<R>& P, const int p[3], long long c, int a,
-                                           const uint8_t* __restrict__ solid, LineDesc<R>& L)
+                                           const uint8_t* LBFD_RESTRICT solid, LineDesc<R>& L)
 {
     L.near = 0;
     L.src[2] = c;
@@ -254,7 +254,7 @@ __device__ __forceinline__ void build_line(const StepParams<R>& P, const int p[3
 // density of a ghost is reconstructed directly, with rho_B = EOS(T_B, Y))
 template <typename S, typename R>
 __device__ __forceinline__ void line_point(const StepParams<R>& P, const LineDesc<R>& L, int j,
-                                           const S* __restrict__ T, const S* __restrict__ Y, R& Tj, R* Yj,
+                                           const S* LBFD_RESTRICT T, const S* LBFD_RESTRICT Y, R& Tj, R* Yj,
                                            R& invWj, R& rhoj)
 {
     const long long s = L.src[j];
@@ -355,10 +355,10 @@ __device__ __forceinline__ void fd_axis(const StepParams<R>& P, int a, int near,
 // ---------------------------------------------------------------------------
 template <int DIM, typename S, typename R, bool FACES = true>
 __device__ __forceinline__ void cell_step_general(const StepParams<R>& P, const int p[3], long long c,
-                                                  const S* __restrict__ g_in, S* __restrict__ g_out,
-                                                  const S* __restrict__ T_in, S* __restrict__ T_out,
-                                                  const S* __restrict__ Y_in, S* __restrict__ Y_out,
-                                                  const uint8_t* __restrict__ solid)
+                                                  const S* LBFD_RESTRICT g_in, S* LBFD_RESTRICT g_out,
+                                                  const S* LBFD_RESTRICT T_in, S* LBFD_RESTRICT T_out,
+                                                  const S* LBFD_RESTRICT Y_in, S* LBFD_RESTRICT Y_out,
+                                                  const uint8_t* LBFD_RESTRICT solid)
 {
     constexpr int Q = DIM == 2 ? 9 : 27;
     const long long N = P.N;

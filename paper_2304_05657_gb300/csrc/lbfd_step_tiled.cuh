@@ -210,7 +210,7 @@ __device__ __forceinline__ int wall_line(const uint8_t* mask, int p0, int st, in
 // plain pull, the x-1, x+1, y-1, y+1 neighbours wrapped on periodic axes
 // (the offsets stay inside the domain for any in-range cell)
 template <typename S, typename R>
-__device__ __forceinline__ void pull_interior(const StepParams<R>& P, const S* __restrict__ g_in, long long c, int x,
+__device__ __forceinline__ void pull_interior(const StepParams<R>& P, const S* LBFD_RESTRICT g_in, long long c, int x,
                                               int y, R* g)
 {
     const int oxm = x == 0 ? P.nx - 1 : -1, oxp = x == P.nx - 1 ? 1 - P.nx : 1;
@@ -220,7 +220,7 @@ __device__ __forceinline__ void pull_interior(const StepParams<R>& P, const S* _
     for (int i = 0; i < 9; ++i) {
         const int ox = cx_of(i) > 0 ? oxm : (cx_of(i) < 0 ? oxp : 0);
         const int oy = cy_of(i) > 0 ? oym : (cy_of(i) < 0 ? oyp : 0);
-        g[i] = R(__ldg(gc + (long long)i * P.N + (ox + oy)));
+        g[i] = R(LBFD_LDG(gc + (long long)i * P.N + (ox + oy)));
     }
 }
 
@@ -232,8 +232,8 @@ __device__ __forceinline__ void pull_interior(const StepParams<R>& P, const S* _
 // like fluid ones, their values are never read.
 template <typename S, typename R, int TX, int TY, bool WALLS, int NTHR>
 __device__ __forceinline__ void stage_tile2d(const StepParams<R>& P, const TileSmem<R>& sm, int x0, int y0, int tid,
-                                             const S* __restrict__ T_in, const S* __restrict__ Y_in,
-                                             const uint8_t* __restrict__ solid)
+                                             const S* LBFD_RESTRICT T_in, const S* LBFD_RESTRICT Y_in,
+                                             const uint8_t* LBFD_RESTRICT solid)
 {
     using G = TileGeom<TX, TY>;
     constexpr int SX = G::SX, NPT = G::NPT;
@@ -313,15 +313,17 @@ __device__ __forceinline__ bool interior_point(const uint8_t* mask, int p0)
     return fast && !mask[p0 + SX + 1] && !mask[p0 + SX - 1] && !mask[p0 - SX + 1] && !mask[p0 - SX - 1];
 }
 
-// body of the 2-D tile kernels.  WALLS == false: the interior cells of
-// every tile.  WALLS == true: only the cells next to in-domain solid cells
-// (or walls that act like them), in the tiles listed in `tiles`.
+// body of the 2-D tile kernels: the tile (bx, by), this thread at (tx, ty)
+// of its TX x TY threads.  WALLS == false: the interior cells of the tile.
+// WALLS == true: only the cells next to in-domain solid cells (or walls that
+// act like them).  Every thread of the block calls it (it synchronises the
+// block once, after the staging).
 template <typename S, typename R, int TX, int TY, bool WALLS>
-__device__ __forceinline__ void tiled2d_body(const StepParams<R>& P, const S* __restrict__ g_in, S* __restrict__ g_out,
-                                             const S* __restrict__ T_in, S* __restrict__ T_out,
-                                             const S* __restrict__ Y_in, S* __restrict__ Y_out,
-                                             const uint8_t* __restrict__ solid, const int* __restrict__ tiles,
-                                             const uint8_t* __restrict__ interior)
+__device__ __forceinline__ void tiled2d_body(const StepParams<R>& P, const S* LBFD_RESTRICT g_in, S* LBFD_RESTRICT g_out,
+                                             const S* LBFD_RESTRICT T_in, S* LBFD_RESTRICT T_out,
+                                             const S* LBFD_RESTRICT Y_in, S* LBFD_RESTRICT Y_out,
+                                             const uint8_t* LBFD_RESTRICT solid,
+                                             const uint8_t* LBFD_RESTRICT interior, int tx, int ty, int bx, int by)
 {
     using G = TileGeom<TX, TY>;
     constexpr int SX = G::SX, NPT = G::NPT;
@@ -334,17 +336,10 @@ __device__ __forceinline__ void tiled2d_body(const StepParams<R>& P, const S* __
     sm.rho = sm.invW + NPT;
     sm.mask = reinterpret_cast<uint8_t*>(sm.rho + NPT);
 
-    int bx = blockIdx.x, by = blockIdx.y;
-    if constexpr (WALLS) {
-        const int t = tiles[blockIdx.x];
-        const int gxn = (P.nx + TX - 1) / TX;
-        bx = t % gxn;
-        by = t / gxn;
-    }
     const int x0 = bx * TX, y0 = by * TY;
-    const int tid = threadIdx.x + TX * threadIdx.y;
+    const int tid = tx + TX * ty;
     const long long N = P.N;
-    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    const int x = x0 + tx, y = y0 + ty;
     const bool inside = x < P.nx && y < P.ny;
     const long long c = (long long)x + (long long)P.nx * y;
     R g[9];
@@ -363,7 +358,7 @@ __device__ __forceinline__ void tiled2d_body(const StepParams<R>& P, const S* __
     __syncthreads();
 
     if (!inside) return;
-    const int p0 = (threadIdx.y + 2) * SX + threadIdx.x + 2;
+    const int p0 = (ty + 2) * SX + tx + 2;
     if constexpr (WALLS) {
         if (sm.mask[p0]) return;  // solid
         fast = interior_point<SX>(sm.mask, p0);
@@ -393,7 +388,7 @@ __device__ __forceinline__ void tiled2d_body(const StepParams<R>& P, const S* __
             const int oy = cy_of(i) > 0 ? oym : (cy_of(i) < 0 ? oyp : 0);
             long long off = (long long)i * N + (ox + oy);
             if (sm.mask[p0 - cx_of(i) - cy_of(i) * SX]) off = (long long)opposite<2>(i) * N;
-            g[i] = R(__ldg(gc + off));
+            g[i] = R(LBFD_LDG(gc + off));
         }
     }
     // a2
@@ -440,31 +435,35 @@ __device__ __forceinline__ void tiled2d_body(const StepParams<R>& P, const S* __
 // FP32: four 256-thread blocks (1024 threads) per SM, i.e. <= 64 registers
 template <typename S, typename R, int TX, int TY>
 __global__ void __launch_bounds__(TX * TY, sizeof(R) == 4 ? 1024 / (TX * TY) : 1)
-    step_kernel_tiled2d(StepParams<R> P, const S* __restrict__ g_in, S* __restrict__ g_out,
-                        const S* __restrict__ T_in, S* __restrict__ T_out, const S* __restrict__ Y_in,
-                        S* __restrict__ Y_out, const uint8_t* __restrict__ interior)
+    step_kernel_tiled2d(StepParams<R> P, const S* LBFD_RESTRICT g_in, S* LBFD_RESTRICT g_out,
+                        const S* LBFD_RESTRICT T_in, S* LBFD_RESTRICT T_out, const S* LBFD_RESTRICT Y_in,
+                        S* LBFD_RESTRICT Y_out, const uint8_t* LBFD_RESTRICT interior)
 {
-    tiled2d_body<S, R, TX, TY, false>(P, g_in, g_out, T_in, T_out, Y_in, Y_out, nullptr, nullptr, interior);
+    tiled2d_body<S, R, TX, TY, false>(P, g_in, g_out, T_in, T_out, Y_in, Y_out, nullptr, interior, threadIdx.x,
+                                      threadIdx.y, blockIdx.x, blockIdx.y);
 }
 
 // the cells next to in-domain solid cells, over the tiles that contain any
 template <typename S, typename R, int TX, int TY>
 __global__ void __launch_bounds__(TX * TY)
-    step_kernel_tiled2d_walls(StepParams<R> P, const S* __restrict__ g_in, S* __restrict__ g_out,
-                              const S* __restrict__ T_in, S* __restrict__ T_out, const S* __restrict__ Y_in,
-                              S* __restrict__ Y_out, const uint8_t* __restrict__ solid, const int* __restrict__ tiles)
+    step_kernel_tiled2d_walls(StepParams<R> P, const S* LBFD_RESTRICT g_in, S* LBFD_RESTRICT g_out,
+                              const S* LBFD_RESTRICT T_in, S* LBFD_RESTRICT T_out, const S* LBFD_RESTRICT Y_in,
+                              S* LBFD_RESTRICT Y_out, const uint8_t* LBFD_RESTRICT solid, const int* LBFD_RESTRICT tiles)
 {
-    tiled2d_body<S, R, TX, TY, true>(P, g_in, g_out, T_in, T_out, Y_in, Y_out, solid, tiles, nullptr);
+    const int t = tiles[blockIdx.x];
+    const int gxn = (P.nx + TX - 1) / TX;
+    tiled2d_body<S, R, TX, TY, true>(P, g_in, g_out, T_in, T_out, Y_in, Y_out, solid, nullptr, threadIdx.x,
+                                     threadIdx.y, t % gxn, t / gxn);
 }
 
 // The cells the tiled kernel leaves out: general form over a cell list
 // (FACES == false: cells whose stencils reach no non-periodic face).
 template <int DIM, typename S, typename R, bool FACES = true>
-__global__ void __launch_bounds__(128) step_kernel_boundary(StepParams<R> P, const S* __restrict__ g_in,
-                                                            S* __restrict__ g_out, const S* __restrict__ T_in,
-                                                            S* __restrict__ T_out, const S* __restrict__ Y_in,
-                                                            S* __restrict__ Y_out, const uint8_t* __restrict__ solid,
-                                                            const long long* __restrict__ cells, long long ncells)
+__global__ void __launch_bounds__(128) step_kernel_boundary(StepParams<R> P, const S* LBFD_RESTRICT g_in,
+                                                            S* LBFD_RESTRICT g_out, const S* LBFD_RESTRICT T_in,
+                                                            S* LBFD_RESTRICT T_out, const S* LBFD_RESTRICT Y_in,
+                                                            S* LBFD_RESTRICT Y_out, const uint8_t* LBFD_RESTRICT solid,
+                                                            const long long* LBFD_RESTRICT cells, long long ncells)
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ncells) return;

@@ -36,7 +36,7 @@ SYMBOLS = (
     "lbfd_last_error", "lbfd_step_graph", "lbfd_num_variants", "lbfd_get_variant", "lbfd_set_variant",
     "lbfd_autotune", "lbfd_diagnostics_noalloc", "lbfd_launches_per_step", "lbfd_read_tangent", "lbfd_gradient",
     "lbfd_diagnostics_rows", "lbfd_set_inlet_velocity", "lbfd_set_curved_walls", "lbfd_read_cells",
-    "lbfd_adjoint_gradient",
+    "lbfd_adjoint_gradient", "lbfd_step_persistent", "lbfd_set_wait_limit",
 )
 
 
@@ -107,6 +107,8 @@ def load(path: str = LIB_PATH):
     lib.lbfd_num_populations.restype = ctypes.c_int
     lib.lbfd_num_populations.argtypes = [H]
     lib.lbfd_step_graph.argtypes = [H, ctypes.c_int]
+    lib.lbfd_step_persistent.argtypes = [H, ctypes.c_int]
+    lib.lbfd_set_wait_limit.argtypes = [H, ctypes.c_longlong]
     lib.lbfd_num_variants.argtypes = [H]
     lib.lbfd_get_variant.argtypes = [H]
     lib.lbfd_set_variant.argtypes = [H, ctypes.c_int]
@@ -217,6 +219,15 @@ class Solver:
 
     def step_graph(self, n: int):
         _check(self.lib, self.lib.lbfd_step_graph(self.h, int(n)), "lbfd_step_graph")
+
+    def step_persistent(self, n: int):
+        """n steps in one persistent launch (grid-wide barriers between
+        steps); raises LbfdError with status ETIMEOUT when a barrier wait
+        gave up."""
+        _check(self.lib, self.lib.lbfd_step_persistent(self.h, int(n)), "lbfd_step_persistent")
+
+    def set_wait_limit(self, ns: int):
+        _check(self.lib, self.lib.lbfd_set_wait_limit(self.h, int(ns)), "lbfd_set_wait_limit")
 
     @property
     def num_variants(self) -> int:
