@@ -70,9 +70,18 @@ extern "C" {
                                 in FP64 above T_fp64 and the objectives accumulated
                                 in FP64 (lbfd_gradient); no curved walls. */
 
-/* objectives of lbfd_gradient */
+/* objectives of lbfd_gradient and of the discrete adjoint */
 #define LBFD_OBJ_FLAME_POSITION 0 /* x_f [m] as in lbfd_flame_position */
-#define LBFD_OBJ_HEAT_RELEASE 1   /* sum of LBFD_FIELD_HRR over fluid cells */
+#define LBFD_OBJ_HEAT_RELEASE 1   /* sum of LBFD_FIELD_HRR over fluid cells (lbfd_gradient only) */
+#define LBFD_OBJ_QUENCH_DISTANCE 2 /* smooth distance [cells] between the reaction zone and the cold
+                                      walls, the differentiable stand-in for the dead-zone thickness of
+                                      Sec. IV.A: J = (sum_c h_c d_c^-4 / sum_c h_c)^(-1/4) over fluid
+                                      cells, h_c = LBFD_FIELD_HRR, d_c the distance from the cell centre
+                                      to the nearest isothermal boundary (an isothermal solid cell or
+                                      wall face; wall planes half-way between cells) along the axis
+                                      directions, 64 when none is that close.  A heat-release-weighted
+                                      soft minimum of the wall distance: it tends to the distance of the
+                                      reacting cells closest to a wall. */
 
 /* number of species the kernels are built for */
 #define LBFD_NSP 5
@@ -283,24 +292,48 @@ int lbfd_flame_position(lbfd_handle* h, double* x_f, double* mass, double* heat_
 int lbfd_read_tangent(lbfd_handle* h, int field, int k, double* out);
 
 /* Tangent precision only: objective J (LBFD_OBJ_*) of the current state and
- * its gradient dJ/dtheta[4].  Either pointer may be NULL.  Synchronises. */
+ * its gradient dJ/dtheta[4] (the forward-mode derivatives carried by the
+ * state).  Either pointer may be NULL.  Synchronises. */
 int lbfd_gradient(lbfd_handle* h, int objective, double* value, double* grad);
 
-/* Discrete adjoint (reverse mode), LBFD_FP64 2-D handles with staircase
- * walls: advances the state by `steps` steps, keeping a checkpoint of the
- * state every `checkpoint_every` steps, and returns J = the flame position
- * x_f [m] after the last step (objective LBFD_OBJ_FLAME_POSITION) and
- * dJ/dtheta[4], theta = (ln A, Ta, T_wall, u_in), by sweeping the steps
- * backwards: each segment is recomputed from its checkpoint and the adjoint
- * of every step, lambda^n = (dF/dx^n)^T lambda^{n+1}, is taken by recording
- * each fluid cell's step on a reverse-mode tape (the exact transpose of the
- * derivative of the discrete step, branches taken on the values) and adding
- * (dF/dtheta)^T lambda^{n+1} to the gradient in FP64.  Device memory for the
- * call: steps/checkpoint_every + checkpoint_every + 6 state copies plus a
- * tape of at most 6 GB (28 B x 4096 nodes per cell, cells in chunks), freed
- * before returning.  Errors: LBFD_EINVAL (arguments),
- * LBFD_ENOTSUP (other precision, 3-D, curved walls, or a cell whose step
- * needs more than the tape's 4096 nodes), LBFD_ENOMEM.  Synchronises. */
+/* Discrete adjoint (reverse mode) of the coupled step, 2-D handles with
+ * staircase walls, LBFD_FP64 or LBFD_MIXED (FP32 forward pass).  The
+ * gradient of an objective J (LBFD_OBJ_FLAME_POSITION, x_f [m], or
+ * LBFD_OBJ_QUENCH_DISTANCE) of the state after n steps with respect to
+ * theta = (ln A, Ta, T_wall, u_in) is the adjoint recursion
+ * lambda^n = (dF/dx^n)^T lambda^{n+1} run backwards from
+ * lambda^N = dJ/dx^N, plus (dF/dtheta)^T lambda^{n+1} summed over the steps
+ * (and J's own dependence on theta).  Each step's adjoint is taken by
+ * recording every fluid cell's step on a reverse-mode tape and sweeping it
+ * backwards: the exact transpose of the derivative of the discrete step,
+ * branches taken on the values.  The forward pass keeps a copy of the state
+ * every `checkpoint_every` steps; the backward pass recomputes each segment
+ * from its copy with the forward kernels (FP32 ones for LBFD_MIXED) and
+ * evaluates every step's adjoint in FP64 at that trajectory, accumulating
+ * lambda and the gradient in FP64.
+ *
+ * lbfd_adjoint_setup: the checkpoint interval of later calls (default 200).
+ * lbfd_adjoint_record: advance the handle's state by `steps` steps, keeping
+ *   the checkpoints (steps/checkpoint_every state copies in device memory,
+ *   held by the handle until lbfd_adjoint_backward or the next record), and
+ *   return J of the final state in *value.
+ * lbfd_adjoint_backward: the sweep over the recorded steps with
+ *   lambda^N = seed * dJ/dx^N; grad[4] = seed * dJ/dtheta.  Frees the
+ *   record.  The forward/backward split serves reverse-mode frameworks
+ *   (the backward call receives the incoming gradient as seed).
+ * lbfd_adjoint_run: record followed by backward with seed 1.
+ * lbfd_adjoint_gradient: lbfd_adjoint_run with this checkpoint interval
+ *   for the one call.
+ * Device memory of a backward call: checkpoint_every + 2 state copies and
+ *   two FP64 adjoint states, plus a tape of at most 6 GB (26 B x 4096 nodes
+ *   per cell, cells in chunks), freed before returning.  All synchronise.
+ * Errors: LBFD_EINVAL (arguments, backward without a record), LBFD_ENOTSUP
+ * (other precision, 3-D, curved walls, or a cell whose step needs more than
+ * the tape's 4096 nodes), LBFD_ENOMEM. */
+int lbfd_adjoint_setup(lbfd_handle* h, int checkpoint_every);
+int lbfd_adjoint_record(lbfd_handle* h, int steps, int objective, double* value);
+int lbfd_adjoint_backward(lbfd_handle* h, double seed, double* grad);
+int lbfd_adjoint_run(lbfd_handle* h, int steps, int objective, double* value, double* grad);
 int lbfd_adjoint_gradient(lbfd_handle* h, int steps, int checkpoint_every, int objective, double* value,
                           double* grad);
 

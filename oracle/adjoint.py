@@ -3,12 +3,15 @@
 Only the tests and the gradient leg of ``bench.py`` import this module; the
 CUDA library and its binding never do.
 
-What it computes.  The gradient of the flame position after n steps,
+What it computes.  The gradient, with respect to theta = (ln A, Ta, T_wall,
+u_in), of an objective of the state after n steps: the flame position
 J = dx * sum_fluid Y_F / (Y_F,in * fluid cells of the x = 0 section)
-(Sec. IV.A: the flame is located from the unburnt fuel), with respect to
-theta = (ln A, Ta, T_wall, u_in), as the transpose of the derivative of the
-discrete D2Q9 step, lambda^n = (dF/dx^n)^T lambda^{n+1}, accumulated in
-reverse over the steps.
+(Sec. IV.A: the flame is located from the unburnt fuel), or the quenching
+distance J = (sum h d^-4 / sum h)^(-1/4) (a heat-release-weighted soft
+minimum of the distance d from a cell to the nearest cold wall, standing in
+for the dead-zone thickness of Sec. IV.A), as the transpose of the
+derivative of the discrete D2Q9 step, lambda^n = (dF/dx^n)^T lambda^{n+1},
+accumulated in reverse over the steps.
 
 How.  The step is restated here with plain PyTorch CPU operations in FP64,
 vectorised over the fluid cells, in the order of the oracle (``orc.c``):
@@ -97,6 +100,7 @@ class Geometry:
                 for j, (k, s, face) in enumerate(pts):
                     self.lkind[a, j, f], self.lsrc[a, j, f], self.lface[a, j, f] = k, s, face
         self.section = int(sum(1 for y in range(ny) if not self.solid[y, 0]))
+        self.wall_distance = np.array([self._wall_distance(c % nx, c // nx) for c in self.fluid])
         self.inlet_y = np.array([c // nx for c in self.fluid], dtype=np.float64) + 0.5
 
     # --- classification of a lattice position (periodic axes wrapped) ----
@@ -165,6 +169,34 @@ class Geometry:
         if self.solid[src[1], src[0]]:
             return BOUNCE, c, -1
         return STREAM, s, -1
+
+    def _wall_distance(self, x, y, cap=64):
+        """Distance (cells, to the wall plane half-way between cells) to the
+        nearest cold boundary along the four axis directions: an isothermal
+        solid cell (when solids are isothermal) or the layer beyond an
+        isothermal wall face; periodic faces are crossed; `cap` if none."""
+        best = float(cap)
+        n = [self.nx, self.ny]
+        for a in range(2):
+            for side in (-1, 1):
+                for j in range(1, cap + 1):
+                    if j - 0.5 >= best:
+                        break
+                    q = [x, y]
+                    q[a] += side * j
+                    if q[a] < 0 or q[a] >= n[a]:
+                        f = 2 * a + (0 if q[a] < 0 else 1)
+                        if self.bc[f] == PERIODIC:
+                            q[a] %= n[a]
+                        else:
+                            if self.bc[f] == WALL_ISO:
+                                best = j - 0.5
+                            break
+                    if self.solid[q[1], q[0]]:
+                        if self.solid_iso:
+                            best = j - 0.5
+                        break
+        return best
 
     def _ghost_kind(self, kind, face):
         """(line point kind, Dirichlet face or -1 for a solid) of a ghost
@@ -477,6 +509,27 @@ class Step:
         """J = dx * sum_fluid Y_F / (Y_F,in * fluid cells of the x = 0 section) [m]."""
         return self.cfg["dx"] * Y[self.fuel, self.fluid].sum() / (self.cfg["Y_in"][self.fuel] * self.geo.section)
 
+    def quench_distance(self, T, Y, theta):
+        """J = (sum_fluid h d^-4 / sum_fluid h)^(-1/4) [cells], h = rho (Q/cp) q
+        the heat release of a cell (the rate with theta's A and Ta) and d its
+        distance to the nearest cold wall."""
+        cfg = self.cfg
+        fl = self.fluid
+        Tc, Yc = T[fl], Y[:, fl]
+        rho = self.eos(Tc, (Yc / self.W[:, None]).sum(0))
+        yf = torch.where(Yc[self.fuel] > 0.0, Yc[self.fuel], torch.zeros_like(Tc))
+        yo = torch.where(Yc[self.ox] > 0.0, Yc[self.ox], torch.zeros_like(Tc))
+        h = rho * cfg["Q"] / cfg["cp"] * torch.exp(theta[0]) * cfg["dt"] * yf * yo * torch.exp(-theta[1] / Tc)
+        w = torch.as_tensor(self.geo.wall_distance) ** -4.0
+        return ((h * w).sum() / h.sum()) ** -0.25
+
+    def objective(self, name, g, T, Y, theta):
+        if name == "flame_position":
+            return self.flame_position(Y)
+        if name == "quench_distance":
+            return self.quench_distance(T, Y, theta)
+        raise ValueError(name)
+
 
 def _to_t(a):
     return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64))
@@ -494,9 +547,11 @@ def forward(cfg, solid, T0, Y0, g0, steps: int, theta=None):
     return g.numpy(), T.numpy(), Y.numpy()
 
 
-def adjoint_gradient(cfg, solid, T0, Y0, steps: int, checkpoint_every: int = 0, g0=None, theta=None):
-    """(J, dJ/dtheta) of the flame position after `steps` steps from
-    (T0, Y0, g0 = 0 by default), by reverse accumulation over the steps.
+def adjoint_gradient(cfg, solid, T0, Y0, steps: int, checkpoint_every: int = 0, g0=None, theta=None,
+                     objective: str = "flame_position"):
+    """(J, dJ/dtheta) of the objective (flame_position or quench_distance)
+    after `steps` steps from (T0, Y0, g0 = 0 by default), by reverse
+    accumulation over the steps.
     checkpoint_every > 0 keeps only the state at the start of each segment
     of that many steps and recomputes the segment's tape in the backward
     sweep."""
@@ -522,6 +577,6 @@ def adjoint_gradient(cfg, solid, T0, Y0, steps: int, checkpoint_every: int = 0, 
         else:
             g, T, Y = segment(n, g, T, Y, th)
         done += n
-    J = st.flame_position(Y)
+    J = st.objective(objective, g, T, Y, th)
     (grad,) = torch.autograd.grad(J, th)
     return float(J.detach()), grad.numpy()

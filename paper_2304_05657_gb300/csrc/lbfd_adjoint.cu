@@ -11,12 +11,14 @@ namespace lbfd {
 
 constexpr int REV_BLOCK = 64;
 
-// the double state as tape input (values only)
-__global__ void __launch_bounds__(256) to_rev_kernel(long long n, const double* __restrict__ in,
+// the state (FP64, or the FP32 state of the mixed form widened to FP64) as
+// tape input (values only)
+template <typename S>
+__global__ void __launch_bounds__(256) to_rev_kernel(long long n, const S* __restrict__ in,
                                                      RevStore* __restrict__ out)
 {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < n) out[e] = RevStore(Rev(in[e]));
+    if (e < n) out[e] = RevStore(Rev((double)in[e]));
 }
 
 template <int DIM>
@@ -134,7 +136,7 @@ static StepParams<Rev> rev_params(const StepParams<double>& D)
 size_t adjoint_node_bytes() { return 2 * sizeof(double) + 2 * sizeof(int16_t) + sizeof(double); }
 size_t rev_store_bytes() { return sizeof(RevStore); }
 
-cudaError_t launch_adjoint_step(int dim, const StepParams<double>& Pd, int planes, const double* state,
+cudaError_t launch_adjoint_step(int dim, const StepParams<double>& Pd, int planes, const void* state, bool fp32,
                                 const uint8_t* solid, const double* lam_next, double* lam, double* dtheta,
                                 const AdjointWork& w, cudaStream_t stream)
 {
@@ -142,7 +144,11 @@ cudaError_t launch_adjoint_step(int dim, const StepParams<double>& Pd, int plane
     const long long nel = (long long)planes * Pd.N;
     RevStore* rin = (RevStore*)w.rin;
     RevStore* rout = (RevStore*)w.rout;
-    to_rev_kernel<<<(unsigned)((nel + 255) / 256), 256, 0, stream>>>(nel, state, rin);
+    const unsigned nb = (unsigned)((nel + 255) / 256);
+    if (fp32)
+        to_rev_kernel<float><<<nb, 256, 0, stream>>>(nel, (const float*)state, rin);
+    else
+        to_rev_kernel<double><<<nb, 256, 0, stream>>>(nel, (const double*)state, rin);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     RevTape tp;
@@ -167,6 +173,133 @@ cudaError_t launch_adjoint_step(int dim, const StepParams<double>& Pd, int plane
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// Objectives of the final state and their adjoint seeds
+// ---------------------------------------------------------------------------
+
+// heat release of one cell, h = rho (Q/cp) q (Sec. IV observables), and its
+// partial derivatives with respect to T and Y_k
+template <typename S>
+__device__ __forceinline__ double cell_hrr(const StepParams<double>& P, const S* T, const S* Y, long long c,
+                                           double* dT, double* dY)
+{
+    const double Tc = (double)T[c];
+    double Yc[NSP], invW = 0.0;
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) {
+        Yc[k] = (double)Y[(long long)k * P.N + c];
+        invW += Yc[k] * P.inv_Wk[k];
+    }
+    const double rho = P.T_in * P.invW_in / (Tc * invW);
+    const double yf = pick_species(Yc, P.fuel), yo = pick_species(Yc, P.oxid);
+    const double yfp = yf > 0.0 ? yf : 0.0, yop = yo > 0.0 ? yo : 0.0;
+    const double e = P.A_lat * ::exp(-P.Ta / Tc);
+    const double h = rho * P.Q_cp * e * yfp * yop;
+    if (dT) {
+        *dT = h * (P.Ta / (Tc * Tc) - 1.0 / Tc);
+#pragma unroll
+        for (int k = 0; k < NSP; ++k) {
+            double d = -h * P.inv_Wk[k] / invW;  // through rho
+            if (k == P.fuel && yf > 0.0) d += rho * P.Q_cp * e * yop;
+            if (k == P.oxid && yo > 0.0) d += rho * P.Q_cp * e * yfp;
+            dY[k] = d;
+        }
+    }
+    return h;
+}
+
+// red[0] += sum h, red[1] += sum h w (FP64, warp shuffles + atomics)
+template <typename S>
+__global__ void __launch_bounds__(256) quench_sums_kernel(StepParams<double> P, const S* __restrict__ T,
+                                                          const S* __restrict__ Y, const uint8_t* __restrict__ solid,
+                                                          const double* __restrict__ wgt, double* red)
+{
+    double a0 = 0.0, a1 = 0.0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < P.ncell; c += stride) {
+        if (solid[c]) continue;
+        const double h = cell_hrr(P, T, Y, c, nullptr, nullptr);
+        a0 += h;
+        a1 += h * wgt[c];
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        a0 += __shfl_down_sync(0xffffffffu, a0, off);
+        a1 += __shfl_down_sync(0xffffffffu, a1, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&red[0], a0);
+        atomicAdd(&red[1], a1);
+    }
+}
+
+// lam = seed * dJ/dstate for J = (S1/S0)^(-1/4), S0 = sum h, S1 = sum h w;
+// dtheta += seed * (the explicit dJ/d ln A and dJ/dTa through h)
+template <typename S>
+__global__ void __launch_bounds__(256) quench_seed_kernel(StepParams<double> P, const S* __restrict__ T,
+                                                          const S* __restrict__ Y, const uint8_t* __restrict__ solid,
+                                                          const double* __restrict__ wgt, double S0, double S1,
+                                                          double J, double seed, double* __restrict__ lam,
+                                                          double* dtheta, int Q)
+{
+    double gA = 0.0, gTa = 0.0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < P.ncell; c += stride) {
+        if (solid[c]) continue;
+        double dT, dY[NSP];
+        const double h = cell_hrr(P, T, Y, c, &dT, dY);
+        const double dJdh = seed * (-0.25) * J * (wgt[c] / S1 - 1.0 / S0);
+        lam[(long long)Q * P.N + c] += dJdh * dT;
+#pragma unroll
+        for (int k = 0; k < NSP; ++k) lam[(long long)(Q + 1 + k) * P.N + c] += dJdh * dY[k];
+        gA += dJdh * h;                           // dh / d ln A = h
+        gTa += dJdh * (-h / (double)T[c]);        // dh / dTa = -h / T
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        gA += __shfl_down_sync(0xffffffffu, gA, off);
+        gTa += __shfl_down_sync(0xffffffffu, gTa, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&dtheta[0], gA);
+        atomicAdd(&dtheta[1], gTa);
+    }
+}
+
+static unsigned red_blocks(long long ncell)
+{
+    const long long want = (ncell + 255) / 256;
+    return (unsigned)(want < 1024 ? (want > 0 ? want : 1) : 1024);
+}
+
+cudaError_t launch_quench_sums(const StepParams<double>& Pd, StateView st, bool fp32, const uint8_t* solid,
+                               const double* wgt, double* red, cudaStream_t stream)
+{
+    cudaError_t e = cudaMemsetAsync(red, 0, 2 * sizeof(double), stream);
+    if (e != cudaSuccess) return e;
+    const unsigned nb = red_blocks(Pd.ncell);
+    if (fp32)
+        quench_sums_kernel<float><<<nb, 256, 0, stream>>>(Pd, (const float*)st.T, (const float*)st.Y, solid, wgt, red);
+    else
+        quench_sums_kernel<double><<<nb, 256, 0, stream>>>(Pd, (const double*)st.T, (const double*)st.Y, solid, wgt,
+                                                            red);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_quench_seed(const StepParams<double>& Pd, StateView st, bool fp32, const uint8_t* solid,
+                               const double* wgt, double S0, double S1, double J, double seed, double* lam,
+                               double* dtheta, int Q, cudaStream_t stream)
+{
+    const unsigned nb = red_blocks(Pd.ncell);
+    if (fp32)
+        quench_seed_kernel<float><<<nb, 256, 0, stream>>>(Pd, (const float*)st.T, (const float*)st.Y, solid, wgt, S0,
+                                                          S1, J, seed, lam, dtheta, Q);
+    else
+        quench_seed_kernel<double><<<nb, 256, 0, stream>>>(Pd, (const double*)st.T, (const double*)st.Y, solid, wgt,
+                                                           S0, S1, J, seed, lam, dtheta, Q);
+    return cudaGetLastError();
 }
 
 }  // namespace lbfd

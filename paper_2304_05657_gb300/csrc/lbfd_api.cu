@@ -75,6 +75,13 @@ struct lbfd_handle {
     // persistent step: barrier words and the bound of each grid-wide wait
     lbfd::PersistentWait* pwait;
     long long wait_limit_ns;
+    // quenching-distance objective: per-cell wall weights d^-4 (device)
+    double* qwgt;
+    // discrete adjoint: checkpoint interval and the recorded forward run
+    int adj_K;
+    char* adj_ck;      // one state copy per segment (storage precision)
+    int adj_steps, adj_nseg, adj_obj;
+    double adj_J;
 };
 
 namespace {
@@ -242,6 +249,8 @@ void free_handle(lbfd_handle* h)
     if (h->aux) cudaFree(h->aux);
     if (h->wtiles) cudaFree(h->wtiles);
     if (h->pwait) cudaFree(h->pwait);
+    if (h->qwgt) cudaFree(h->qwgt);
+    if (h->adj_ck) cudaFree(h->adj_ck);
     void* curved[] = {h->link_row, h->link_q, h->ghost_row, h->gh_start, h->gh_idx, h->gh_w, h->gval};
     for (void* p : curved)
         if (p) cudaFree(p);
@@ -379,6 +388,7 @@ int lbfd_create(const lbfd_grid* grid, const uint8_t* solid_mask, const lbfd_mec
     h->stream = nullptr;
     h->variant = is_tangent(h->precision) ? 0 : 1;
     h->wait_limit_ns = 2000000000LL;  // 2 s per grid-wide wait of the persistent step
+    h->adj_K = 200;
     const size_t bytes = h->planes * (size_t)h->stride * h->esz;
     for (int b = 0; b < 2; ++b) {
         e = cudaMalloc(&h->buf[b], bytes);
@@ -872,14 +882,133 @@ static StateView view_of(const lbfd_handle* h, void* base)
     return v;
 }
 
-int lbfd_adjoint_gradient(lbfd_handle* h, int steps, int checkpoint_every, int objective, double* value,
-                          double* grad)
+// wall weights of the quenching-distance objective: d^-4 with d the distance
+// (cells, to the wall plane half-way between cells) from a fluid cell to the
+// nearest isothermal boundary along the axis directions: an isothermal solid
+// cell, or the layer beyond an isothermal wall face (periodic axes wrap);
+// 64 cells when there is none that close
+static int quench_weights(lbfd_handle* h)
 {
-    if (!h || steps < 1 || checkpoint_every < 1 || objective != LBFD_OBJ_FLAME_POSITION) return LBFD_EINVAL;
-    if (h->precision != LBFD_FP64 || h->dim != 2 || h->nghost > 0 || h->Pd.curved) return LBFD_ENOTSUP;
-    const int K = checkpoint_every < steps ? checkpoint_every : steps;
+    if (h->qwgt) return LBFD_OK;
+    const int nx = h->grid.nx, ny = h->grid.ny, nz = h->grid.nz, dim = h->dim;
+    const int n[3] = {nx, ny, nz};
+    const int* bc = h->grid.bc;
+    const bool iso_solid = h->prm.solid_isothermal != 0;
+    constexpr int CAP = 64;
+    std::vector<double> w((size_t)h->stride, 0.0);
+    for (long long c = 0; c < h->ncell; ++c) {
+        if (h->mask_host[c]) continue;
+        const int p[3] = {(int)(c % nx), (int)((c / nx) % ny), (int)(c / ((long long)nx * ny))};
+        double d = CAP;
+        for (int a = 0; a < dim; ++a)
+            for (int side = -1; side <= 1; side += 2)
+                for (int j = 1; j <= CAP && j - 0.5 < d; ++j) {
+                    int q[3] = {p[0], p[1], p[2]};
+                    q[a] += side * j;
+                    if (q[a] < 0 || q[a] >= n[a]) {
+                        const int f = 2 * a + (q[a] < 0 ? 0 : 1);
+                        if (bc[f] == LBFD_BC_PERIODIC) {
+                            q[a] = ((q[a] % n[a]) + n[a]) % n[a];
+                        } else {
+                            if (bc[f] == LBFD_BC_WALL_ISOTHERMAL) d = j - 0.5;
+                            break;
+                        }
+                    }
+                    const long long e = (long long)q[0] + (long long)nx * ((long long)q[1] + (long long)ny * q[2]);
+                    if (h->mask_host[e]) {
+                        if (iso_solid) d = j - 0.5;
+                        break;
+                    }
+                }
+        w[c] = 1.0 / (d * d * d * d);
+    }
+    if (cudaMalloc((void**)&h->qwgt, w.size() * sizeof(double)) != cudaSuccess) {
+        h->qwgt = nullptr;
+        return LBFD_ENOMEM;
+    }
+    CK(cudaMemcpy(h->qwgt, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice));
+    return LBFD_OK;
+}
+
+static bool adjoint_precision(const lbfd_handle* h) { return h->precision == LBFD_FP64 || h->precision == LBFD_MIXED; }
+
+static void adjoint_release(lbfd_handle* h)
+{
+    if (h->adj_ck) cudaFree(h->adj_ck);
+    h->adj_ck = nullptr;
+    h->adj_steps = h->adj_nseg = 0;
+}
+
+int lbfd_adjoint_setup(lbfd_handle* h, int checkpoint_every)
+{
+    if (!h || checkpoint_every < 1) return LBFD_EINVAL;
+    h->adj_K = checkpoint_every;
+    return LBFD_OK;
+}
+
+int lbfd_adjoint_record(lbfd_handle* h, int steps, int objective, double* value)
+{
+    if (!h || steps < 1 || (objective != LBFD_OBJ_FLAME_POSITION && objective != LBFD_OBJ_QUENCH_DISTANCE))
+        return LBFD_EINVAL;
+    if (!adjoint_precision(h) || h->dim != 2 || h->nghost > 0 || h->Pd.curved) return LBFD_ENOTSUP;
+    adjoint_release(h);
+    const int K = h->adj_K < steps ? h->adj_K : steps;
     const int nseg = (steps + K - 1) / K;
-    const size_t sbytes = h->planes * (size_t)h->stride * sizeof(double);
+    const size_t sbytes = h->planes * (size_t)h->stride * h->esz;
+    if (objective == LBFD_OBJ_QUENCH_DISTANCE) {
+        const int st = quench_weights(h);
+        if (st != LBFD_OK) return st;
+    }
+    if (cudaMalloc((void**)&h->adj_ck, sbytes * nseg) != cudaSuccess) {
+        h->adj_ck = nullptr;
+        snprintf(g_last_error, sizeof g_last_error, "cudaMalloc(adjoint checkpoints, %zu bytes)", sbytes * nseg);
+        return LBFD_ENOMEM;
+    }
+    // forward pass from the handle's state, one checkpoint per segment
+    for (int g = 0; g < nseg; ++g) {
+        CK(cudaMemcpyAsync(h->adj_ck + (size_t)g * sbytes, h->buf[h->cur], sbytes, cudaMemcpyDeviceToDevice,
+                           h->stream));
+        const int len = steps - g * K < K ? steps - g * K : K;
+        const int st = lbfd_step(h, len);
+        if (st != LBFD_OK) {
+            adjoint_release(h);
+            return st;
+        }
+    }
+    double J = 0.0;
+    if (objective == LBFD_OBJ_FLAME_POSITION) {
+        double d[LBFD_NDIAG];
+        const int dst = lbfd_diagnostics(h, d);
+        if (dst != LBFD_OK) {
+            adjoint_release(h);
+            return dst;
+        }
+        J = d[LBFD_DIAG_XF] * h->prm.dx;
+    } else {
+        double r[2];
+        CK(lbfd::launch_quench_sums(h->Pd, view(h, h->cur), h->precision == LBFD_MIXED, h->solid, h->qwgt, h->red,
+                                    h->stream));
+        CK(cudaMemcpyAsync(r, h->red, sizeof r, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        J = r[1] > 0.0 && r[0] > 0.0 ? pow(r[1] / r[0], -0.25) : 0.0;
+    }
+    h->adj_steps = steps;
+    h->adj_nseg = nseg;
+    h->adj_obj = objective;
+    h->adj_J = J;
+    if (value) *value = J;
+    return LBFD_OK;
+}
+
+int lbfd_adjoint_backward(lbfd_handle* h, double seed, double* grad)
+{
+    if (!h || !grad) return LBFD_EINVAL;
+    if (!h->adj_ck || h->adj_steps < 1) return LBFD_EINVAL;  // nothing recorded
+    const int steps = h->adj_steps, nseg = h->adj_nseg;
+    const int K = h->adj_K < steps ? h->adj_K : steps;
+    const bool fp32 = h->precision == LBFD_MIXED;
+    const size_t sbytes = h->planes * (size_t)h->stride * h->esz;       // a state copy, storage precision
+    const size_t lbytes = h->planes * (size_t)h->stride * sizeof(double);  // an adjoint state, FP64
     const long long nel = (long long)h->planes * h->stride;
     const int planes = (int)h->planes;
     // tape: at most 6 GB, in chunks of cells
@@ -892,7 +1021,7 @@ int lbfd_adjoint_gradient(lbfd_handle* h, int steps, int checkpoint_every, int o
     const long long need = (h->ncell + 63) / 64 * 64;
     w.chunk = chunk < need ? chunk : need;
     const size_t tape = (size_t)w.maxn * w.chunk;
-    char *ck = nullptr, *seg = nullptr;
+    char* seg = nullptr;
     double *lam0 = nullptr, *lam1 = nullptr, *dth = nullptr;
     std::vector<void*> owned;
     auto alloc = [&](void** p, size_t bytes) {
@@ -902,10 +1031,11 @@ int lbfd_adjoint_gradient(lbfd_handle* h, int steps, int checkpoint_every, int o
     };
     auto release = [&]() {
         for (void* p : owned) cudaFree(p);
+        adjoint_release(h);
     };
     cudaError_t e;
-    if ((e = alloc((void**)&ck, sbytes * nseg)) != cudaSuccess || (e = alloc((void**)&seg, sbytes * K)) != cudaSuccess ||
-        (e = alloc((void**)&lam0, sbytes)) != cudaSuccess || (e = alloc((void**)&lam1, sbytes)) != cudaSuccess ||
+    if ((e = alloc((void**)&seg, sbytes * K)) != cudaSuccess || (e = alloc((void**)&lam0, lbytes)) != cudaSuccess ||
+        (e = alloc((void**)&lam1, lbytes)) != cudaSuccess ||
         (e = alloc((void**)&dth, lbfd::NTAN * sizeof(double))) != cudaSuccess ||
         (e = alloc(&w.rin, nel * lbfd::rev_store_bytes())) != cudaSuccess ||
         (e = alloc(&w.rout, nel * lbfd::rev_store_bytes())) != cudaSuccess ||
@@ -930,46 +1060,42 @@ int lbfd_adjoint_gradient(lbfd_handle* h, int steps, int checkpoint_every, int o
     } while (0)
     AK(cudaMemsetAsync(w.flags, 0, 2 * sizeof(int), s));
     AK(cudaMemsetAsync(dth, 0, lbfd::NTAN * sizeof(double), s));
-    // forward pass from the handle's state, one checkpoint per segment
-    for (int g = 0; g < nseg; ++g) {
-        AK(cudaMemcpyAsync(ck + (size_t)g * sbytes, h->buf[h->cur], sbytes, cudaMemcpyDeviceToDevice, s));
-        const int len = steps - g * K < K ? steps - g * K : K;
-        const int st = lbfd_step(h, len);
-        if (st != LBFD_OK) {
-            release();
-            return st;
-        }
-    }
-    // J and its adjoint: x_f = dx sum_fluid Y_F / (Y_F,in * section)
-    double d[LBFD_NDIAG];
-    const int dst = lbfd_diagnostics(h, d);
-    if (dst != LBFD_OK) {
-        release();
-        return dst;
-    }
-    const double scale = h->section > 0.0 ? h->prm.dx / (h->prm.Y_in[h->mech.fuel] * h->section) : 0.0;
-    {
-        std::vector<double> lam((size_t)nel, 0.0);
-        const size_t off = (size_t)(h->Q + 1 + h->mech.fuel) * h->stride;
+    // the adjoint of J with respect to the final state (FP64), times seed
+    AK(cudaMemsetAsync(lam1, 0, lbytes, s));
+    if (h->adj_obj == LBFD_OBJ_FLAME_POSITION) {
+        // x_f = dx sum_fluid Y_F / (Y_F,in * section)
+        const double scale = h->section > 0.0 ? seed * h->prm.dx / (h->prm.Y_in[h->mech.fuel] * h->section) : 0.0;
+        std::vector<double> lam((size_t)h->stride, 0.0);
         for (long long c = 0; c < h->ncell; ++c)
-            if (!h->mask_host[c]) lam[off + c] = scale;
-        AK(cudaMemcpyAsync(lam1, lam.data(), sbytes, cudaMemcpyHostToDevice, s));
+            if (!h->mask_host[c]) lam[c] = scale;
+        AK(cudaMemcpyAsync(lam1 + (size_t)(h->Q + 1 + h->mech.fuel) * h->stride, lam.data(),
+                           (size_t)h->stride * sizeof(double), cudaMemcpyHostToDevice, s));
         AK(cudaStreamSynchronize(s));
+    } else {
+        double r[2];
+        AK(lbfd::launch_quench_sums(h->Pd, view(h, h->cur), fp32, h->solid, h->qwgt, h->red, s));
+        AK(cudaMemcpyAsync(r, h->red, sizeof r, cudaMemcpyDeviceToHost, s));
+        AK(cudaStreamSynchronize(s));
+        if (r[0] > 0.0 && r[1] > 0.0)
+            AK(lbfd::launch_quench_seed(h->Pd, view(h, h->cur), fp32, h->solid, h->qwgt, r[0], r[1], h->adj_J, seed,
+                                        lam1, dth, h->Q, s));
     }
-    // backward pass: each segment recomputed from its checkpoint
+    // backward pass: each segment recomputed from its checkpoint with the
+    // forward kernels (FP32 in the mixed form), every step's adjoint in FP64
     const lbfd::BoundaryLists b = lists(h);
     for (int g = nseg - 1; g >= 0; --g) {
         const int len = steps - g * K < K ? steps - g * K : K;
         for (int j = 0; j < len; ++j)  // every slot starts as the checkpoint (solid cells never change)
-            AK(cudaMemcpyAsync(seg + (size_t)j * sbytes, ck + (size_t)g * sbytes, sbytes, cudaMemcpyDeviceToDevice,
-                               s));
+            AK(cudaMemcpyAsync(seg + (size_t)j * sbytes, h->adj_ck + (size_t)g * sbytes, sbytes,
+                               cudaMemcpyDeviceToDevice, s));
         for (int j = 1; j < len; ++j)
-            AK(lbfd::launch_step(h->dim, 0, h->variant, h->Pd, h->Pf, view_of(h, seg + (size_t)(j - 1) * sbytes),
-                                 view_of(h, seg + (size_t)j * sbytes), h->solid, b, h->side, s));
+            AK(lbfd::launch_step(h->dim, h->precision, h->variant, h->Pd, h->Pf,
+                                 view_of(h, seg + (size_t)(j - 1) * sbytes), view_of(h, seg + (size_t)j * sbytes),
+                                 h->solid, b, h->side, s));
         for (int j = len - 1; j >= 0; --j) {
-            AK(cudaMemsetAsync(lam0, 0, sbytes, s));
-            AK(lbfd::launch_adjoint_step(h->dim, h->Pd, planes, (const double*)(seg + (size_t)j * sbytes), h->solid,
-                                         lam1, lam0, dth, w, s));
+            AK(cudaMemsetAsync(lam0, 0, lbytes, s));
+            AK(lbfd::launch_adjoint_step(h->dim, h->Pd, planes, seg + (size_t)j * sbytes, fp32, h->solid, lam1, lam0,
+                                         dth, w, s));
             std::swap(lam0, lam1);
         }
     }
@@ -981,10 +1107,31 @@ int lbfd_adjoint_gradient(lbfd_handle* h, int steps, int checkpoint_every, int o
 #undef AK
     release();
     if (flags[0]) return LBFD_ENOTSUP;  // a cell's step needs more tape than provided
-    if (value) *value = d[LBFD_DIAG_XF] * h->prm.dx;
-    if (grad)
-        for (int k = 0; k < lbfd::NTAN; ++k) grad[k] = gr[k];
+    for (int k = 0; k < lbfd::NTAN; ++k) grad[k] = gr[k];
     return LBFD_OK;
+}
+
+int lbfd_adjoint_run(lbfd_handle* h, int steps, int objective, double* value, double* grad)
+{
+    const int st = lbfd_adjoint_record(h, steps, objective, value);
+    if (st != LBFD_OK) return st;
+    double g[lbfd::NTAN];
+    const int bt = lbfd_adjoint_backward(h, 1.0, g);
+    if (bt != LBFD_OK) return bt;
+    if (grad)
+        for (int k = 0; k < lbfd::NTAN; ++k) grad[k] = g[k];
+    return LBFD_OK;
+}
+
+int lbfd_adjoint_gradient(lbfd_handle* h, int steps, int checkpoint_every, int objective, double* value,
+                          double* grad)
+{
+    if (!h || checkpoint_every < 1) return LBFD_EINVAL;
+    const int K = h->adj_K;
+    h->adj_K = checkpoint_every;
+    const int st = lbfd_adjoint_run(h, steps, objective, value, grad);
+    h->adj_K = K;
+    return st;
 }
 
 int lbfd_flame_position(lbfd_handle* h, double* x_f, double* mass, double* heat_release)
@@ -1044,15 +1191,30 @@ int lbfd_read_tangent(lbfd_handle* h, int field, int k, double* out)
 int lbfd_gradient(lbfd_handle* h, int objective, double* value, double* grad)
 {
     if (!h || !is_tangent(h->precision) ||
-        (objective != LBFD_OBJ_FLAME_POSITION && objective != LBFD_OBJ_HEAT_RELEASE))
+        (objective != LBFD_OBJ_FLAME_POSITION && objective != LBFD_OBJ_HEAT_RELEASE &&
+         objective != LBFD_OBJ_QUENCH_DISTANCE))
         return LBFD_EINVAL;
-    double r[1 + lbfd::NTAN];
+    if (objective == LBFD_OBJ_QUENCH_DISTANCE) {
+        const int st = quench_weights(h);
+        if (st != LBFD_OK) return st;
+    }
+    double r[2 * (1 + lbfd::NTAN)];
     if (h->precision == LBFD_TANGENT)
-        CK(lbfd::launch_objective(h->Pt, view(h, h->cur), h->solid, objective, h->red, h->stream));
+        CK(lbfd::launch_objective(h->Pt, view(h, h->cur), h->solid, objective, h->qwgt, h->red, h->stream));
     else
-        CK(lbfd::launch_objective(h->Ptf, view(h, h->cur), h->solid, objective, h->red, h->stream));
+        CK(lbfd::launch_objective(h->Ptf, view(h, h->cur), h->solid, objective, h->qwgt, h->red, h->stream));
     CK(cudaMemcpyAsync(r, h->red, sizeof r, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    if (objective == LBFD_OBJ_QUENCH_DISTANCE) {
+        // J = (S1/S0)^(-1/4): dJ = -J/4 (dS1/S1 - dS0/S0)
+        const double S0 = r[0], S1 = r[1 + lbfd::NTAN];
+        const double J = S0 > 0.0 && S1 > 0.0 ? pow(S1 / S0, -0.25) : 0.0;
+        if (value) *value = J;
+        if (grad)
+            for (int k = 0; k < lbfd::NTAN; ++k)
+                grad[k] = S0 > 0.0 && S1 > 0.0 ? -0.25 * J * (r[2 + lbfd::NTAN + k] / S1 - r[1 + k] / S0) : 0.0;
+        return LBFD_OK;
+    }
     double scale = 1.0;
     if (objective == LBFD_OBJ_FLAME_POSITION)  // x_f = dx sum Y_F / (Y_F,in * section)
         scale = h->section > 0.0 ? h->prm.dx / (h->prm.Y_in[h->mech.fuel] * h->section) : 0.0;

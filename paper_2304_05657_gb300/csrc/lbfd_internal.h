@@ -113,10 +113,10 @@ cudaError_t launch_step_tangent(int dim, const StepParams<Tanf>& P, StateView in
                                 cudaStream_t stream);
 cudaError_t launch_tangent_field(bool fp32, long long ncell, long long N, const void* state_base, int plane, int k,
                                  double* out, cudaStream_t stream);
-cudaError_t launch_objective(const StepParams<Tan>& P, StateView st, const uint8_t* solid, int objective, double* red,
-                             cudaStream_t stream);
-cudaError_t launch_objective(const StepParams<Tanf>& P, StateView st, const uint8_t* solid, int objective, double* red,
-                             cudaStream_t stream);
+cudaError_t launch_objective(const StepParams<Tan>& P, StateView st, const uint8_t* solid, int objective,
+                             const double* wgt, double* red, cudaStream_t stream);
+cudaError_t launch_objective(const StepParams<Tanf>& P, StateView st, const uint8_t* solid, int objective,
+                             const double* wgt, double* red, cudaStream_t stream);
 
 // Discrete adjoint of one FP64 step (lbfd_adjoint.cu): scratch of the
 // reverse-mode tape, node k of thread t at k * chunk + t.
@@ -136,9 +136,18 @@ size_t adjoint_node_bytes();
 size_t rev_store_bytes();
 // lam (zeroed by the caller) += (dF/dx)^T lam_next, dtheta += (dF/dtheta)^T
 // lam_next for the step F taken from `state` (planes of N doubles)
-cudaError_t launch_adjoint_step(int dim, const StepParams<double>& Pd, int planes, const double* state,
+cudaError_t launch_adjoint_step(int dim, const StepParams<double>& Pd, int planes, const void* state, bool fp32,
                                 const uint8_t* solid, const double* lam_next, double* lam, double* dtheta,
                                 const AdjointWork& w, cudaStream_t stream);
+// quenching-distance objective J = (S1/S0)^(-1/4), S0 = sum_fluid h,
+// S1 = sum_fluid h w (h the heat release of a cell, w = d^-4 its wall
+// weight): red[0..1] = S0, S1 of state st; and the adjoint seed
+// lam += seed dJ/dstate, dtheta += seed (explicit dJ/dtheta)
+cudaError_t launch_quench_sums(const StepParams<double>& Pd, StateView st, bool fp32, const uint8_t* solid,
+                               const double* wgt, double* red, cudaStream_t stream);
+cudaError_t launch_quench_seed(const StepParams<double>& Pd, StateView st, bool fp32, const uint8_t* solid,
+                               const double* wgt, double S0, double S1, double J, double seed, double* lam,
+                               double* dtheta, int Q, cudaStream_t stream);
 
 // Curved walls (lbfd_geometry.cu): host tables of cut links and ghosts.
 struct CurvedTables {

@@ -78,13 +78,17 @@ cudaError_t launch_tangent_field(bool fp32, long long ncell, long long N, const 
 // parameters' own seeds (A and Ta in the rate) enter too:
 //   0: sum Y_F                                (the flame position up to a constant)
 //   1: sum rho (Q/cp) A dt Y_F Y_O exp(-Ta/T) (total heat release)
-// red[0] = value, red[1 + k] = derivative k; accumulated in FP64.
+//   2: the same heat release, and its sum weighted by the cell's wall
+//      weight wgt (the two sums of the quenching distance)
+// red[0] = value, red[1 + k] = derivative k (objective 2 adds the weighted
+// sum at red[5 + ...]); accumulated in FP64.
 template <typename TT>
 __global__ void __launch_bounds__(256) objective_kernel(StepParams<TT> P, const TT* __restrict__ T,
                                                         const TT* __restrict__ Y, const uint8_t* __restrict__ solid,
-                                                        int objective, double* red)
+                                                        int objective, const double* __restrict__ wgt, double* red)
 {
-    double acc[1 + NTAN] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    constexpr int NV = 1 + NTAN;
+    double acc[2 * NV] = {};
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < P.ncell; c += stride) {
         if (solid[c]) continue;
@@ -102,36 +106,42 @@ __global__ void __launch_bounds__(256) objective_kernel(StepParams<TT> P, const 
         acc[0] += (double)j.v;
 #pragma unroll
         for (int k = 0; k < NTAN; ++k) acc[1 + k] += (double)j.d[k];
+        if (objective == 2) {
+            const double w = wgt[c];
+            acc[NV] += w * (double)j.v;
+#pragma unroll
+            for (int k = 0; k < NTAN; ++k) acc[NV + 1 + k] += w * (double)j.d[k];
+        }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
-        for (int k = 0; k < 1 + NTAN; ++k) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], off);
+        for (int k = 0; k < 2 * NV; ++k) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], off);
     if ((threadIdx.x & 31) == 0)
 #pragma unroll
-        for (int k = 0; k < 1 + NTAN; ++k) atomicAdd(&red[k], acc[k]);
+        for (int k = 0; k < 2 * NV; ++k) atomicAdd(&red[k], acc[k]);
 }
 
 template <typename TT>
-static cudaError_t objective(const StepParams<TT>& P, StateView st, const uint8_t* solid, int obj, double* red,
-                             cudaStream_t stream)
+static cudaError_t objective(const StepParams<TT>& P, StateView st, const uint8_t* solid, int obj, const double* wgt,
+                             double* red, cudaStream_t stream)
 {
-    cudaError_t e = cudaMemsetAsync(red, 0, (1 + NTAN) * sizeof(double), stream);
+    cudaError_t e = cudaMemsetAsync(red, 0, 2 * (1 + NTAN) * sizeof(double), stream);
     if (e != cudaSuccess) return e;
     long long want = (P.ncell + 255) / 256;
     const unsigned blocks = (unsigned)(want < 1024 ? (want > 0 ? want : 1) : 1024);
-    objective_kernel<TT><<<blocks, 256, 0, stream>>>(P, (const TT*)st.T, (const TT*)st.Y, solid, obj, red);
+    objective_kernel<TT><<<blocks, 256, 0, stream>>>(P, (const TT*)st.T, (const TT*)st.Y, solid, obj, wgt, red);
     return cudaGetLastError();
 }
-cudaError_t launch_objective(const StepParams<Tan>& P, StateView st, const uint8_t* solid, int obj, double* red,
-                             cudaStream_t stream)
+cudaError_t launch_objective(const StepParams<Tan>& P, StateView st, const uint8_t* solid, int obj, const double* wgt,
+                             double* red, cudaStream_t stream)
 {
-    return objective(P, st, solid, obj, red, stream);
+    return objective(P, st, solid, obj, wgt, red, stream);
 }
-cudaError_t launch_objective(const StepParams<Tanf>& P, StateView st, const uint8_t* solid, int obj, double* red,
-                             cudaStream_t stream)
+cudaError_t launch_objective(const StepParams<Tanf>& P, StateView st, const uint8_t* solid, int obj, const double* wgt,
+                             double* red, cudaStream_t stream)
 {
-    return objective(P, st, solid, obj, red, stream);
+    return objective(P, st, solid, obj, wgt, red, stream);
 }
 
 }  // namespace lbfd

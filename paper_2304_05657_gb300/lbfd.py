@@ -21,7 +21,7 @@ OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, EUNSTABLE, ENOTSUP = range(8)
 BC = {"periodic": 0, "wall_adiabatic": 1, "wall_isothermal": 2, "inlet": 3, "outlet": 4, "outlet_pressure": 5}
 FP64, MIXED, TANGENT, TANGENT_MIXED = 0, 1, 2, 3
 PRECISION = {"fp64": FP64, "mixed": MIXED, "tangent": TANGENT, "tangent_mixed": TANGENT_MIXED}
-OBJ_FLAME_POSITION, OBJ_HEAT_RELEASE = 0, 1
+OBJ_FLAME_POSITION, OBJ_HEAT_RELEASE, OBJ_QUENCH_DISTANCE = 0, 1, 2
 THETA = ("ln_A", "Ta", "T_wall", "u_in")
 NSP = 5
 FIELD_T, FIELD_Y0, FIELD_UX, FIELD_UY, FIELD_UZ, FIELD_PH, FIELD_RHO, FIELD_HRR, FIELD_G0 = 0, 1, 6, 7, 8, 9, 10, 11, 16
@@ -36,7 +36,8 @@ SYMBOLS = (
     "lbfd_last_error", "lbfd_step_graph", "lbfd_num_variants", "lbfd_get_variant", "lbfd_set_variant",
     "lbfd_autotune", "lbfd_diagnostics_noalloc", "lbfd_launches_per_step", "lbfd_read_tangent", "lbfd_gradient",
     "lbfd_diagnostics_rows", "lbfd_set_inlet_velocity", "lbfd_set_curved_walls", "lbfd_read_cells",
-    "lbfd_adjoint_gradient", "lbfd_step_persistent", "lbfd_set_wait_limit",
+    "lbfd_adjoint_gradient", "lbfd_step_persistent", "lbfd_set_wait_limit", "lbfd_adjoint_setup",
+    "lbfd_adjoint_record", "lbfd_adjoint_backward", "lbfd_adjoint_run",
 )
 
 
@@ -119,6 +120,10 @@ def load(path: str = LIB_PATH):
     lib.lbfd_set_curved_walls.argtypes = [H, ctypes.c_int, D]
     lib.lbfd_gradient.argtypes = [H, ctypes.c_int, D, D]
     lib.lbfd_adjoint_gradient.argtypes = [H, ctypes.c_int, ctypes.c_int, ctypes.c_int, D, D]
+    lib.lbfd_adjoint_setup.argtypes = [H, ctypes.c_int]
+    lib.lbfd_adjoint_record.argtypes = [H, ctypes.c_int, ctypes.c_int, D]
+    lib.lbfd_adjoint_backward.argtypes = [H, ctypes.c_double, D]
+    lib.lbfd_adjoint_run.argtypes = [H, ctypes.c_int, ctypes.c_int, D, D]
     lib.lbfd_autotune.argtypes = [H, ctypes.c_int, D, ctypes.POINTER(ctypes.c_int)]
     lib.lbfd_diagnostics_noalloc.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Mechanism), ctypes.POINTER(Params),
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong,
@@ -262,6 +267,29 @@ class Solver:
         st = self.lib.lbfd_adjoint_gradient(self.h, int(steps), int(checkpoint_every), int(objective), _dp(val),
                                             _dp(grad))
         _check(self.lib, st, "lbfd_adjoint_gradient")
+        return float(val[0]), grad
+
+    def adjoint_setup(self, checkpoint_every: int):
+        _check(self.lib, self.lib.lbfd_adjoint_setup(self.h, int(checkpoint_every)), "lbfd_adjoint_setup")
+
+    def adjoint_record(self, steps: int, objective: int = OBJ_FLAME_POSITION) -> float:
+        """Advance `steps` steps keeping checkpoints; J of the final state."""
+        val = np.zeros(1)
+        _check(self.lib, self.lib.lbfd_adjoint_record(self.h, int(steps), int(objective), _dp(val)),
+               "lbfd_adjoint_record")
+        return float(val[0])
+
+    def adjoint_backward(self, seed: float = 1.0) -> np.ndarray:
+        """seed * dJ/dtheta by the backward sweep over the recorded steps."""
+        grad = np.zeros(4)
+        _check(self.lib, self.lib.lbfd_adjoint_backward(self.h, float(seed), _dp(grad)), "lbfd_adjoint_backward")
+        return grad
+
+    def adjoint_run(self, steps: int, objective: int = OBJ_FLAME_POSITION):
+        val = np.zeros(1)
+        grad = np.zeros(4)
+        _check(self.lib, self.lib.lbfd_adjoint_run(self.h, int(steps), int(objective), _dp(val), _dp(grad)),
+               "lbfd_adjoint_run")
         return float(val[0]), grad
 
     @property

@@ -156,3 +156,80 @@ def test_adjoint_matches_the_cpu_adjoint_and_central_differences(lbfd_lib):
     fd = central_fd(lambda t: J_gpu(cfg, solid, T, Y, t, lbfd.OBJ_FLAME_POSITION), theta)
     for k, name in enumerate(lbfd.THETA):
         assert abs(gg[k] - fd[k]) <= 1e-4 * abs(fd[k]), (name, gg[k], fd[k])
+
+
+def quench_case():
+    cfg, solid, T, Y = inputs.channel(nx=40, ny=12, walls="isothermal", T_wall=350.0, u_in=0.004)
+    T, Y = inputs.ignition_fields(cfg, solid, 10, 30, burnt=False)
+    return cfg, solid, T, Y
+
+
+def test_quench_distance_tangent_adjoint_cpu_and_fd(lbfd_lib):
+    """The quenching-distance objective: the FP64 tangent, the GPU adjoint and
+    the CPU adjoint agree (1e-8 relative per component; J to 1e-12), and all
+    match central differences of the FP64 GPU step (1e-4)."""
+    from oracle import adjoint
+
+    cfg, solid, T, Y = quench_case()
+    steps = 40
+    Jt, gt = grad.run_tangent(cfg, solid, T, Y, steps, lbfd.OBJ_QUENCH_DISTANCE)
+    Ja, ga = grad.run_tangent(cfg, solid, T, Y, steps, lbfd.OBJ_QUENCH_DISTANCE, precision="adjoint",
+                              checkpoint_every=9)
+    Jc, gc = adjoint.adjoint_gradient(cfg, solid, T, Y, steps, objective="quench_distance")
+    assert abs(Jt - Jc) <= 1e-12 * Jc and abs(Ja - Jc) <= 1e-12 * Jc, (Jt, Ja, Jc)
+    for k, name in enumerate(lbfd.THETA):
+        assert abs(ga[k] - gc[k]) <= 1e-8 * abs(gc[k]), (name, ga[k], gc[k])
+        assert abs(gt[k] - gc[k]) <= 1e-8 * abs(gc[k]), (name, gt[k], gc[k])
+
+    def J_gpu_q(theta):
+        c = grad.apply_theta(cfg, theta)
+        c["precision"] = "tangent"
+        s = lbfd.Solver(c, solid)
+        s.init_fields(T, Y)
+        s.step(steps)
+        J, _ = s.gradient(lbfd.OBJ_QUENCH_DISTANCE)
+        s.close()
+        return J
+
+    fd = central_fd(J_gpu_q, grad.theta_of(cfg))
+    for k, name in enumerate(lbfd.THETA):
+        assert abs(ga[k] - fd[k]) <= 1e-4 * abs(fd[k]), (name, ga[k], fd[k])
+
+
+@pytest.mark.parametrize("objective", [lbfd.OBJ_FLAME_POSITION, lbfd.OBJ_QUENCH_DISTANCE])
+def test_mixed_forward_adjoint_matches_fp64_adjoint(lbfd_lib, objective):
+    """FP32 forward pass (the mixed kernels, FP64 Arrhenius above 1000 K),
+    adjoint and gradient in FP64 at that trajectory: within 2e-3 of the FP64
+    adjoint per component (FP32 rounding of the trajectory, as for the mixed
+    tangent form), J within 1e-5."""
+    cfg, solid, T, Y = case() if objective == lbfd.OBJ_FLAME_POSITION else quench_case()
+    J, g = grad.run_tangent(cfg, solid, T, Y, STEPS, objective, precision="adjoint", checkpoint_every=40)
+    Jm, gm = grad.run_tangent(cfg, solid, T, Y, STEPS, objective, precision="adjoint_mixed", checkpoint_every=40)
+    assert abs(Jm - J) <= 1e-5 * abs(J), (Jm, J)
+    for k, name in enumerate(lbfd.THETA):
+        assert abs(gm[k] - g[k]) <= 2e-3 * abs(g[k]), (name, gm[k], g[k])
+
+
+def test_adjoint_record_backward_and_autograd(lbfd_lib):
+    """The forward/backward split: backward with seed s gives s dJ/dtheta;
+    backward without a record is EINVAL; FlameObjective with the adjoint
+    keeps only checkpoints in forward and sweeps in backward."""
+    torch = pytest.importorskip("torch")
+    cfg, solid, T, Y = case()
+    steps = 60
+    J1, g1 = grad.run_tangent(cfg, solid, T, Y, steps, precision="adjoint", checkpoint_every=25)
+    s = grad.adjoint_solver(cfg, solid, T, Y, None, 25)
+    J2 = s.adjoint_record(steps)
+    g2 = s.adjoint_backward(-3.0)
+    assert J2 == J1 and np.allclose(g2, -3.0 * g1, rtol=1e-12, atol=0)
+    with pytest.raises(lbfd.LbfdError) as err:
+        s.adjoint_backward(1.0)  # the record was consumed
+    assert err.value.status == lbfd.EINVAL
+    s.close()
+    for prec in ("adjoint", "adjoint_mixed"):
+        theta = torch.tensor(grad.theta_of(cfg), dtype=torch.float64, requires_grad=True)
+        J = grad.FlameObjective.apply(theta, cfg, solid, T, Y, steps, lbfd.OBJ_FLAME_POSITION, prec, 25)
+        (2.0 * J).backward()
+        tol = 1e-12 if prec == "adjoint" else 2e-3
+        assert abs(J.item() - J1) <= (1e-14 if prec == "adjoint" else 1e-5) * abs(J1)
+        assert np.allclose(theta.grad.numpy(), 2.0 * g1, rtol=tol, atol=0), (prec, theta.grad, g1)

@@ -108,3 +108,61 @@ def test_adjoint_with_solids_and_the_eq32_outlet(oracle_mod):
     Jo, fd = central_fd_oracle(oracle_mod, cfg, solid, T, Y, steps)
     assert abs(J - Jo) <= 1e-13 * abs(Jo)
     assert np.all(np.abs(g - fd) <= 1e-5 * np.abs(fd)), (g, fd)
+
+
+def test_quench_distance_objective_closed_form():
+    """Only the cells of one row react (the others are cold): the soft
+    minimum of the wall distance is that row's distance to the nearest cold
+    wall, half-way between cells: row y of an isothermal channel of height
+    H is min(y + 1/2, H - y - 1/2) from the walls."""
+    from oracle import adjoint
+
+    nx, ny = 20, 11
+    cfg = inputs.base_config(dim=2, nx=nx, ny=ny, bc=["inlet", "outlet_pressure", "wall_isothermal",
+                                                      "wall_isothermal", "periodic", "periodic"])
+    solid = np.zeros((ny, nx), np.uint8)
+    st = adjoint.Step(cfg, solid)
+    for row in (0, 3, 5, 8):
+        T = np.full(nx * ny, 300.0)
+        T.reshape(ny, nx)[row, :] = 1800.0
+        Y = np.tile(np.asarray(cfg["Y_in"])[:, None], (1, nx * ny))
+        J = float(st.quench_distance(torch.as_tensor(T), torch.as_tensor(Y), st.theta0()))
+        d = min(row + 0.5, ny - row - 0.5)
+        # the cold rows' rate exp(-Ta/300) / exp(-Ta/1800) ~ 1e-18 contributes nothing measurable
+        assert abs(J - d) <= 1e-9 * d, (row, J, d)
+    # a solid block: distance to the nearest solid cell along the axes
+    solid[5, 10] = 1
+    st2 = adjoint.Step(dict(cfg, bc=["periodic"] * 6), solid)
+    c = 5 * nx + 7
+    assert st2.geo.wall_distance[list(st2.geo.fluid).index(c)] == 2.5
+
+
+def test_quench_adjoint_equals_central_differences_of_the_c_oracle(oracle_mod):
+    """The quenching-distance objective of the C oracle's final state
+    (evaluated by the objective pinned above), differentiated by central
+    differences, against the reverse accumulation: 1e-4 (measured 3e-5)."""
+    from oracle import adjoint
+
+    cfg, solid, T, Y = inputs.channel(nx=40, ny=12, walls="isothermal", T_wall=350.0, u_in=0.004)
+    T, Y = inputs.ignition_fields(cfg, solid, 10, 30, burnt=False)
+    steps = 40
+    J, g = adjoint.adjoint_gradient(cfg, solid, T, Y, steps, objective="quench_distance")
+
+    def Jq(theta):
+        c = grad.apply_theta(cfg, theta)
+        o = oracle_mod.Sim(c, solid)
+        o.set_state(T, Y)
+        o.step(steps)
+        To, Yo, _ = o.get_state()
+        st = adjoint.Step(c, solid)
+        return float(st.quench_distance(torch.as_tensor(To), torch.as_tensor(Yo), st.theta0()))
+
+    th = grad.theta_of(cfg)
+    assert abs(J - Jq(th)) <= 1e-12 * abs(J)
+    for k in range(4):
+        h = 1e-4 if k == 0 else 1e-4 * abs(th[k])
+        tp, tm = th.copy(), th.copy()
+        tp[k] += h
+        tm[k] -= h
+        fd = (Jq(tp) - Jq(tm)) / (2 * h)
+        assert abs(g[k] - fd) <= 1e-4 * abs(fd), (k, g[k], fd)
