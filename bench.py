@@ -400,6 +400,32 @@ def gradient_rate(args):
     out["adjoint_grad_steps_per_s"] = S / (time.perf_counter() - t0)
     s.close()
     out["adjoint_vs_fp64_step_time"] = out["fp64_steps_per_s"] / out["adjoint_grad_steps_per_s"]
+    # the same with the FP32 forward pass (mixed kernels), adjoint in FP64
+    s = lbfd.Solver(dict(cfg, precision="mixed"), solid, stream=stream)
+    s.init_fields(T, Y)
+    s.autotune(reps=5)
+    s.init_fields(T, Y)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Jm, gm = s.adjoint_gradient(S, K)
+    torch.cuda.synchronize()
+    out["adjoint_mixed_grad_steps_per_s"] = S / (time.perf_counter() - t0)
+    s.close()
+    # against the FP64 CPU adjoint of the oracle on a bounded sample: the
+    # first 10 steps of the same case
+    from oracle import adjoint as cpu_adjoint
+
+    ns = 10
+    s = lbfd.Solver(dict(cfg, precision="fp64"), solid, stream=stream)
+    s.init_fields(T, Y)
+    _, g10 = s.adjoint_gradient(ns, 5)
+    s.close()
+    t0 = time.perf_counter()
+    _, c10 = cpu_adjoint.adjoint_gradient(cfg, solid, T, Y, ns, checkpoint_every=5)
+    out["cpu_adjoint"] = {"steps": ns, "seconds": time.perf_counter() - t0,
+                          "gpu_adjoint_vs_cpu_adjoint_max_rel": float(np.max(np.abs(g10 - c10) / np.abs(c10))),
+                          "sample": "the first 10 steps of the same case (torch autograd through the FP64 "
+                                    "restatement of the step, CPU)"}
 
     def J_fp64(theta):
         c = grad.apply_theta(cfg, theta)
@@ -426,7 +452,48 @@ def gradient_rate(args):
     out["adjoint_vs_fd_max_rel"] = float(np.max(np.abs(ga - fd) / np.abs(fd)))
     out["adjoint_vs_tangent_max_rel"] = float(np.max(np.abs(ga - gt) / np.abs(gt)))
     out["tangent_mixed_vs_fp64_max_rel"] = float(np.max(np.abs(grads["tangent_mixed"] - gt) / np.abs(gt)))
+    out["adjoint_mixed_vs_fp64_adjoint_max_rel"] = float(np.max(np.abs(np.asarray(gm) - ga) / np.abs(ga)))
     out["J_m"] = Ja
+    return out
+
+
+def flame_speed_accuracy():
+    """Flame speed S_F = u_in - dx_f/dt (x_f sampled every 50 steps over
+    steps 1000-2000, least-squares slope) of the 256x32 adiabatic channel
+    ignited at the inlet: the mixed and FP64 GPU forms against the FP64
+    oracle (all host cores)."""
+    import oracle
+
+    from paper_2304_05657_gb300 import lbfd
+
+    cfg, solid, T, Y = inputs.channel(nx=256, ny=32)
+    T, Y = inputs.ignition_fields(cfg, solid, 0, 20, burnt=False)
+
+    def history(sim, step, diag):
+        step(sim, 1000)
+        ts, xs = [], []
+        for i in range(21):
+            ts.append(50 * i)
+            xs.append(diag(sim))
+            if i < 20:
+                step(sim, 50)
+        return cfg["u_in"] - np.polyfit(ts, xs, 1)[0]
+
+    oracle.build()
+    used = oracle.set_threads(os.cpu_count() or 1)
+    o = oracle.Sim(cfg, solid)
+    o.set_state(T, Y)
+    So = history(o, lambda m, n: m.step(n), lambda m: m.diagnostics()["x_f"])
+    oracle.set_threads(1)
+    out = {"workload": "D2Q9 channel 256x32, adiabatic walls, unburnt mixture at 2000 K in columns 0-19",
+           "S_F_oracle": So, "oracle_threads": used}
+    for prec in ("mixed", "fp64"):
+        s = lbfd.Solver(dict(cfg, precision=prec), solid)
+        s.init_fields(T, Y)
+        Sg = history(s, lambda m, n: m.step_graph(n), lambda m: m.diagnostics()["x_f"])
+        s.close()
+        out[f"S_F_{prec}"] = Sg
+        out[f"{prec}_rel_err"] = abs(Sg - So) / abs(So)
     return out
 
 
@@ -519,6 +586,26 @@ def secondary(args, flush):
         s.step(1)
     best, _ = s.autotune(reps=10)
     ms = timed_steps(s, flush, stream, args.secondary_steps)
+    # the channel study itself (Sec. IV.A): flame speed of every channel from
+    # the slope of its flame position over 2000 more steps, burning flags,
+    # quenching width and the dead-zone thickness
+    from paper_2304_05657_gb300 import channels
+
+    seg = inputs.batched_channels()[4]
+    tr = channels.FlameSpeedTracker(segments=seg)
+    for n in range(0, 2001, 200):
+        if n:
+            s.step_graph(200)
+        tr.record(s, n)
+    widths = [y1 - y0 for y0, y1 in seg]
+    burning = tr.burning()
+    study = {"widths": widths, "S_F": [float(v) for v in tr.flame_speed(window=11)],
+             "burning": [bool(b) for b in burning],
+             "quenching_width": channels.quenching_width(widths, burning),
+             "delta_dead": channels.channel_dead_zones(s, seg),
+             "note": "lattice units (cells, cells per step), after 10 000 + warm-up + timed steps; S_F = u_in - "
+                     "dx_f/dt fitted over 2000 steps; delta_dead: smallest wall distance of the per-column "
+                     "peak heat release over the columns within 10 % of the channel's peak"}
     fluid = int((solid == 0).sum())
     mean_s = float(ms.mean()) * 1e-3
     alg = fluid * bytes_per_cell(cfg) + (solid.size - fluid)
@@ -528,7 +615,21 @@ def secondary(args, flush):
            "launches_per_step": s.launches_per_step, "prerun_steps": 10000,
            "roofline": {"bound": "hbm", "achieved": alg / mean_s / 1e9, "peak": peaks()[0], "unit": "GB/s",
                         "frac": alg / mean_s / 1e9 / peaks()[0], "traffic": traffic,
-                        "algorithmic_bytes_per_step": alg}}
+                        "algorithmic_bytes_per_step": alg},
+           "channel_study": study}
+    # the same steps in one persistent launch (grid-wide barriers between steps)
+    for _ in range(3):
+        s.step(1)
+    s.step_persistent(10)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step_persistent(args.secondary_steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    tp = e0.elapsed_time(e1) / args.secondary_steps
+    out["persistent"] = {"ms_per_step": tp, "value": fluid / (tp * 1e-3) / 1e6, "unit": "MLUPS",
+                         "launches": 1, "steps": args.secondary_steps, "l2": "not flushed between steps"}
     s.close()
     return out
 
@@ -664,6 +765,8 @@ def run_ours(args):
         line["fp64_form"] = fp64_form(args, flush, (cfg, solid, T, Y))
     if extra and args.secondary_steps > 0 and args.workload != "batched16x1024":
         line["secondary"] = secondary(args, flush)
+    if extra and not args.no_baseline:
+        line["flame_speed_accuracy"] = flame_speed_accuracy()
     if extra and args.grad_steps > 0:
         line["gradient"] = gradient_rate(args)
     if rank == 0:

@@ -274,6 +274,19 @@ int lbfd_diagnostics(lbfd_handle* h, double* out);
  * y = (y0 + y1)/2.  EINVAL unless 0 <= y0 < y1 <= ny. */
 int lbfd_diagnostics_rows(lbfd_handle* h, int y0, int y1, double* out);
 
+/* Reaction front per column, for the dead zone of Sec. IV.A (2-D,
+ * LBFD_FP64 or LBFD_MIXED): for every column x, the peak of LBFD_FIELD_HRR
+ * over the fluid cells of rows y0 <= y < y1 (one channel of a packed batch)
+ * into host peak[nx] (0 for a column without fluid there), and the distance
+ * from that cell's centre to the nearer edge of the row band (the walls lie
+ * half-way between cells: min(y - y0 + 1/2, y1 - 1/2 - y); the smallest y
+ * on ties) into host wall_distance[nx].  The dead-zone thickness delta_dead
+ * is the smallest such distance over the columns where the front burns
+ * (channels.py takes the columns whose peak is at least 10 % of the
+ * channel's largest).  Synchronises.  EINVAL unless 0 <= y0 < y1 <= ny;
+ * ENOTSUP in 3-D and the tangent precisions. */
+int lbfd_column_peaks(lbfd_handle* h, int y0, int y1, double* peak, double* wall_distance);
+
 /* Change the inlet velocity of subsequent steps (the flow rate control that
  * holds a flame in place, Sec. IV.A).  EUNSTABLE if |u_in| >= cs.  A
  * captured step graph is re-captured at its next use. */

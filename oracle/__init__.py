@@ -93,6 +93,7 @@ def _load():
         lib.orc_central_moments.argtypes = [P, D, D, D]
         lib.orc_central_moments_inverse.argtypes = [P, D, D, D]
         lib.orc_diagnostics.argtypes = [P, D]
+        lib.orc_column_peaks.argtypes = [P, ctypes.c_int, ctypes.c_int, D, D]
         lib.orc_cumulants.argtypes = [ctypes.c_int, D, D]
         lib.orc_cumulants_inverse.argtypes = [ctypes.c_int, D, D]
         lib.orc_weno3.restype = ctypes.c_double
@@ -243,6 +244,15 @@ class Sim:
         f = np.zeros(self.Q)
         self.lib.orc_central_moments_inverse(self.h, _dp(Pi), _dp(u), _dp(f))
         return f
+
+    def column_peaks(self, rows=None):
+        """Per column: the peak heat release over rows y0 <= y < y1 and its
+        distance to the nearer edge of the band (2-D)."""
+        y0, y1 = rows if rows is not None else (0, self.cfg["ny"])
+        peak = np.zeros(self.cfg["nx"])
+        dist = np.zeros(self.cfg["nx"])
+        self.lib.orc_column_peaks(self.h, int(y0), int(y1), _dp(peak), _dp(dist))
+        return peak, dist
 
     def diagnostics(self) -> dict:
         out = np.zeros(8)

@@ -1325,3 +1325,30 @@ void orc_diagnostics(const orc_sim *S, double *out)
     out[6] = nonfinite;
     out[7] = nfluid;
 }
+
+/* Reaction front per column (the dead zone of Sec. IV.A), 2-D: for every
+ * column x, the largest heat release rho (Q/cp) q over the fluid cells of
+ * rows y0 <= y < y1 into peak[x] (0 when there is none) and the distance of
+ * that cell's centre from the nearer edge of the row band, walls half-way
+ * between cells, into dist[x]; ties go to the smallest y. */
+void orc_column_peaks(const orc_sim *S, int y0, int y1, double *peak, double *dist)
+{
+    long N = S->N;
+    for (int x = 0; x < S->s.nx; ++x) {
+        double best = -1.0;
+        int by = y0;
+        for (int y = y0; y < y1; ++y) {
+            int p[3] = {x, y, 0};
+            long c = cell_index(S, p);
+            if (S->solid[c]) continue;
+            double Y[ORC_MAXSP];
+            for (int k = 0; k < S->nsp; ++k) Y[k] = S->Y[(long)k * N + c];
+            double rho = eos_rho(S, S->T[c], inv_molar_mass(S, Y));
+            double h = rho * S->s.Q / S->s.cp * rate_q(S, S->T[c], Y);
+            if (h > best) { best = h; by = y; }
+        }
+        double d0 = by - y0 + 0.5, d1 = y1 - 0.5 - by;
+        peak[x] = best < 0.0 ? 0.0 : best;
+        dist[x] = d0 < d1 ? d0 : d1;
+    }
+}

@@ -53,6 +53,25 @@ class FlameSpeedTracker:
         return h > rel * max(h.max(), 1e-300)
 
 
+def dead_zone(peak, wall_distance, rel: float = 0.1) -> float:
+    """Dead-zone thickness delta_dead of one channel (Sec. IV.A): the
+    smallest distance between the reaction front (the peak heat release of
+    each column across the channel) and a wall, over the columns where the
+    front burns (peak >= rel x the channel's largest); nan when nothing
+    burns.  Inputs: the two arrays of lbfd_column_peaks for the channel."""
+    peak = np.asarray(peak, dtype=np.float64)
+    top = peak.max() if peak.size else 0.0
+    if not top > 0.0:
+        return float("nan")
+    sel = peak >= rel * top
+    return float(np.asarray(wall_distance, dtype=np.float64)[sel].min())
+
+
+def channel_dead_zones(solver, segments, rel: float = 0.1) -> list:
+    """delta_dead [cells] of every channel (segments = [(y0, y1), ...])."""
+    return [dead_zone(*solver.column_peaks(seg), rel=rel) for seg in segments]
+
+
 def quenching_width(widths, burning) -> float:
     """Smallest width that still burns, given per-channel burning flags of
     channels sorted by width (nan if none burns)."""

@@ -845,6 +845,29 @@ int lbfd_diagnostics_rows(lbfd_handle* h, int y0, int y1, double* out)
     return u[5] ? LBFD_ENONFINITE : LBFD_OK;
 }
 
+int lbfd_column_peaks(lbfd_handle* h, int y0, int y1, double* peak, double* wall_distance)
+{
+    if (!h || !peak || !wall_distance || y0 < 0 || y1 > h->grid.ny || y0 >= y1) return LBFD_EINVAL;
+    if (h->dim != 2 || (h->precision != LBFD_FP64 && h->precision != LBFD_MIXED)) return LBFD_ENOTSUP;
+    const int nx = h->grid.nx;
+    double* out = h->tmp;
+    double* own = nullptr;
+    if (h->ncell < 2LL * nx) {  // a one-row grid: tmp holds nx values only
+        if (cudaMalloc((void**)&own, 2 * (size_t)nx * sizeof(double)) != cudaSuccess) return LBFD_ENOMEM;
+        out = own;
+    }
+    std::vector<double> r(2 * (size_t)nx);
+    cudaError_t e = lbfd::launch_column_peaks(h->precision, h->Pd, view(h, h->cur), h->solid, y0, y1, out, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(r.data(), out, r.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (own) cudaFree(own);
+    if (e != cudaSuccess) return cuda_fail(e, "column peaks");
+    memcpy(peak, r.data(), (size_t)nx * sizeof(double));
+    memcpy(wall_distance, r.data() + nx, (size_t)nx * sizeof(double));
+    return LBFD_OK;
+}
+
 int lbfd_diagnostics(lbfd_handle* h, double* out)
 {
     if (!h) return LBFD_EINVAL;

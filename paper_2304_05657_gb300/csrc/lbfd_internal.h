@@ -97,6 +97,12 @@ void boundary_cells(int dim, int nx, int ny, int nz, const int* bc, const uint8_
 cudaError_t launch_diagnostics(int dim, int precision, const StepParams<double>& Pd, StateView st,
                                const uint8_t* solid, int y0, int y1, double* red, cudaStream_t stream);
 
+// Column peaks of the heat release over rows y0 <= y < y1 of a 2-D grid
+// (FP64 or mixed state): out[x] = peak, out[nx + x] = its distance to the
+// nearer band edge (device, 2 nx doubles).
+cudaError_t launch_column_peaks(int precision, const StepParams<double>& P, StateView st, const uint8_t* solid,
+                                int y0, int y1, double* out, cudaStream_t stream);
+
 // Derived or raw field of every cell into double out[ncell] (device).
 cudaError_t launch_field(int dim, int precision, const StepParams<double>& Pd, StateView st,
                          const uint8_t* solid, int field, double* out, cudaStream_t stream);

@@ -211,6 +211,54 @@ cudaError_t launch_diagnostics(int dim, int precision, const StepParams<double>&
                     : diag_launch<3, float>(P, st, solid, y0, y1, red, stream);
 }
 
+// Per column x of a 2-D grid: the peak heat release over the fluid cells of
+// rows y0 <= y < y1 (the reaction front where it crosses the column, Sec.
+// IV.A) and the distance of that cell's centre to the nearer edge of the
+// row band (walls half-way between cells): out[x] = peak (0 when the column
+// has no fluid cell there), out[nx + x] = distance (smallest y on ties).
+template <typename S>
+__global__ void __launch_bounds__(256) column_peaks_kernel(StepParams<double> P, const S* __restrict__ T,
+                                                           const S* __restrict__ Y,
+                                                           const uint8_t* __restrict__ solid, int y0, int y1,
+                                                           double* __restrict__ out)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= P.nx) return;
+    double best = -1.0;
+    int by = y0;
+    for (int y = y0; y < y1; ++y) {
+        const long long c = (long long)x + (long long)P.nx * y;
+        if (solid[c]) continue;
+        double Yc[NSP];
+#pragma unroll
+        for (int k = 0; k < NSP; ++k) Yc[k] = val(Y[(long long)k * P.N + c]);
+        double rho, q;
+        const double h = hrr_of<S>(P, val(T[c]), Yc, &rho, &q);
+        if (h > best) {
+            best = h;
+            by = y;
+        }
+    }
+    const double d0 = by - y0 + 0.5, d1 = y1 - 0.5 - by;
+    out[x] = best < 0.0 ? 0.0 : best;
+    out[P.nx + x] = d0 < d1 ? d0 : d1;
+}
+
+cudaError_t launch_column_peaks(int precision, const StepParams<double>& P, StateView st, const uint8_t* solid,
+                                int y0, int y1, double* out, cudaStream_t stream)
+{
+    const unsigned nb = (unsigned)((P.nx + 255) / 256);
+    if (precision == 0)
+        column_peaks_kernel<double><<<nb, 256, 0, stream>>>(P, (const double*)st.T, (const double*)st.Y, solid, y0,
+                                                            y1, out);
+    else if (precision == 1)
+        column_peaks_kernel<float><<<nb, 256, 0, stream>>>(P, (const float*)st.T, (const float*)st.Y, solid, y0, y1,
+                                                           out);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
 // field ids follow include/lbfd.h
 template <int DIM, typename S>
 __global__ void __launch_bounds__(256) field_kernel(StepParams<double> P, const S* __restrict__ g,

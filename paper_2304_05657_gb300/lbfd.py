@@ -37,7 +37,7 @@ SYMBOLS = (
     "lbfd_autotune", "lbfd_diagnostics_noalloc", "lbfd_launches_per_step", "lbfd_read_tangent", "lbfd_gradient",
     "lbfd_diagnostics_rows", "lbfd_set_inlet_velocity", "lbfd_set_curved_walls", "lbfd_read_cells",
     "lbfd_adjoint_gradient", "lbfd_step_persistent", "lbfd_set_wait_limit", "lbfd_adjoint_setup",
-    "lbfd_adjoint_record", "lbfd_adjoint_backward", "lbfd_adjoint_run",
+    "lbfd_adjoint_record", "lbfd_adjoint_backward", "lbfd_adjoint_run", "lbfd_column_peaks",
 )
 
 
@@ -116,6 +116,7 @@ def load(path: str = LIB_PATH):
     lib.lbfd_launches_per_step.argtypes = [H]
     lib.lbfd_read_tangent.argtypes = [H, ctypes.c_int, ctypes.c_int, D]
     lib.lbfd_diagnostics_rows.argtypes = [H, ctypes.c_int, ctypes.c_int, D]
+    lib.lbfd_column_peaks.argtypes = [H, ctypes.c_int, ctypes.c_int, D, D]
     lib.lbfd_set_inlet_velocity.argtypes = [H, ctypes.c_double]
     lib.lbfd_set_curved_walls.argtypes = [H, ctypes.c_int, D]
     lib.lbfd_gradient.argtypes = [H, ctypes.c_int, D, D]
@@ -335,6 +336,16 @@ class Solver:
             st = self.lib.lbfd_diagnostics_rows(self.h, int(rows[0]), int(rows[1]), _dp(out))
         _check(self.lib, st, "lbfd_diagnostics", allow=(ENONFINITE,))
         return dict(zip(DIAG_KEYS, out.tolist()))
+
+    def column_peaks(self, rows=None):
+        """(peak heat release per column, distance of the peak to the nearer
+        edge of the rows y0 <= y < y1) over all x; 2-D."""
+        y0, y1 = rows if rows is not None else (0, self.cfg["ny"])
+        peak = np.empty(self.cfg["nx"])
+        dist = np.empty(self.cfg["nx"])
+        _check(self.lib, self.lib.lbfd_column_peaks(self.h, int(y0), int(y1), _dp(peak), _dp(dist)),
+               "lbfd_column_peaks")
+        return peak, dist
 
     def set_curved_walls(self, prims):
         """Curved walls from primitives (type, p0, p1, p2, p3); see lbfd.h."""

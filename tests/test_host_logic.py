@@ -120,3 +120,15 @@ def test_traffic_record_only_for_the_recorded_sources(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 64)
     assert bench.measured_traffic("w", 5, "mixed")[0] is None
     assert bench.measured_instructions("w", 5, "mixed") is None
+
+
+def test_dead_zone_from_column_peaks():
+    """delta_dead is the smallest front-to-wall distance over the columns
+    whose peak heat release is at least 10 % of the channel's largest."""
+    from paper_2304_05657_gb300 import channels
+
+    peak = np.array([0.0, 0.05, 1.0, 2.0, 0.3, 0.01])
+    dist = np.array([0.5, 0.5, 3.5, 6.5, 2.5, 0.5])
+    assert channels.dead_zone(peak, dist) == 2.5  # columns 2, 3, 4 burn
+    assert channels.dead_zone(peak, dist, rel=0.6) == 6.5
+    assert np.isnan(channels.dead_zone(np.zeros(4), np.ones(4)))

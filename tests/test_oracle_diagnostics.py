@@ -139,3 +139,30 @@ def test_diagnostics_closed_forms(oracle_mod):
     assert d2["T_max"] == 2000.0
     # every hot unburnt cell on the centre line has the same rate: ties go to x = 0
     assert d2["x_hrr_max"] == 0.0
+
+
+def test_column_peaks_closed_form(oracle_mod):
+    """A front drawn by hand: in column x the only reacting cell is at row
+    r(x) of a band y0 <= y < y1, so the peak is that cell's heat release and
+    the distance is min(r - y0 + 1/2, y1 - 1/2 - r); a column with two equal
+    peaks reports the smaller row."""
+    nx, ny = 12, 15
+    cfg = inputs.base_config(dim=2, nx=nx, ny=ny)
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[9, :] = 1  # a separator: the band is rows 10..14
+    y0, y1 = 10, 15
+    T = np.full((ny, nx), 300.0)
+    rows = [10, 11, 12, 13, 14, 12, 11, 10, 13, 14, 12, 11]
+    for x, r in enumerate(rows):
+        T[r, x] = 1500.0 + 10.0 * x
+    T[12, 4] = T[11, 4] = 1600.0  # a tie in column 4: rows 11 and 12 (distances 1.5 and 2.5)
+    T[14, 4] = 300.0
+    Y = np.tile(np.asarray(cfg["Y_in"])[:, None], (1, nx * ny))
+    sim = oracle_mod.Sim(cfg, solid)
+    sim.set_state(T.ravel(), Y)
+    peak, dist = sim.column_peaks((y0, y1))
+    for x, r in enumerate(rows):
+        if x == 4:
+            r = 11
+        assert dist[x] == min(r - y0 + 0.5, y1 - 0.5 - r), (x, dist[x])
+    assert np.all(peak > 0) and np.argmax(peak) == nx - 1
