@@ -224,14 +224,17 @@ int lbfd_set_wait_limit(lbfd_handle* h, long long ns);
  * with two interior cells per thread in packed FP32 arithmetic (tiles of
  * 32x8, 64x8, 32x8, 64x4 at 4, 2, 5 and 5 blocks per SM; the FP64 form runs
  * them one cell per thread).
- * In 3-D (6 variants), 1..2 are 32x4 columns marching through 16 or 32
+ * In 3-D (8 variants), 1..2 are 32x4 columns marching through 16 or 32
  * z-planes with a five-plane shared-memory ring, 3 is 1 with the registers
- * capped for four blocks per SM, and 4..5 are 1..2 split into an FD tile
+ * capped for four blocks per SM, 4..5 are 1..2 split into an FD tile
  * kernel (a1-a7, writing Lambda and grad rho to a scratch buffer of four
- * planes) and a per-cell collision kernel (a8-a10).  The cells the tiles leave out go through
- * the general form over lists computed at create (in 3-D, one list for
- * cells near domain faces and one, with the face rules compiled out, for
- * cells next to in-domain solids).  All variants compute the same step up
+ * planes) and a per-cell collision kernel (a8-a10), and 6..7 are 1..2 with
+ * the cells next to in-domain solids updated in the tile kernel too (ghost
+ * points by the mirror rule from the staged mask, bounce-back pulls).  The
+ * cells the tiles leave out go through the general form over lists
+ * computed at create (in 3-D, one list for cells near domain faces and one,
+ * with the face rules compiled out, for cells next to in-domain solids,
+ * which variants 6..7 launch only with curved walls).  All variants compute the same step up
  * to rounding order.  Default: 1 (0 for LBFD_TANGENT, which has the
  * general form only). */
 int lbfd_num_variants(const lbfd_handle* h);

@@ -468,6 +468,20 @@ int lbfd_create(const lbfd_grid* grid, const uint8_t* solid_mask, const lbfd_mec
         std::set_difference(lists_host[0].begin(), lists_host[0].end(), lists_host[1].begin(), lists_host[1].end(),
                             std::back_inserter(wl));
         h->nbndw = (long long)wl.size();
+        // class 2: next to in-domain solids, no domain face in reach (the
+        // wall-aware tiles update these cells themselves)
+        if (!wl.empty()) {
+            std::vector<uint8_t> cls((size_t)h->ncell);
+            if ((e = cudaMemcpy(cls.data(), h->interior, (size_t)h->ncell, cudaMemcpyDeviceToHost)) != cudaSuccess) {
+                free_handle(h);
+                return cuda_fail(e, "interior flags");
+            }
+            for (long long c : wl) cls[c] = 2;
+            if ((e = cudaMemcpy(h->interior, cls.data(), (size_t)h->ncell, cudaMemcpyHostToDevice)) != cudaSuccess) {
+                free_handle(h);
+                return cuda_fail(e, "interior flags");
+            }
+        }
         // the Lambda / grad rho planes of the split variants
         if (!is_tangent(h->precision) &&
             (e = cudaMalloc(&h->aux, (size_t)4 * h->stride * h->esz)) != cudaSuccess) {
@@ -657,7 +671,8 @@ int lbfd_launches_per_step(const lbfd_handle* h)
     int n = 1;
     if (h->variant > 0 && !is_tangent(h->precision)) {
         if (h->dim == 3) {
-            n += (b.nface > 0 ? 1 : 0) + (b.nwall > 0 ? 1 : 0) + (h->variant >= 4 ? 1 : 0);
+            const bool wall_list = b.nwall > 0 && (h->variant < 6 || h->Pd.curved);
+            n += (b.nface > 0 ? 1 : 0) + (wall_list ? 1 : 0) + (h->variant == 4 || h->variant == 5 ? 1 : 0);
         } else {
             const bool wv = h->variant >= 5 && b.nwall_tiles > 0;
             n += ((wv ? b.nface : b.nall) > 0 ? 1 : 0) + (wv ? 1 : 0);

@@ -138,7 +138,7 @@ static cudaError_t launch_2d(int variant, const StepParams<R>& P, StateView in, 
     }
 }
 
-int num_variants(int dim) { return dim == 2 ? 13 : 6; }
+int num_variants(int dim) { return dim == 2 ? 13 : 8; }
 
 void wall_tiles(int nx, int ny, const std::vector<long long>& all, const std::vector<long long>& face,
                 std::vector<int>& out)

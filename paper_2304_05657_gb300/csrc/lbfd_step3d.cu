@@ -18,17 +18,23 @@ static auto tile3_kernel()
 
 // SPLIT: the tile kernel does a1-a7 and a per-cell kernel a8-a10 (two
 // smaller kernels instead of one; Lambda and grad rho pass through aux)
-template <typename S, typename R, int TX, int TY, int ZC, int MINB = 0, bool SPLIT = false>
+// WALLS: the wall-aware tile kernel also updates the cells next to
+// in-domain solids, so the wall list runs only with curved walls
+template <typename S, typename R, int TX, int TY, int ZC, int MINB = 0, bool SPLIT = false, bool WALLS = false>
 static cudaError_t launch_t3(const StepParams<R>& P, StateView in, StateView out, const uint8_t* solid,
-                             const BoundaryLists& b, const SideStream& side, cudaStream_t stream)
+                             const BoundaryLists& bin, const SideStream& side, cudaStream_t stream)
 {
     constexpr size_t smem = tile3_smem_bytes<R, TX, TY>();
     auto kern = tile3_kernel<S, R, TX, TY, ZC, MINB>();
     auto fkern = step_kernel_fd3d<S, R, TX, TY, ZC>;
-    cudaError_t e = SPLIT ? cudaFuncSetAttribute(fkern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                          : cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto wkern = step_kernel_tiled3d_walls<S, R, TX, TY, ZC>;
+    cudaError_t e = SPLIT   ? cudaFuncSetAttribute(fkern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                    : WALLS ? cudaFuncSetAttribute(wkern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                            : cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    if (b.interior == nullptr || (SPLIT && b.aux == nullptr)) return cudaErrorInvalidValue;
+    if (bin.interior == nullptr || (SPLIT && bin.aux == nullptr)) return cudaErrorInvalidValue;
+    BoundaryLists b = bin;
+    if (WALLS && !P.curved) b.nwall = 0;
     const bool fork = (b.nface > 0 || b.nwall > 0) && side.stream != nullptr;
     if (fork) {
         if ((e = cudaEventRecord(side.fork, stream)) != cudaSuccess) return e;
@@ -55,6 +61,9 @@ static cudaError_t launch_t3(const StepParams<R>& P, StateView in, StateView out
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         step_kernel_collide3d<S, R><<<dim3((P.nx + 127) / 128, P.ny, P.nz), 128, 0, stream>>>(
             P, (const S*)in.g, (S*)out.g, (const S*)in.T, (const S*)in.Y, b.interior, (const R*)b.aux);
+    } else if constexpr (WALLS) {
+        wkern<<<grid, dim3(TX, TY), smem, stream>>>(P, (const S*)in.g, (S*)out.g, (const S*)in.T, (S*)out.T,
+                                                    (const S*)in.Y, (S*)out.Y, b.interior, solid);
     } else {
         kern<<<grid, dim3(TX, TY), smem, stream>>>(P, (const S*)in.g, (S*)out.g, (const S*)in.T, (S*)out.T,
                                                    (const S*)in.Y, (S*)out.Y, b.interior);
@@ -80,6 +89,10 @@ static cudaError_t launch_3d_tiles(int variant, const StepParams<R>& P, StateVie
     // variants 4, 5: as 1, 2 split into an FD tile kernel and a collision kernel
     case 4: return launch_t3<S, R, 32, 4, 16, 0, true>(P, in, out, solid, b, side, stream);
     case 5: return launch_t3<S, R, 32, 4, 32, 0, true>(P, in, out, solid, b, side, stream);
+    // variants 6, 7: as 1, 2 with the cells next to in-domain solids in the
+    // tile kernel (wall-aware), no wall list
+    case 6: return launch_t3<S, R, 32, 4, 16, 0, false, true>(P, in, out, solid, b, side, stream);
+    case 7: return launch_t3<S, R, 32, 4, 32, 0, false, true>(P, in, out, solid, b, side, stream);
     default: return cudaErrorInvalidValue;
     }
 }

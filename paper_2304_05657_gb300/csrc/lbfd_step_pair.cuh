@@ -79,8 +79,8 @@ __device__ __forceinline__ void pair_store(float* p, const F2& v, bool ok0, bool
 // shared store.  Odd nx takes stage_tile2d.
 template <int TX, int TY, int NTHR>
 __device__ __forceinline__ void stage_tile2d_pairs(const StepParams<float>& P, const TileSmem<float>& sm, int x0,
-                                                   int y0, int tid, const float* __restrict__ T_in,
-                                                   const float* __restrict__ Y_in)
+                                                   int y0, int tid, const float* LBFD_RESTRICT T_in,
+                                                   const float* LBFD_RESTRICT Y_in)
 {
     using G = TileGeom<TX, TY>;
     constexpr int SX = G::SX, NPT = G::NPT, NPP = NPT / 2;
@@ -139,9 +139,9 @@ __device__ __forceinline__ void stage_tile2d_pairs(const StepParams<float>& P, c
 // SM (which caps the registers); FP32 storage and arithmetic
 template <int TXP, int TY, int MINB>
 __global__ void __launch_bounds__(TXP * TY, MINB)
-    step_kernel_pair2d(StepParams<float> P, const float* __restrict__ g_in, float* __restrict__ g_out,
-                       const float* __restrict__ T_in, float* __restrict__ T_out, const float* __restrict__ Y_in,
-                       float* __restrict__ Y_out, const uint8_t* __restrict__ interior)
+    step_kernel_pair2d(StepParams<float> P, const float* LBFD_RESTRICT g_in, float* LBFD_RESTRICT g_out,
+                       const float* LBFD_RESTRICT T_in, float* LBFD_RESTRICT T_out, const float* LBFD_RESTRICT Y_in,
+                       float* LBFD_RESTRICT Y_out, const uint8_t* LBFD_RESTRICT interior)
 {
     constexpr int TX = 2 * TXP;
     using G = TileGeom<TX, TY>;

@@ -6,8 +6,12 @@
 // and the derived W, 1/W, rho of every point (X_k = Y_k W / W_k is formed
 // when used); each plane is loaded once per column pass.  Interior cells
 // (every +-2 axis neighbour and all 26 LB neighbours are fluid cells of the
-// domain; a per-cell flag computed at create) are updated here; the others
-// go to step_kernel_boundary over the face and wall lists.
+// domain; per-cell class 1, computed at create) are updated here.  The
+// wall-aware variants (WALLS) also update the cells next to in-domain
+// solids whose stencils reach no domain face (class 2): their FD lines take
+// ghost points by the mirror rule of Eq. 34 from the staged tile and mask,
+// and their pull bounces back from solid neighbours (Eq. 28), so only the
+// cells near domain faces are left to step_kernel_boundary.
 #pragma once
 #include "lbfd_step_tiled.cuh"
 
@@ -30,19 +34,34 @@ __host__ __device__ constexpr size_t tile3_smem_bytes()
 }
 
 // FD terms along one axis from five explicit shared-memory points (the
-// X_k lines first, as in fd_axis_core); returns d rho / d x_a
+// X_k lines first, as in fd_axis_core); returns d rho / d x_a.  `ghost`
+// flags (bit j) the points that are ghosts of an in-domain solid (pts then
+// holds their mirror points): T and rho take the Dirichlet form at
+// isothermal solids, Y_k and W mirror, and the convection of the axis is
+// centred (Sec. II.D, next to a boundary).  ghost == 0 for interior cells.
 template <typename R>
 __device__ __forceinline__ R fd_axis_pts(const StepParams<R>& P, const TileSmem<R>& sm, int npt, const int* pts,
-                                         R u_a, const R* Y0, R invW0, R rho0, TileAccum<R>& acc)
+                                         int ghost, R u_a, const R* Y0, R invW0, R rho0, TileAccum<R>& acc)
 {
     R v[5], w[5];
+    const bool dir = ghost != 0 && P.solid_isothermal;
 #pragma unroll
-    for (int j = 0; j < 5; ++j) v[j] = sm.rho[pts[j]];
+    for (int j = 0; j < 5; ++j) {
+        v[j] = sm.rho[pts[j]];
+        if (dir && ((ghost >> j) & 1)) v[j] = R(2) * eos(P, P.T_solid, sm.invW[pts[j]]) - v[j];
+    }
     const R drho = fd_d1(v);
     const R drho_r = fdiv(drho, rho0);
 #pragma unroll
-    for (int j = 0; j < 5; ++j) v[j] = sm.T[pts[j]];
-    acc.conv_T += u_a * weno3_deriv_fast(v, u_a, P.epsT);
+    for (int j = 0; j < 5; ++j) {
+        v[j] = sm.T[pts[j]];
+        if (dir && ((ghost >> j) & 1)) v[j] = R(2) * P.T_solid - v[j];
+    }
+    // next to a wall the axis is centred: both are formed and one is kept,
+    // so that a warp mixing wall and interior cells does not branch
+    const bool near = ghost != 0;
+    const R wT = weno3_deriv_fast(v, u_a, P.epsT);
+    acc.conv_T += u_a * (near ? fd_c2(v) : wT);
     acc.diff_T += P.alpha12 * (fd_D2(v) + drho_r * fd_D1(v));  // 12x stencils, alpha / 12
 #pragma unroll
     for (int j = 0; j < 5; ++j) w[j] = sm.invW[pts[j]];
@@ -67,7 +86,8 @@ __device__ __forceinline__ R fd_axis_pts(const StepParams<R>& P, const TileSmem<
     for (int k = 0; k < NSP; ++k) {
 #pragma unroll
         for (int j = 0; j < 5; ++j) v[j] = sm.Y[k * npt + pts[j]];
-        const R Lk = weno3_deriv_fast(v, u_a, P.epsY);
+        const R wk = weno3_deriv_fast(v, u_a, P.epsY);
+        const R Lk = near ? fd_c2(v) : wk;
         sumL += Lk;
         const R dY = fd_d1(v);
         const R dk = dm[k] - dY * M - Y0[k] * dM + (m[k] - Y0[k] * M) * drho_r;
@@ -80,11 +100,39 @@ __device__ __forceinline__ R fd_axis_pts(const StepParams<R>& P, const TileSmem<
     return drho;
 }
 
+// the five points of an axis line after the mirror rule of Eq. 34 for a
+// cell next to in-domain solid cells: raw[j] are the staged points at
+// offsets -2..2; the ghost at distance j beyond a wall at distance w
+// mirrors the point at offset 2w - 1 - j (the neighbour on the other side,
+// or the centre when that is solid, for offset -1).  Returns the ghost bits.
+__device__ __forceinline__ int wall_line_pts(const uint8_t* mask, const int* raw, int* pts)
+{
+    int ghost = 0;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) pts[j] = raw[j];
+#pragma unroll
+    for (int side = -1; side <= 1; side += 2) {
+        const int w = mask[raw[2 + side]] ? 1 : (mask[raw[2 + 2 * side]] ? 2 : 0);
+        if (!w) continue;
+#pragma unroll
+        for (int j = 1; j <= 2; ++j) {
+            if (j < w) continue;
+            const int m = 2 * w - 1 - j;
+            const int mp = m >= 0 ? raw[2 + side * m] : (mask[raw[2 - side]] ? raw[2] : raw[2 - side]);
+            pts[2 + side * j] = mp;
+            ghost |= 1 << (2 + side * j);
+        }
+    }
+    return ghost;
+}
+
 // stage plane z (grid coordinate) into ring slot `slot`; solid points are
-// staged like fluid ones (never read: the tile updates interior cells only)
-template <typename S, typename R, int TX, int TY>
+// staged like fluid ones (never read by an interior cell; with WALLS the
+// mask marks them, 1 solid, 2 outside the domain, for the wall cells)
+template <typename S, typename R, int TX, int TY, bool WALLS = false>
 __device__ __forceinline__ void stage_plane(const StepParams<R>& P, const TileSmem<R>& sm, int slot, int x0, int y0,
-                                            int z, const S* __restrict__ T_in, const S* __restrict__ Y_in)
+                                            int z, const S* LBFD_RESTRICT T_in, const S* LBFD_RESTRICT Y_in,
+                                            const uint8_t* LBFD_RESTRICT solid = nullptr)
 {
     using G = Tile3Geom<TX, TY>;
     constexpr int NPT = G::NPT;
@@ -105,9 +153,13 @@ __device__ __forceinline__ void stage_plane(const StepParams<R>& P, const TileSm
         if ((gx < 0 || gx >= P.nx) && P.bc[0] == BC_PERIODIC) gx = ((gx % P.nx) + P.nx) % P.nx;
         if ((gy < 0 || gy >= P.ny) && P.bc[2] == BC_PERIODIC) gy = ((gy % P.ny) + P.ny) % P.ny;
         if ((gz < 0 || gz >= P.nz) && P.bc[4] == BC_PERIODIC) gz = ((gz % P.nz) + P.nz) % P.nz;
-        if (gx < 0 || gx >= P.nx || gy < 0 || gy >= P.ny || gz < 0 || gz >= P.nz) continue;
+        if (gx < 0 || gx >= P.nx || gy < 0 || gy >= P.ny || gz < 0 || gz >= P.nz) {
+            if constexpr (WALLS) sm.mask[slot * G::NPP + q] = 2;
+            continue;
+        }
         const long long c = (long long)gx + (long long)P.nx * (gy + (long long)P.ny * gz);
         cell[it] = c;
+        if constexpr (WALLS) sm.mask[slot * G::NPP + q] = solid[c] ? 1 : 0;
         T[it] = R(T_in[c]);
 #pragma unroll
         for (int k = 0; k < NSP; ++k) Y[it][k] = R(Y_in[(long long)k * N + c]);
@@ -129,12 +181,13 @@ __device__ __forceinline__ void stage_plane(const StepParams<R>& P, const TileSm
 
 // SPLIT: steps a1-a7 only; Lambda and grad rho of every interior cell go
 // to aux (four planes) for step_kernel_collide3d, which does a8-a10
-template <typename S, typename R, int TX, int TY, int ZC, bool SPLIT = false>
-__device__ __forceinline__ void tiled3d_body(const StepParams<R>& P, const S* __restrict__ g_in,
-                                             S* __restrict__ g_out, const S* __restrict__ T_in,
-                                             S* __restrict__ T_out, const S* __restrict__ Y_in,
-                                             S* __restrict__ Y_out, const uint8_t* __restrict__ interior,
-                                             R* __restrict__ aux = nullptr)
+template <typename S, typename R, int TX, int TY, int ZC, bool SPLIT = false, bool WALLS = false>
+__device__ __forceinline__ void tiled3d_body(const StepParams<R>& P, const S* LBFD_RESTRICT g_in,
+                                             S* LBFD_RESTRICT g_out, const S* LBFD_RESTRICT T_in,
+                                             S* LBFD_RESTRICT T_out, const S* LBFD_RESTRICT Y_in,
+                                             S* LBFD_RESTRICT Y_out, const uint8_t* LBFD_RESTRICT interior,
+                                             R* LBFD_RESTRICT aux = nullptr,
+                                             const uint8_t* LBFD_RESTRICT solid = nullptr)
 {
     using G = Tile3Geom<TX, TY>;
     constexpr int SX = G::SX, NPP = G::NPP, NPT = G::NPT;
@@ -152,7 +205,9 @@ __device__ __forceinline__ void tiled3d_body(const StepParams<R>& P, const S* __
     const long long plane = (long long)P.nx * P.ny;
     // ring slot of grid plane z: (z + 5*big) % 5 keeps it non-negative
     auto slot_of = [](int z) { return (z + 10) % 5; };
-    for (int dz = -2; dz <= 1; ++dz) stage_plane<S, R, TX, TY>(P, sm, slot_of(zb + dz), x0, y0, zb + dz, T_in, Y_in);
+    for (int dz = -2; dz <= 1; ++dz)
+        stage_plane<S, R, TX, TY, WALLS>(P, sm, slot_of(zb + dz), x0, y0, zb + dz, T_in, Y_in, solid);
+    if constexpr (WALLS) __syncthreads();  // the masks of planes z-1..z+1 are read by the first pull
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     const int q0 = (threadIdx.y + 2) * SX + threadIdx.x + 2;  // in-plane point of this thread
     const int zend = zb + ZC < P.nz ? zb + ZC : P.nz;
@@ -163,11 +218,14 @@ __device__ __forceinline__ void tiled3d_body(const StepParams<R>& P, const S* __
         // offsets stay inside the domain for any in-range cell)
         const long long c = (long long)x + (long long)P.nx * y + plane * z;
         R g[27];
-        // the cell's class (+-2 along the three axes and the 26 neighbours
-        // are fluid cells of the domain), precomputed per cell
-        bool active = false;
+        // the cell's class (1: +-2 along the three axes and the 26 neighbours
+        // are fluid cells of the domain; 2: next to in-domain solids, no
+        // domain face in reach), precomputed per cell
+        bool active = false, wall = false;
         if (inside) {
-            active = interior[c] != 0;
+            const int cls = interior[c];
+            wall = WALLS && cls == 2 && !P.curved;
+            active = cls == 1 || wall;
             const int oxm = x == 0 ? P.nx - 1 : -1, oxp = x == P.nx - 1 ? 1 - P.nx : 1;
             const long long oym = y == 0 ? (long long)(P.ny - 1) * P.nx : -(long long)P.nx;
             const long long oyp = y == P.ny - 1 ? (long long)(1 - P.ny) * P.nx : (long long)P.nx;
@@ -176,13 +234,19 @@ __device__ __forceinline__ void tiled3d_body(const StepParams<R>& P, const S* __
             const S* gc = g_in + c;
 #pragma unroll
             for (int i = 0; i < 27; ++i) {
-                const long long o = (cx_of(i) > 0 ? oxm : (cx_of(i) < 0 ? oxp : 0)) +
-                                    (cy_of(i) > 0 ? oym : (cy_of(i) < 0 ? oyp : 0)) +
-                                    (cz_of(i) > 0 ? ozm : (cz_of(i) < 0 ? ozp : 0));
-                g[i] = R(__ldg(gc + (long long)i * N + o));
+                long long o = (long long)i * N + (cx_of(i) > 0 ? oxm : (cx_of(i) < 0 ? oxp : 0)) +
+                              (cy_of(i) > 0 ? oym : (cy_of(i) < 0 ? oyp : 0)) +
+                              (cz_of(i) > 0 ? ozm : (cz_of(i) < 0 ? ozp : 0));
+                if constexpr (WALLS) {
+                    // half-way bounce-back from a solid neighbour (Eq. 28)
+                    const int src = slot_of(z - cz_of(i)) * NPP + q0 - cx_of(i) - cy_of(i) * SX;
+                    const bool bb = (sm.mask[src] != 0) & wall;
+                    o = bb ? (long long)opposite<3>(i) * N : o;
+                }
+                g[i] = R(LBFD_LDG(gc + o));
             }
         }
-        stage_plane<S, R, TX, TY>(P, sm, slot_of(z + 2), x0, y0, z + 2, T_in, Y_in);
+        stage_plane<S, R, TX, TY, WALLS>(P, sm, slot_of(z + 2), x0, y0, z + 2, T_in, Y_in, solid);
         __syncthreads();
         const int sc = slot_of(z);
         const int p0 = sc * NPP + q0;
@@ -215,8 +279,17 @@ __device__ __forceinline__ void tiled3d_body(const StepParams<R>& P, const S* __
 #pragma unroll
                 for (int j = 0; j < 5; ++j)
                     pts[j] = a == 0 ? p0 + (j - 2) : (a == 1 ? p0 + (j - 2) * SX : slot_of(z + j - 2) * NPP + q0);
+                int ghost = 0;
+                if constexpr (WALLS) {
+                    if (wall) {
+                        int raw[5];
+#pragma unroll
+                        for (int j = 0; j < 5; ++j) raw[j] = pts[j];
+                        ghost = wall_line_pts(sm.mask, raw, pts);
+                    }
+                }
                 const R u_a = a == 0 ? u[0] : (a == 1 ? u[1] : u[2]);
-                const R drho = fd_axis_pts<R>(P, sm, NPT, pts, u_a, Y0, invW0, rho0, acc);
+                const R drho = fd_axis_pts<R>(P, sm, NPT, pts, ghost, u_a, Y0, invW0, rho0, acc);
                 acc.grad_rho[0] = a == 0 ? drho : acc.grad_rho[0];
                 acc.grad_rho[1] = a == 1 ? drho : acc.grad_rho[1];
                 acc.grad_rho[2] = a == 2 ? drho : acc.grad_rho[2];
@@ -243,21 +316,36 @@ __device__ __forceinline__ void tiled3d_body(const StepParams<R>& P, const S* __
 }
 
 template <typename S, typename R, int TX, int TY, int ZC>
-__global__ void __launch_bounds__(TX * TY) step_kernel_tiled3d(StepParams<R> P, const S* __restrict__ g_in,
-                                                               S* __restrict__ g_out, const S* __restrict__ T_in,
-                                                               S* __restrict__ T_out, const S* __restrict__ Y_in,
-                                                               S* __restrict__ Y_out,
-                                                               const uint8_t* __restrict__ interior)
+__global__ void __launch_bounds__(TX * TY) step_kernel_tiled3d(StepParams<R> P, const S* LBFD_RESTRICT g_in,
+                                                               S* LBFD_RESTRICT g_out, const S* LBFD_RESTRICT T_in,
+                                                               S* LBFD_RESTRICT T_out, const S* LBFD_RESTRICT Y_in,
+                                                               S* LBFD_RESTRICT Y_out,
+                                                               const uint8_t* LBFD_RESTRICT interior)
 {
     tiled3d_body<S, R, TX, TY, ZC>(P, g_in, g_out, T_in, T_out, Y_in, Y_out, interior);
+}
+
+// interior cells and, from the same staging, the cells next to in-domain
+// solids (class 2): no separate wall-list kernel
+template <typename S, typename R, int TX, int TY, int ZC>
+__global__ void __launch_bounds__(TX * TY) step_kernel_tiled3d_walls(StepParams<R> P, const S* LBFD_RESTRICT g_in,
+                                                                     S* LBFD_RESTRICT g_out,
+                                                                     const S* LBFD_RESTRICT T_in,
+                                                                     S* LBFD_RESTRICT T_out,
+                                                                     const S* LBFD_RESTRICT Y_in,
+                                                                     S* LBFD_RESTRICT Y_out,
+                                                                     const uint8_t* LBFD_RESTRICT interior,
+                                                                     const uint8_t* LBFD_RESTRICT solid)
+{
+    tiled3d_body<S, R, TX, TY, ZC, false, true>(P, g_in, g_out, T_in, T_out, Y_in, Y_out, interior, nullptr, solid);
 }
 
 // the same with the registers capped so that MINB blocks fit on an SM
 template <typename S, typename R, int TX, int TY, int ZC, int MINB>
 __global__ void __launch_bounds__(TX * TY, MINB)
-    step_kernel_tiled3d_capped(StepParams<R> P, const S* __restrict__ g_in, S* __restrict__ g_out,
-                               const S* __restrict__ T_in, S* __restrict__ T_out, const S* __restrict__ Y_in,
-                               S* __restrict__ Y_out, const uint8_t* __restrict__ interior)
+    step_kernel_tiled3d_capped(StepParams<R> P, const S* LBFD_RESTRICT g_in, S* LBFD_RESTRICT g_out,
+                               const S* LBFD_RESTRICT T_in, S* LBFD_RESTRICT T_out, const S* LBFD_RESTRICT Y_in,
+                               S* LBFD_RESTRICT Y_out, const uint8_t* LBFD_RESTRICT interior)
 {
     tiled3d_body<S, R, TX, TY, ZC>(P, g_in, g_out, T_in, T_out, Y_in, Y_out, interior);
 }
@@ -266,9 +354,9 @@ __global__ void __launch_bounds__(TX * TY, MINB)
 // four 128-thread blocks per SM
 template <typename S, typename R, int TX, int TY, int ZC>
 __global__ void __launch_bounds__(TX * TY, sizeof(R) == 4 ? 512 / (TX * TY) : 1)
-    step_kernel_fd3d(StepParams<R> P, const S* __restrict__ g_in, const S* __restrict__ T_in, S* __restrict__ T_out,
-                     const S* __restrict__ Y_in, S* __restrict__ Y_out, const uint8_t* __restrict__ interior,
-                     R* __restrict__ aux)
+    step_kernel_fd3d(StepParams<R> P, const S* LBFD_RESTRICT g_in, const S* LBFD_RESTRICT T_in, S* LBFD_RESTRICT T_out,
+                     const S* LBFD_RESTRICT Y_in, S* LBFD_RESTRICT Y_out, const uint8_t* LBFD_RESTRICT interior,
+                     R* LBFD_RESTRICT aux)
 {
     tiled3d_body<S, R, TX, TY, ZC, true>(P, g_in, nullptr, T_in, T_out, Y_in, Y_out, interior, aux);
 }
@@ -279,16 +367,16 @@ __global__ void __launch_bounds__(TX * TY, sizeof(R) == 4 ? 512 / (TX * TY) : 1)
 // per block.
 template <typename S, typename R>
 __global__ void __launch_bounds__(128)
-    step_kernel_collide3d(StepParams<R> P, const S* __restrict__ g_in, S* __restrict__ g_out,
-                          const S* __restrict__ T_in, const S* __restrict__ Y_in,
-                          const uint8_t* __restrict__ interior, const R* __restrict__ aux)
+    step_kernel_collide3d(StepParams<R> P, const S* LBFD_RESTRICT g_in, S* LBFD_RESTRICT g_out,
+                          const S* LBFD_RESTRICT T_in, const S* LBFD_RESTRICT Y_in,
+                          const uint8_t* LBFD_RESTRICT interior, const R* LBFD_RESTRICT aux)
 {
     const int x = blockIdx.x * 128 + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
     if (x >= P.nx) return;
     const long long N = P.N;
     const long long plane = (long long)P.nx * P.ny;
     const long long c = (long long)x + (long long)P.nx * y + plane * z;
-    if (!interior[c]) return;
+    if (interior[c] != 1) return;
     R g[27];
     {
         const int oxm = x == 0 ? P.nx - 1 : -1, oxp = x == P.nx - 1 ? 1 - P.nx : 1;
@@ -302,7 +390,7 @@ __global__ void __launch_bounds__(128)
             const long long o = (cx_of(i) > 0 ? oxm : (cx_of(i) < 0 ? oxp : 0)) +
                                 (cy_of(i) > 0 ? oym : (cy_of(i) < 0 ? oyp : 0)) +
                                 (cz_of(i) > 0 ? ozm : (cz_of(i) < 0 ? ozp : 0));
-            g[i] = R(__ldg(gc + (long long)i * N + o));
+            g[i] = R(LBFD_LDG(gc + (long long)i * N + o));
         }
     }
     // the density as staged by the FD half
