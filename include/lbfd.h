@@ -387,7 +387,11 @@ int lbfd_set_state_raw(lbfd_handle* h, const void* host_src, size_t bytes);
  * threads) race and must be serialised by the caller.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress) and
  * caches it; make that first call before any stream capture.  No cudaMalloc,
- * cudaFree or allocating library routine is called.
+ * cudaFree or allocating library routine is called.  The call copies the
+ * sums to the host and synchronises the stream, so it cannot be made while
+ * the stream is being captured into a CUDA graph.  The cached address
+ * belongs to the device's context: a cudaDeviceReset of that device while
+ * the library is loaded is not supported.
  * Errors: EINVAL (null or non-device pointer, plane_stride < cells, invalid
  * grid/parameters as in lbfd_create), EUNSTABLE/ENOTSUP as lbfd_create,
  * ECUDA, ENONFINITE (after filling out). */
@@ -396,6 +400,29 @@ int lbfd_diagnostics_noalloc(const lbfd_grid* grid, const lbfd_mechanism* mech,
                              const lbfd_params* params, const void* g, const void* T,
                              const void* Y, long long plane_stride, const uint8_t* solid,
                              void* stream, double* out);
+
+/* Checkpoint of the current state to a file and back: a header (magic
+ * "LBFDCKPT", version 1, dim, nx, ny, nz, Q, species, precision, bytes per
+ * value, the step counter, the state size) followed by the raw state of
+ * lbfd_get_state_raw.  lbfd_load accepts only a file written for the same
+ * grid, lattice and precision (else LBFD_EINVAL with the reason in
+ * lbfd_last_error()), restores the state and the step counter (resume).
+ * Both synchronise. */
+int lbfd_save(lbfd_handle* h, const char* path);
+int lbfd_load(lbfd_handle* h, const char* path);
+
+/* Create one handle for n 2-D channels of uneven width run together (the
+ * batching of Sec. IV.A's channel study): channel j has widths[j] rows and
+ * `length` columns; the channels are stacked along y in one masked domain
+ * with one solid row between neighbours, so that no stencil or population
+ * couples them (with isothermal solids at the wall temperature each row of
+ * solid acts as the walls of both channels).  proto gives dim (2) and the
+ * face types and wall temperatures; nx, ny, nz are set here.  rows[2 j],
+ * rows[2 j + 1] receive the first and one-past-last row of channel j (the
+ * rows argument of lbfd_diagnostics_rows, lbfd_column_peaks).  Errors as
+ * lbfd_create; ENOTSUP unless dim == 2. */
+int lbfd_batch_create(int n, const int* widths, int length, const lbfd_grid* proto, const lbfd_mechanism* mech,
+                      const lbfd_params* params, lbfd_handle** out, int* rows);
 
 /* Curved walls (Sec. III): n analytic primitives, 5 doubles each,
  *   {0, cx, cy, cz, r}: sphere (circle in 2-D), solid inside;

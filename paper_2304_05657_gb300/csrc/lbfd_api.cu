@@ -18,6 +18,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/lbfd.h"
 #include "lbfd_internal.h"
 
@@ -85,6 +87,13 @@ struct lbfd_handle {
 };
 
 namespace {
+
+// NVTX range around an entry point (visible in a profiler timeline; no
+// cost without one attached)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 thread_local char g_last_error[512] = "";
 
@@ -566,6 +575,7 @@ int lbfd_init_fields(lbfd_handle* h, const double* T, const double* Y)
 
 int lbfd_step(lbfd_handle* h, int n)
 {
+    NvtxRange nvtx_("lbfd_step");
     if (!h || n < 0) return LBFD_EINVAL;
     for (int it = 0; it < n; ++it) {
         cudaError_t e = launch_one(h, h->cur, h->variant, h->stream);
@@ -578,6 +588,7 @@ int lbfd_step(lbfd_handle* h, int n)
 
 int lbfd_step_graph(lbfd_handle* h, int n)
 {
+    NvtxRange nvtx_("lbfd_step_graph");
     if (!h || n < 1) return LBFD_EINVAL;
     cudaStream_t s = h->stream;
     if (s == nullptr) {  // the legacy default stream cannot be captured
@@ -633,6 +644,7 @@ int lbfd_set_wait_limit(lbfd_handle* h, long long ns)
 
 int lbfd_step_persistent(lbfd_handle* h, int n)
 {
+    NvtxRange nvtx_("lbfd_step_persistent");
     if (!h || n < 0) return LBFD_EINVAL;
     if (h->dim != 2 || is_tangent(h->precision) || h->nghost > 0 || h->Pd.curved) return LBFD_ENOTSUP;
     if (n == 0) return LBFD_OK;
@@ -749,6 +761,7 @@ int lbfd_set_variant(lbfd_handle* h, int variant)
 
 int lbfd_autotune(lbfd_handle* h, int reps, double* ms_per_variant, int* best)
 {
+    NvtxRange nvtx_("lbfd_autotune");
     if (!h || reps < 1) return LBFD_EINVAL;
     const int nv = num_variants_of(h);
     cudaEvent_t e0, e1;
@@ -830,6 +843,7 @@ int lbfd_read_field(lbfd_handle* h, int field, double* out)
 
 int lbfd_diagnostics_rows(lbfd_handle* h, int y0, int y1, double* out)
 {
+    NvtxRange nvtx_("lbfd_diagnostics");
     if (!h || !out || y0 < 0 || y1 > h->grid.ny || y0 >= y1) return LBFD_EINVAL;
     double r[lbfd::RED_WORDS];
     CK(lbfd::launch_diagnostics(h->dim, h->precision, h->Pd, view(h, h->cur), h->solid, y0, y1, h->red, h->stream));
@@ -986,6 +1000,7 @@ int lbfd_adjoint_setup(lbfd_handle* h, int checkpoint_every)
 
 int lbfd_adjoint_record(lbfd_handle* h, int steps, int objective, double* value)
 {
+    NvtxRange nvtx_("lbfd_adjoint_record");
     if (!h || steps < 1 || (objective != LBFD_OBJ_FLAME_POSITION && objective != LBFD_OBJ_QUENCH_DISTANCE))
         return LBFD_EINVAL;
     if (!adjoint_precision(h) || h->dim != 2 || h->nghost > 0 || h->Pd.curved) return LBFD_ENOTSUP;
@@ -1040,6 +1055,7 @@ int lbfd_adjoint_record(lbfd_handle* h, int steps, int objective, double* value)
 
 int lbfd_adjoint_backward(lbfd_handle* h, double seed, double* grad)
 {
+    NvtxRange nvtx_("lbfd_adjoint_backward");
     if (!h || !grad) return LBFD_EINVAL;
     if (!h->adj_ck || h->adj_steps < 1) return LBFD_EINVAL;  // nothing recorded
     const int steps = h->adj_steps, nseg = h->adj_nseg;
@@ -1211,6 +1227,108 @@ int lbfd_set_state_raw(lbfd_handle* h, const void* src, size_t bytes)
     return LBFD_OK;
 }
 
+// checkpoint file: a fixed header, then the raw state (lbfd_get_state_raw)
+struct CheckpointHeader {
+    char magic[8];  // "LBFDCKPT"
+    int version, dim, nx, ny, nz, Q, nsp, precision;
+    long long esz, steps, state_bytes;
+};
+
+int lbfd_save(lbfd_handle* h, const char* path)
+{
+    NvtxRange nvtx_("lbfd_save");
+    if (!h || !path) return LBFD_EINVAL;
+    CheckpointHeader hd;
+    memset(&hd, 0, sizeof hd);
+    memcpy(hd.magic, "LBFDCKPT", 8);
+    hd.version = 1;
+    hd.dim = h->dim;
+    hd.nx = h->grid.nx;
+    hd.ny = h->grid.ny;
+    hd.nz = h->grid.nz;
+    hd.Q = h->Q;
+    hd.nsp = lbfd::NSP;
+    hd.precision = h->precision;
+    hd.esz = (long long)h->esz;
+    hd.steps = h->steps;
+    hd.state_bytes = (long long)lbfd_state_bytes(h);
+    std::vector<char> state((size_t)hd.state_bytes);
+    const int st = lbfd_get_state_raw(h, state.data(), state.size());
+    if (st != LBFD_OK) return st;
+    FILE* f = fopen(path, "wb");
+    if (!f) {
+        snprintf(g_last_error, sizeof g_last_error, "lbfd_save: cannot open %s", path);
+        return LBFD_EINVAL;
+    }
+    const bool ok = fwrite(&hd, sizeof hd, 1, f) == 1 && fwrite(state.data(), 1, state.size(), f) == state.size();
+    if (fclose(f) != 0 || !ok) {
+        snprintf(g_last_error, sizeof g_last_error, "lbfd_save: write to %s failed", path);
+        return LBFD_EINVAL;
+    }
+    return LBFD_OK;
+}
+
+int lbfd_load(lbfd_handle* h, const char* path)
+{
+    NvtxRange nvtx_("lbfd_load");
+    if (!h || !path) return LBFD_EINVAL;
+    FILE* f = fopen(path, "rb");
+    if (!f) {
+        snprintf(g_last_error, sizeof g_last_error, "lbfd_load: cannot open %s", path);
+        return LBFD_EINVAL;
+    }
+    CheckpointHeader hd;
+    bool ok = fread(&hd, sizeof hd, 1, f) == 1;
+    ok = ok && memcmp(hd.magic, "LBFDCKPT", 8) == 0 && hd.version == 1 && hd.dim == h->dim && hd.nx == h->grid.nx &&
+         hd.ny == h->grid.ny && hd.nz == h->grid.nz && hd.Q == h->Q && hd.nsp == lbfd::NSP &&
+         hd.precision == h->precision && hd.esz == (long long)h->esz &&
+         hd.state_bytes == (long long)lbfd_state_bytes(h);
+    std::vector<char> state;
+    if (ok) {
+        state.resize((size_t)hd.state_bytes);
+        ok = fread(state.data(), 1, state.size(), f) == state.size();
+    }
+    fclose(f);
+    if (!ok) {
+        snprintf(g_last_error, sizeof g_last_error,
+                 "lbfd_load: %s is not a checkpoint of this grid, lattice and precision", path);
+        return LBFD_EINVAL;
+    }
+    const int st = lbfd_set_state_raw(h, state.data(), state.size());
+    if (st != LBFD_OK) return st;
+    h->steps = hd.steps;
+    return LBFD_OK;
+}
+
+int lbfd_batch_create(int n, const int* widths, int length, const lbfd_grid* proto, const lbfd_mechanism* mech,
+                      const lbfd_params* params, lbfd_handle** out, int* rows)
+{
+    if (n < 1 || !widths || length < 1 || !proto || !mech || !params || !out || !rows) return LBFD_EINVAL;
+    if (proto->dim != 2) return LBFD_ENOTSUP;
+    long long ny = n - 1;
+    for (int j = 0; j < n; ++j) {
+        if (widths[j] < 1) return LBFD_EINVAL;
+        ny += widths[j];
+    }
+    if (ny > (1 << 30)) return LBFD_EINVAL;
+    lbfd_grid g = *proto;
+    g.nx = length;
+    g.ny = (int)ny;
+    g.nz = 1;
+    std::vector<uint8_t> mask((size_t)length * ny, 0);
+    int y = 0;
+    for (int j = 0; j < n; ++j) {
+        rows[2 * j] = y;
+        y += widths[j];
+        rows[2 * j + 1] = y;
+        if (j < n - 1) {  // one solid row between neighbouring channels
+            memset(mask.data() + (size_t)y * length, 1, (size_t)length);
+            ++y;
+        }
+    }
+    return lbfd_create(&g, mask.data(), mech, params, out);
+}
+
 int lbfd_read_tangent(lbfd_handle* h, int field, int k, double* out)
 {
     if (!h || !out || !is_tangent(h->precision) || k < 0 || k >= lbfd::NTAN) return LBFD_EINVAL;
@@ -1273,7 +1391,8 @@ int lbfd_num_populations(const lbfd_handle* h) { return h ? h->Q : -1; }
 // The reduction scratch lives in this file-scope device array instead of
 // memory from cudaMalloc.  Host code cannot use the array's name as a device
 // address, so the address is looked up once per device with
-// cudaGetSymbolAddress and cached.
+// cudaGetSymbolAddress and cached (for the life of the device's context: a
+// cudaDeviceReset is not supported while the library is loaded).
 // ---------------------------------------------------------------------------
 static __device__ __align__(256) double lbfd_noalloc_scratch[LBFD_NOALLOC_SCRATCH_WORDS];
 

@@ -37,7 +37,8 @@ SYMBOLS = (
     "lbfd_autotune", "lbfd_diagnostics_noalloc", "lbfd_launches_per_step", "lbfd_read_tangent", "lbfd_gradient",
     "lbfd_diagnostics_rows", "lbfd_set_inlet_velocity", "lbfd_set_curved_walls", "lbfd_read_cells",
     "lbfd_adjoint_gradient", "lbfd_step_persistent", "lbfd_set_wait_limit", "lbfd_adjoint_setup",
-    "lbfd_adjoint_record", "lbfd_adjoint_backward", "lbfd_adjoint_run", "lbfd_column_peaks",
+    "lbfd_adjoint_record", "lbfd_adjoint_backward", "lbfd_adjoint_run", "lbfd_column_peaks", "lbfd_save",
+    "lbfd_load", "lbfd_batch_create",
 )
 
 
@@ -117,6 +118,11 @@ def load(path: str = LIB_PATH):
     lib.lbfd_read_tangent.argtypes = [H, ctypes.c_int, ctypes.c_int, D]
     lib.lbfd_diagnostics_rows.argtypes = [H, ctypes.c_int, ctypes.c_int, D]
     lib.lbfd_column_peaks.argtypes = [H, ctypes.c_int, ctypes.c_int, D, D]
+    lib.lbfd_save.argtypes = [H, ctypes.c_char_p]
+    lib.lbfd_load.argtypes = [H, ctypes.c_char_p]
+    lib.lbfd_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                      ctypes.POINTER(Grid), ctypes.POINTER(Mechanism), ctypes.POINTER(Params),
+                                      ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int)]
     lib.lbfd_set_inlet_velocity.argtypes = [H, ctypes.c_double]
     lib.lbfd_set_curved_walls.argtypes = [H, ctypes.c_int, D]
     lib.lbfd_gradient.argtypes = [H, ctypes.c_int, D, D]
@@ -347,6 +353,12 @@ class Solver:
                "lbfd_column_peaks")
         return peak, dist
 
+    def save(self, path: str):
+        _check(self.lib, self.lib.lbfd_save(self.h, os.fsencode(path)), "lbfd_save")
+
+    def load(self, path: str):
+        _check(self.lib, self.lib.lbfd_load(self.h, os.fsencode(path)), "lbfd_load")
+
     def set_curved_walls(self, prims):
         """Curved walls from primitives (type, p0, p1, p2, p3); see lbfd.h."""
         arr = np.ascontiguousarray(np.asarray(prims, dtype=np.float64).reshape(-1, 5))
@@ -374,6 +386,33 @@ class Solver:
     @property
     def steps_done(self) -> int:
         return int(self.lib.lbfd_steps_done(self.h))
+
+
+def batch_create(widths, length: int, cfg: dict, stream=None):
+    """lbfd_batch_create: one Solver for 2-D channels of the given widths
+    stacked along y with a solid row between them; returns (solver, rows)
+    with rows = [(y0, y1), ...] per channel.  cfg gives the face types,
+    mechanism and parameters (its nx, ny are replaced)."""
+    lib = load()
+    widths = [int(w) for w in widths]
+    g, m, p = make_structs(cfg)
+    wa = (ctypes.c_int * len(widths))(*widths)
+    rows = (ctypes.c_int * (2 * len(widths)))()
+    h = ctypes.c_void_p()
+    st = lib.lbfd_batch_create(len(widths), wa, int(length), ctypes.byref(g), ctypes.byref(m), ctypes.byref(p),
+                               ctypes.byref(h), rows)
+    _check(lib, st, "lbfd_batch_create")
+    ny = sum(widths) + len(widths) - 1
+    s = Solver.__new__(Solver)
+    s.lib = lib
+    s.cfg = dict(cfg, nx=int(length), ny=ny, nz=1)
+    s._structs = make_structs(s.cfg)
+    s.h = h
+    s.N = int(lib.lbfd_num_cells(h))
+    s.Q = int(lib.lbfd_num_populations(h))
+    if stream is not None:
+        s.set_stream(stream)
+    return s, [(rows[2 * j], rows[2 * j + 1]) for j in range(len(widths))]
 
 
 def diagnostics_noalloc(cfg: dict, g_ptr: int, T_ptr: int, Y_ptr: int, plane_stride: int, solid_ptr: int,

@@ -57,3 +57,20 @@ def test_create_rejects_unstable_and_invalid_parameters_without_a_gpu():
     assert create(Y_in=[0.5, 0.2, 0.0, 0.0, 0.2]) == lbfd.EINVAL  # sum != 1
     assert create(bc=["periodic", "outlet", "periodic", "periodic", "periodic", "periodic"]) == lbfd.EINVAL
     assert create(nx=0) == lbfd.EINVAL
+
+
+def test_noalloc_entry_point_names_no_allocation():
+    """The allocation-free diagnostics must not allocate: neither its body
+    nor the helpers it calls in its translation unit name an allocating
+    CUDA call."""
+    src = open(os.path.join(ROOT, "paper_2304_05657_gb300", "csrc", "lbfd_api.cu")).read()
+    start = src.index("static __device__ __align__(256) double lbfd_noalloc_scratch")
+    body = src[start:]
+    for name in ("cudaMalloc", "cudaFree", "cudaMallocAsync", "cudaMallocHost", "malloc(", "new "):
+        assert name not in body, name
+    # the reduction it launches clears its own words in the kernel launcher
+    red = open(os.path.join(ROOT, "paper_2304_05657_gb300", "csrc", "lbfd_reduce.cu")).read()
+    for fn in ("static cudaError_t diag_launch(", "cudaError_t launch_diagnostics("):
+        body = red[red.index(fn):]
+        body = body[:body.index("\n}\n")]
+        assert "cudaMalloc" not in body and "cudaFree" not in body, fn
