@@ -45,6 +45,7 @@ struct lbfd_handle {
     long long nbndf;
     long long* bndw;      // 3-D: the others (next to in-domain solids only)
     long long nbndw;
+    unsigned long long* bndw_code;  // 3-D: their neighbourhood codes
     uint8_t* interior;    // per cell, 1 = updated by the interior tile kernels
     void* aux;            // 3-D: Lambda and grad rho planes of the split variants
     int* wtiles;          // tiles holding the other boundary cells (2-D)
@@ -254,6 +255,7 @@ void free_handle(lbfd_handle* h)
     if (h->bnd) cudaFree(h->bnd);
     if (h->bndf) cudaFree(h->bndf);
     if (h->bndw) cudaFree(h->bndw);
+    if (h->bndw_code) cudaFree(h->bndw_code);
     if (h->interior) cudaFree(h->interior);
     if (h->aux) cudaFree(h->aux);
     if (h->wtiles) cudaFree(h->wtiles);
@@ -312,11 +314,13 @@ lbfd::BoundaryLists lists(const lbfd_handle* h)
     b.nwall_tiles = curved ? 0 : h->nwtiles;
     b.wall = nullptr;
     b.nwall = 0;
+    b.wall_code = nullptr;
     if (h->dim == 3) {  // the general form takes curved walls in both lists
         b.face = h->bndf;
         b.nface = h->nbndf;
         b.wall = h->bndw;
         b.nwall = h->nbndw;
+        b.wall_code = h->bndw_code;
     }
     b.interior = h->interior;
     b.aux = h->aux;
@@ -498,9 +502,14 @@ int lbfd_create(const lbfd_grid* grid, const uint8_t* solid_mask, const lbfd_mec
             return cuda_fail(e, "split-step buffers");
         }
         if (!wl.empty()) {
+            std::vector<unsigned long long> codes;
+            lbfd::wall_codes(h->grid.nx, h->grid.ny, h->grid.nz, h->Pd.bc, m.data(), wl, codes);
             if ((e = cudaMalloc(&h->bndw, wl.size() * sizeof(long long))) != cudaSuccess ||
                 (e = cudaMemcpy(h->bndw, wl.data(), wl.size() * sizeof(long long), cudaMemcpyHostToDevice)) !=
-                    cudaSuccess) {
+                    cudaSuccess ||
+                (e = cudaMalloc(&h->bndw_code, codes.size() * sizeof(unsigned long long))) != cudaSuccess ||
+                (e = cudaMemcpy(h->bndw_code, codes.data(), codes.size() * sizeof(unsigned long long),
+                                cudaMemcpyHostToDevice)) != cudaSuccess) {
                 free_handle(h);
                 return cuda_fail(e, "wall list");
             }

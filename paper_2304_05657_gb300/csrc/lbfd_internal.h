@@ -66,6 +66,7 @@ struct BoundaryLists {
     long long nwall_tiles;
     const long long* wall;  // 3-D: all \ face, cells whose stencils reach no non-periodic face
     long long nwall;
+    const unsigned long long* wall_code;  // 3-D: their neighbourhood codes (cell_step_coded)
     const uint8_t* interior;  // per cell, 1 for the cells the interior tile kernels update
     void* aux;                // 3-D: 4 planes of the compute type for the split variants
 };
@@ -85,6 +86,11 @@ int num_variants(int dim);
 cudaError_t launch_step3d_tiled(int precision, int variant, const StepParams<double>& Pd, const StepParams<float>& Pf,
                                 StateView in, StateView out, const uint8_t* solid, const BoundaryLists& b,
                                 const SideStream& side, cudaStream_t stream);
+
+// Neighbourhood codes of the cells of a 3-D wall list (host, at create;
+// layout in cell_step_coded).
+void wall_codes(int nx, int ny, int nz, const int* bc, const uint8_t* solid, const std::vector<long long>& cells,
+                std::vector<unsigned long long>& out);
 
 // Fluid cells that are not interior for the tile kernels (host, at create);
 // faces_only (2-D): only cells whose stencil leaves the domain.

@@ -174,6 +174,47 @@ cudaError_t launch_step(int dim, int precision, int variant, const StepParams<do
     return launch_general<3, float, float>(Pf, in, out, solid, stream);
 }
 
+void wall_codes(int nx, int ny, int nz, const int* bc, const uint8_t* solid, const std::vector<long long>& cells,
+                std::vector<unsigned long long>& out)
+{
+    // every neighbour within reach of a listed cell is inside the domain up
+    // to periodic wrap (the list leaves out the cells near other faces)
+    const int n[3] = {nx, ny, nz};
+    auto at = [&](int x, int y, int z) {
+        x = ((x % nx) + nx) % nx;
+        y = ((y % ny) + ny) % ny;
+        z = ((z % nz) + nz) % nz;
+        return solid[(long long)x + (long long)nx * ((long long)y + (long long)ny * z)] != 0;
+    };
+    (void)bc;
+    (void)n;
+    out.resize(cells.size());
+    for (size_t t = 0; t < cells.size(); ++t) {
+        const long long c = cells[t];
+        const int p[3] = {(int)(c % nx), (int)((c / nx) % ny), (int)(c / ((long long)nx * ny))};
+        unsigned long long code = 0;
+        for (int i = 0; i < 27; ++i)  // the source x - c_i is solid: bounce-back
+            if (at(p[0] - cx_of(i), p[1] - cy_of(i), p[2] - cz_of(i))) code |= 1ull << i;
+        for (int a = 0; a < 3; ++a) {
+            unsigned bits6 = 0;
+            for (int side = -1; side <= 1; side += 2) {
+                int q1[3] = {p[0], p[1], p[2]}, q2[3] = {p[0], p[1], p[2]}, qo[3] = {p[0], p[1], p[2]};
+                q1[a] += side;
+                q2[a] += 2 * side;
+                qo[a] -= side;
+                const unsigned w = at(q1[0], q1[1], q1[2]) ? 1u : (at(q2[0], q2[1], q2[2]) ? 2u : 0u);
+                const unsigned opp = at(qo[0], qo[1], qo[2]) ? 1u : 0u;
+                const unsigned b3 = w | (opp << 2);
+                bits6 |= (side < 0 ? b3 : b3 << 3);
+            }
+            if (!(bits6 & 3u)) bits6 &= ~7u;          // no wall on this side: the flag is unused
+            if (!((bits6 >> 3) & 3u)) bits6 &= ~56u;
+            code |= (unsigned long long)bits6 << (32 + 6 * a);
+        }
+        out[t] = code;
+    }
+}
+
 void boundary_cells(int dim, int nx, int ny, int nz, const int* bc, const uint8_t* solid, std::vector<long long>& out,
                     bool faces_only, const int* face_solid)
 {

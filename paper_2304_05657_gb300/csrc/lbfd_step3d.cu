@@ -6,8 +6,9 @@ namespace lbfd {
 
 // The interior cells go to the tile kernel; on the side stream (same input
 // state, disjoint writes) the general form takes the cells near domain
-// faces (b.face) and, with the face rules compiled out, the cells next to
-// in-domain solids (b.wall).
+// faces (b.face), and the cells next to in-domain solids (b.wall) go
+// through their coded neighbourhoods (or, with curved walls, the general
+// form with the face rules compiled out).
 // the tile kernel instance: MINB > 0 caps its registers for MINB blocks per SM
 template <typename S, typename R, int TX, int TY, int ZC, int MINB>
 static auto tile3_kernel()
@@ -50,8 +51,14 @@ static cudaError_t launch_t3(const StepParams<R>& P, StateView in, StateView out
     }
     if (b.nwall > 0) {
         const unsigned nb = (unsigned)((b.nwall + 127) / 128);
-        e = launch_prio(step_kernel_boundary<3, S, R, false>, dim3(nb), dim3(128), 0, bs, prio, P, (const S*)in.g,
-                        (S*)out.g, (const S*)in.T, (S*)out.T, (const S*)in.Y, (S*)out.Y, solid, b.wall, b.nwall);
+        if (!P.curved && b.wall_code != nullptr)  // staircase walls: the coded neighbourhoods
+            e = launch_prio(step_kernel_wallcode<3, S, R>, dim3(nb), dim3(128), 0, bs, prio, P, (const S*)in.g,
+                            (S*)out.g, (const S*)in.T, (S*)out.T, (const S*)in.Y, (S*)out.Y, b.wall, b.wall_code,
+                            b.nwall);
+        else
+            e = launch_prio(step_kernel_boundary<3, S, R, false>, dim3(nb), dim3(128), 0, bs, prio, P,
+                            (const S*)in.g, (S*)out.g, (const S*)in.T, (S*)out.T, (const S*)in.Y, (S*)out.Y, solid,
+                            b.wall, b.nwall);
         if (e != cudaSuccess) return e;
     }
     dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY, (P.nz + ZC - 1) / ZC);

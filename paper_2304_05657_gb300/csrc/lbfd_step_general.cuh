@@ -443,4 +443,140 @@ __device__ __forceinline__ void cell_step_general(const StepParams<R>& P, const 
     for (int i = 0; i < Q; ++i) g_out[(long long)i * N + c] = S(g[i]);
 }
 
+// ---------------------------------------------------------------------------
+// The same update for a cell next to in-domain solids whose stencils reach
+// no non-periodic face (staircase walls), with its neighbourhood given by a
+// code computed at create instead of mask reads:
+//   bits 0..26   population i is pulled from a solid cell (bounce-back)
+//   bits 32..49  per axis a (6 bits at 32 + 6a), per side (low 3 bits: -,
+//                high 3 bits: +): the distance 1 or 2 of the first solid cell
+//                along the line (0: none within 2) and, in the third bit,
+//                whether the neighbour on the other side is solid
+// so that all loads of the cell can be issued at once.
+// ---------------------------------------------------------------------------
+template <int DIM, typename R>
+__device__ __forceinline__ void coded_line(const StepParams<R>& P, const int p[3], long long c, int a, unsigned code,
+                                           LineDesc<R>& L)
+{
+    // the line's cells (periodic wrap: only periodic faces are in reach),
+    // without indexing an array by the run-time axis
+    const int pa = a == 0 ? p[0] : (a == 1 ? p[1] : p[2]);
+    const int n = a == 0 ? P.nx : (a == 1 ? P.ny : P.nz);
+    const long long stride = a == 0 ? 1LL : (a == 1 ? (long long)P.nx : (long long)P.nx * P.ny);
+    long long raw[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        int qa = pa + j - 2;
+        qa = qa < 0 ? qa + n : (qa >= n ? qa - n : qa);
+        qa = qa < 0 ? qa + n : (qa >= n ? qa - n : qa);  // extents down to 1
+        raw[j] = c + (long long)(qa - pa) * stride;
+        L.src[j] = raw[j];
+        L.mode[j] = G_DIRECT;
+        L.TB[j] = R(0);
+    }
+    L.near = code != 0;
+    const int mode = P.solid_isothermal ? G_DIRICHLET_T : G_NEUMANN;
+#pragma unroll
+    for (int side = -1; side <= 1; side += 2) {
+        const unsigned bits = side < 0 ? (code & 7u) : (code >> 3);
+        const int w = (int)(bits & 3u);
+        if (!w) continue;
+        const bool opp_solid = (bits >> 2) & 1u;
+#pragma unroll
+        for (int j = 1; j <= 2; ++j) {
+            if (j < w) continue;
+            const int m = 2 * w - 1 - j;  // mirror offset on this side (Eq. 34)
+            L.src[2 + side * j] = m >= 0 ? L.src[2 + side * m] : (opp_solid ? c : raw[2 - side]);
+            L.mode[2 + side * j] = mode;
+            L.TB[2 + side * j] = P.T_solid;
+        }
+    }
+}
+
+template <int DIM, typename S, typename R>
+__device__ __forceinline__ void cell_step_coded(const StepParams<R>& P, const int p[3], long long c,
+                                                unsigned long long code, const S* LBFD_RESTRICT g_in,
+                                                S* LBFD_RESTRICT g_out, const S* LBFD_RESTRICT T_in,
+                                                S* LBFD_RESTRICT T_out, const S* LBFD_RESTRICT Y_in,
+                                                S* LBFD_RESTRICT Y_out)
+{
+    constexpr int Q = DIM == 2 ? 9 : 27;
+    const long long N = P.N;
+    const R T0 = R(T_in[c]);
+    R Y0[NSP];
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) Y0[k] = R(Y_in[(long long)k * N + c]);
+    const R invW0 = inv_molar_mass(P, Y0);
+    const R rho0 = eos(P, T0, invW0);
+    // a1: pull, half-way bounce-back (Eq. 28) where the code says solid
+    R g[Q];
+    {
+        const long long plane = (long long)P.nx * P.ny;
+        const long long oxm = p[0] == 0 ? P.nx - 1 : -1, oxp = p[0] == P.nx - 1 ? 1 - P.nx : 1;
+        const long long oym = p[1] == 0 ? (long long)(P.ny - 1) * P.nx : -(long long)P.nx;
+        const long long oyp = p[1] == P.ny - 1 ? (long long)(1 - P.ny) * P.nx : (long long)P.nx;
+        long long ozm = 0, ozp = 0;
+        if (DIM == 3) {
+            ozm = p[2] == 0 ? (P.nz - 1) * plane : -plane;
+            ozp = p[2] == P.nz - 1 ? (1 - P.nz) * plane : plane;
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int cx = ccomp<DIM>(i, 0), cy = ccomp<DIM>(i, 1), cz = ccomp<DIM>(i, 2);
+            const long long s = c + (cx > 0 ? oxm : (cx < 0 ? oxp : 0)) + (cy > 0 ? oym : (cy < 0 ? oyp : 0)) +
+                                (cz > 0 ? ozm : (cz < 0 ? ozp : 0));
+            const bool bb = (code >> i) & 1ull;
+            g[i] = R(g_in[bb ? (long long)opposite<DIM>(i) * N + c : (long long)i * N + s]);
+        }
+    }
+    R u[3] = {R(0), R(0), R(0)};
+    {
+        const R inv = fdiv(R(3), rho0);
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            R m = R(0);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int ci = ccomp<DIM>(i, a);
+                if (ci) m += R(ci) * g[i];
+            }
+            u[a] = m * inv;
+        }
+    }
+    FDAccum<R> acc;
+    acc.conv_T = acc.diff_T = R(0);
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) acc.conv_Y[k] = acc.diff_Y[k] = R(0);
+    acc.grad_rho[0] = acc.grad_rho[1] = acc.grad_rho[2] = R(0);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        LineDesc<R> L;
+        coded_line<DIM, R>(P, p, c, a, (unsigned)(code >> (32 + 6 * a)) & 63u, L);
+        R Tl[5], Yl[NSP][5], invWl[5], rhol[5];
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {  // every point's loads at once
+            R Yj[NSP];
+            line_point<S, R>(P, L, j, T_in, Y_in, Tl[j], Yj, invWl[j], rhol[j]);
+#pragma unroll
+            for (int k = 0; k < NSP; ++k) Yl[k][j] = Yj[k];
+        }
+        fd_axis<R>(P, a, L.near, Tl, Yl, invWl, rhol, u[a], T0, Y0, invW0, rho0, acc);
+    }
+    const R q = arrhenius(P, T0, pick_species(Y0, P.fuel), pick_species(Y0, P.oxid));
+    const R reac_T = P.Q_cp * q;
+    const R DT = acc.diff_T + reac_T;
+    T_out[c] = S(T0 + (DT - acc.conv_T));
+    R lam_Y = R(0);
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) {
+        const R DY = acc.diff_Y[k] + P.yield[k] * q;
+        Y_out[(long long)k * N + c] = S(Y0[k] + (DY - acc.conv_Y[k]));
+        lam_Y += P.inv_Wk[k] * DY;
+    }
+    const R Lam = fdiv(DT, T0) + fdiv(lam_Y, invW0);
+    collide<DIM, R>(P, g, rho0, u, acc.grad_rho, Lam);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) g_out[(long long)i * N + c] = S(g[i]);
+}
+
 }  // namespace lbfd

@@ -456,6 +456,28 @@ __global__ void __launch_bounds__(TX * TY)
                                      threadIdx.y, t % gxn, t / gxn);
 }
 
+// The cells next to in-domain solids of a coded list (staircase walls, no
+// non-periodic face in reach): cell_step_coded
+template <int DIM, typename S, typename R>
+__global__ void __launch_bounds__(128) step_kernel_wallcode(StepParams<R> P, const S* LBFD_RESTRICT g_in,
+                                                            S* LBFD_RESTRICT g_out, const S* LBFD_RESTRICT T_in,
+                                                            S* LBFD_RESTRICT T_out, const S* LBFD_RESTRICT Y_in,
+                                                            S* LBFD_RESTRICT Y_out,
+                                                            const long long* LBFD_RESTRICT cells,
+                                                            const unsigned long long* LBFD_RESTRICT codes,
+                                                            long long ncells)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ncells) return;
+    const long long c = cells[t];
+    int p[3];
+    p[0] = (int)(c % P.nx);
+    const long long r = c / P.nx;
+    p[1] = (int)(r % P.ny);
+    p[2] = (int)(r / P.ny);
+    cell_step_coded<DIM, S, R>(P, p, c, codes[t], g_in, g_out, T_in, T_out, Y_in, Y_out);
+}
+
 // The cells the tiled kernel leaves out: general form over a cell list
 // (FACES == false: cells whose stencils reach no non-periodic face).
 template <int DIM, typename S, typename R, bool FACES = true>
