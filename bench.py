@@ -602,10 +602,11 @@ def secondary(args, flush):
     study = {"widths": widths, "S_F": [float(v) for v in tr.flame_speed(window=11)],
              "burning": [bool(b) for b in burning],
              "quenching_width": channels.quenching_width(widths, burning),
-             "delta_dead": channels.channel_dead_zones(s, seg),
+             "delta_dead": [d if b else None for d, b in zip(channels.channel_dead_zones(s, seg), burning)],
              "note": "lattice units (cells, cells per step), after 10 000 + warm-up + timed steps; S_F = u_in - "
                      "dx_f/dt fitted over 2000 steps; delta_dead: smallest wall distance of the per-column "
-                     "peak heat release over the columns within 10 % of the channel's peak"}
+                     "peak heat release over the columns within 10 % of the channel's peak (null where the "
+                     "channel does not burn)"}
     fluid = int((solid == 0).sum())
     mean_s = float(ms.mean()) * 1e-3
     alg = fluid * bytes_per_cell(cfg) + (solid.size - fluid)
