@@ -193,6 +193,54 @@ def test_mixed_precision_channel_1000_steps(lbfd_lib, oracle_mod):
     assert np.abs(gg - go).max() <= 1e-4 * scale
 
 
+def mixed_vs_oracle_after(lbfd_lib, oracle_mod, cfg, solid, T, Y, steps, variant=None):
+    import os
+
+    s = lbfd_lib.Solver(dict(cfg, precision="mixed"), solid)
+    if variant is not None:
+        s.variant = variant
+    s.set_state(T, Y)
+    s.step_graph(steps)
+    Tg, Yg, gg = s.get_state()
+    s.close()
+    oracle_mod.set_threads(os.cpu_count() or 1)
+    try:
+        o = oracle_mod.Sim(cfg, solid)
+        o.set_state(T, Y)
+        o.step(steps)
+        To, Yo, go = o.get_state()
+    finally:
+        oracle_mod.set_threads(1)
+    fl = solid.ravel() == 0
+    errs = {"T": rel_l2(Tg[fl], To[fl])}
+    for k in range(5):
+        if np.linalg.norm(Yo[k][fl]) > 0:
+            errs[f"Y{k}"] = rel_l2(Yg[k][fl], Yo[k][fl])
+    errs["g"] = np.abs(gg[:, fl] - go[:, fl]).max() / np.abs(go[:, fl]).max()
+    return errs
+
+
+def test_mixed_precision_packing_crop_1000_steps(lbfd_lib, oracle_mod):
+    """The precision bar (fields within 1e-5 relative L2 of the FP64 oracle
+    after 1000 steps) on the 3-D workload's recipe at a size the oracle
+    runs in seconds: a 64x24x24 sphere packing (r in [3, 6]) with its band
+    of burning gas behind it, the autotuner's 3-D variant (2)."""
+    cfg, solid, T, Y = inputs.sphere_packing(nx=64, ny=24, nz=24, x_range=(6, 34), r_range=(3.0, 6.0))
+    assert 0.05 < solid.mean() < 0.2 and (T > 1000.0).any()
+    errs = mixed_vs_oracle_after(lbfd_lib, oracle_mod, cfg, solid, T, Y, 1000, variant=2)
+    assert all(v <= 1e-5 for k, v in errs.items() if k != "g"), errs
+    assert errs["g"] <= 1e-4, errs
+
+
+def test_mixed_precision_batched_channels_1000_steps(lbfd_lib, oracle_mod):
+    """The same bar on packed channels (isothermal walls and separators,
+    closed ignition end), the packed-pair variant 11."""
+    cfg, solid, T, Y, seg = inputs.batched_channels(widths=[16, 40, 64], length=128)
+    errs = mixed_vs_oracle_after(lbfd_lib, oracle_mod, cfg, solid, T, Y, 1000, variant=11)
+    assert all(v <= 1e-5 for k, v in errs.items() if k != "g"), errs
+    assert errs["g"] <= 1e-4, errs
+
+
 # ---------------------------------------------------------------------------
 # kernel variants, graph launches, autotuner
 # ---------------------------------------------------------------------------
