@@ -341,8 +341,10 @@ int lbfd_gradient(lbfd_handle* h, int objective, double* value, double* grad);
  * lbfd_adjoint_gradient: lbfd_adjoint_run with this checkpoint interval
  *   for the one call.
  * Device memory of a backward call: checkpoint_every + 2 state copies and
- *   two FP64 adjoint states, plus a tape of at most 6 GB (26 B x 4096 nodes
- *   per cell, cells in chunks), freed before returning.  All synchronise.
+ *   two FP64 adjoint states, plus tapes of at most 12 GB (20 B x 4096 nodes
+ *   per cell and recorded step, up to 8 steps recorded per launch when they
+ *   fit, else one step with its cells in chunks, and 8 B x 4096 nodes per
+ *   cell for the sweep), freed before returning.  All synchronise.
  * Errors: LBFD_EINVAL (arguments, backward without a record), LBFD_ENOTSUP
  * (other precision, 3-D, curved walls, or a cell whose step needs more than
  * the tape's 4096 nodes), LBFD_ENOMEM. */

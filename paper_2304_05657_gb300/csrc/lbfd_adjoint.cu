@@ -2,7 +2,8 @@
 // lambda^{n+1} of the state after a step, the adjoint lambda^n of the state
 // before it and the contribution to dJ/dtheta, theta = (ln A, Ta, T_wall,
 // u_in).  One thread per fluid cell records the general-form step of its
-// cell on a tape (lbfd_rev.cuh) and sweeps it backwards.
+// cell on a tape (lbfd_rev.cuh), several steps per launch, and one thread per
+// cell sweeps a step's tape backwards.
 #include "lbfd_internal.h"
 #include "lbfd_step_general.cuh"
 #include "lbfd_rev.cuh"
@@ -10,6 +11,10 @@
 namespace lbfd {
 
 constexpr int REV_BLOCK = 64;
+// the adjoints of this many recent tape nodes per thread stay in shared
+// memory during the reverse sweep; the loads of tape entries and of farther
+// adjoints run this many sweeps ahead
+constexpr int REV_WIN = 32, REV_LAG = 8;
 
 // the state (FP64, or the FP32 state of the mixed form widened to FP64) as
 // tape input (values only)
@@ -21,64 +26,149 @@ __global__ void __launch_bounds__(256) to_rev_kernel(long long n, const S* __res
     if (e < n) out[e] = RevStore(Rev((double)in[e]));
 }
 
+// Record: thread t of the launch takes cell c0 + u, u = t % chunk, of the
+// step from the state of slot t / chunk (several steps' tapes are recorded
+// in one launch), and leaves its node count in count[t].
 template <int DIM>
-__global__ void __launch_bounds__(REV_BLOCK)
-    adjoint_kernel(StepParams<Rev> P, const RevStore* __restrict__ in, RevStore* __restrict__ out,
-                   const uint8_t* __restrict__ solid, long long c0, long long n, int planes,
-                   const double* __restrict__ lam_next, double* __restrict__ lam, double* __restrict__ dtheta,
-                   int* __restrict__ max_nodes)
+__global__ void __launch_bounds__(REV_BLOCK, 8)
+    adjoint_record_kernel(StepParams<Rev> P, const RevStore* __restrict__ rin, RevStore* __restrict__ rout,
+                          const uint8_t* __restrict__ solid, long long c0, long long n, long long chunk,
+                          long long nel, int* __restrict__ count)
 {
     constexpr int Q = DIM == 2 ? 9 : 27;
     rev_count_dyn[threadIdx.x] = 0;
     const long long t = rev_thread();
-    const long long c = c0 + t;
-    if (t >= n || c >= P.ncell || solid[c]) return;
-    const long long N = P.N;
-    // forward: the step of cell c, recorded, with theta as parameter leaves
-    {
-        StepParams<Rev> Pl = P;
-        Pl.A_lat = rev_theta(P.A_lat.v, 0, P.A_lat.v);  // d(A dt)/d(ln A)
-        Pl.Ta = rev_theta(P.Ta.v, 1, 1.0);
-        for (int f = 0; f < 6; ++f)
-            if (P.bc[f] == BC_WALL_ISOTHERMAL) Pl.T_wall[f] = rev_theta(P.T_wall[f].v, 2, 1.0);
-        if (P.solid_isothermal) Pl.T_solid = rev_theta(P.T_solid.v, 2, 1.0);
-        Pl.u_in = rev_theta(P.u_in.v, 3, 1.0);
+    const long long slot = t / chunk, u = t - slot * chunk, c = c0 + u;
+    if (u < n && c < P.ncell && !solid[c]) {
+        // theta = (ln A, Ta, T_wall, u_in) are the tape's first four nodes
+        // (parameter leaves), and P names them as the nodes of A dt, Ta, the
+        // isothermal wall and solid temperatures and u_in (rev_params)
+        rev_push(0.0, REV_THETA, P.A_lat.v, REV_NONE);  // d(A dt)/d(ln A) = A dt
+        rev_push(1.0, REV_THETA, 1.0, REV_NONE);
+        rev_push(2.0, REV_THETA, 1.0, REV_NONE);
+        rev_push(3.0, REV_THETA, 1.0, REV_NONE);
+        const long long N = P.N;
+        const RevStore* in = rin + slot * nel;
+        RevStore* out = rout + slot * nel;
         int p[3];
         p[0] = (int)(c % P.nx);
         const long long r = c / P.nx;
         p[1] = (int)(r % P.ny);
         p[2] = (int)(r / P.ny);
-        cell_step_general<DIM, RevStore, Rev>(Pl, p, c, in, out, in + (long long)Q * N, out + (long long)Q * N,
+        cell_step_general<DIM, RevStore, Rev>(P, p, c, in, out, in + (long long)Q * N, out + (long long)Q * N,
                                               in + (long long)(Q + 1) * N, out + (long long)(Q + 1) * N, solid);
     }
-    // reverse sweep: seed the outputs of the cell with lambda^{n+1}
-    const int nn = rev_count_dyn[threadIdx.x];
+    count[t] = rev_count_dyn[threadIdx.x];
+}
+
+// Reverse sweep of the tapes of slot `slot` (threads slot * chunk + u of the
+// record launch, NT threads in all): lam += (dF/dx)^T lam_next, dtheta +=
+// (dF/dtheta)^T lam_next.  The adjoints of the REV_WIN most recent nodes not
+// yet swept live in shared memory (slot k % REV_WIN of this thread), older
+// ones in adj (node k of thread u at k * chunk + u), which the farther
+// children update with atomic adds that nothing waits for (the thread's own
+// later read of the same element sees them).  When node k is swept its slot
+// passes to node k - REV_WIN, whose value in adj is final then: it is loaded
+// at once and added REV_LAG sweeps later.  The tape entries of node
+// k - REV_LAG are loaded when node k is swept, so no sweep waits on a load;
+// theta contributions accumulate in registers.
+__global__ void __launch_bounds__(REV_BLOCK)
+    adjoint_sweep_kernel(const RevStore* __restrict__ out, const uint8_t* __restrict__ solid, long long c0,
+                         long long n, long long ncell, long long N, int planes, long long slot, long long NT,
+                         long long ebase, const int* __restrict__ count, const double* __restrict__ lam_next,
+                         double* __restrict__ lam, double* __restrict__ dtheta, double* __restrict__ adj_buf,
+                         int* __restrict__ max_nodes)
+{
+    extern __shared__ double win_dyn[];
+    const long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned chunk = gridDim.x * blockDim.x;
+    const long long c = c0 + u;
+    if (u >= n || c >= ncell || solid[c]) return;
+    const long long t = slot * chunk + u;
+    const int nn = count[t];
     atomicMax(max_nodes, nn);
-    const long long NT = rev_threads();
-    double* adj = rev_tape.adj + t;
-    for (int k = 0; k < nn; ++k) adj[(long long)k * NT] = 0.0;
-    for (int j = 0; j < planes; ++j) {
+    // node offsets in the tape (k * NT) and in adj (k * chunk) fit 32 bits
+    // (the host keeps maxn * NT below 2^32)
+    double* adj = adj_buf + u;
+    double* win = win_dyn + threadIdx.x;
+    constexpr unsigned WM = REV_WIN - 1;
+    for (int k = 0; k < nn - REV_WIN; ++k) adj[(unsigned)k * chunk] = 0.0;
+#pragma unroll
+    for (int j = 0; j < REV_WIN; ++j) win[j * REV_BLOCK] = 0.0;
+    for (int j = 0; j < planes; ++j) {  // seed the outputs of the cell with lambda^{n+1}
         const long long e = (long long)j * N + c;
         const int node = out[e].i - 1;
-        if (node >= 0) adj[(long long)node * NT] += lam_next[e];
+        if (node < 0) continue;
+        if (node >= nn - REV_WIN) win[((unsigned)node & WM) * REV_BLOCK] += lam_next[e];
+        else adj[(unsigned)node * chunk] += lam_next[e];
     }
     const double* a0 = rev_tape.a0 + t;
     const double* a1 = rev_tape.a1 + t;
-    const int16_t* p0 = rev_tape.p0 + t;
-    const int16_t* p1 = rev_tape.p1 + t;
-    for (int k = nn - 1; k >= 0; --k) {
-        const long long at = (long long)k * NT;
-        const double a = adj[at];
-        if (a == 0.0) continue;
-        const int q0 = p0[at], q1 = p1[at];
-        if (q0 >= 0) adj[(long long)q0 * NT] += a * a0[at];
-        else if (q0 == REV_STATE) atomicAdd(&lam[__double_as_longlong(a0[at])], a);
-        else if (q0 == REV_THETA) atomicAdd(&dtheta[(int)a0[at]], a * a1[at]);
-        if (q1 >= 0) adj[(long long)q1 * NT] += a * a1[at];
+    const int32_t* par = rev_tape.par + t;
+    double th0 = 0.0, th1 = 0.0, th2 = 0.0, th3 = 0.0;
+    // queue slot j holds, while node k = k0 - j is swept, its tape entry and
+    // the adj value of node k + REV_LAG - REV_WIN
+    double lag[REV_LAG], qa0[REV_LAG], qa1[REV_LAG];
+    int32_t qp[REV_LAG];
+#pragma unroll
+    for (int j = 0; j < REV_LAG; ++j) {
+        const int k = nn - 1 - j;
+        lag[j] = qa0[j] = qa1[j] = 0.0;
+        qp[j] = -1;  // both parents REV_NONE
+        if (k >= 0) {
+            const unsigned at = (unsigned)k * (unsigned)NT;
+            qp[j] = par[at];
+            qa0[j] = a0[at];
+            qa1[j] = a1[at];
+        }
     }
+    auto add = [&](int q, int k, double x) {
+        if (q >= k - REV_WIN) win[((unsigned)q & WM) * REV_BLOCK] += x;
+        else atomicAdd(&adj[(unsigned)q * chunk], x);
+    };
+    for (int k0 = nn - 1; k0 >= 0; k0 -= REV_LAG) {
+#pragma unroll
+        for (int j = 0; j < REV_LAG; ++j) {
+            const int k = k0 - j;
+            if (k < 0) break;
+            if (k + REV_LAG - REV_WIN >= 0) win[((unsigned)(k + REV_LAG) & WM) * REV_BLOCK] += lag[j];
+            double* ws = win + ((unsigned)k & WM) * REV_BLOCK;
+            const double a = *ws;
+            *ws = 0.0;  // from now on the slot of node k - REV_WIN
+            lag[j] = k >= REV_WIN ? adj[(unsigned)(k - REV_WIN) * chunk] : 0.0;
+            const int q0 = (int16_t)(qp[j] & 0xffff), q1 = qp[j] >> 16;
+            const double x0 = qa0[j], x1 = qa1[j];
+            if (k >= REV_LAG) {
+                const unsigned at = (unsigned)(k - REV_LAG) * (unsigned)NT;
+                qp[j] = par[at];
+                qa0[j] = a0[at];
+                qa1[j] = a1[at];
+            }
+            if (a == 0.0) continue;
+            if (q0 >= 0) {
+                add(q0, k, a * x0);
+            } else if (q0 == REV_STATE) {
+                atomicAdd(&lam[__double_as_longlong(x0) - ebase], a);
+            } else if (q0 == REV_THETA) {
+                const double d = a * x1;
+                const int m = (int)x0;
+                th0 += m == 0 ? d : 0.0;
+                th1 += m == 1 ? d : 0.0;
+                th2 += m == 2 ? d : 0.0;
+                th3 += m == 3 ? d : 0.0;
+            }
+            if (q1 >= 0) add(q1, k, a * x1);
+        }
+    }
+    if (th0 != 0.0) atomicAdd(&dtheta[0], th0);
+    if (th1 != 0.0) atomicAdd(&dtheta[1], th1);
+    if (th2 != 0.0) atomicAdd(&dtheta[2], th2);
+    if (th3 != 0.0) atomicAdd(&dtheta[3], th3);
 }
 
-// the parameters as reverse-mode constants (theta becomes leaves per cell)
+// the parameters as reverse-mode constants, except those that depend on
+// theta: they name the parameter leaves that each thread pushes first (node
+// 0: A dt, 1: Ta, 2: the isothermal wall and solid temperatures, 3: u_in)
 static StepParams<Rev> rev_params(const StepParams<double>& D)
 {
     StepParams<Rev> P;
@@ -91,7 +181,7 @@ static StepParams<Rev> rev_params(const StepParams<double>& D)
     P.N = D.N;
     for (int f = 0; f < 6; ++f) {
         P.bc[f] = D.bc[f];
-        P.T_wall[f] = Rev(D.T_wall[f]);
+        P.T_wall[f] = D.bc[f] == BC_WALL_ISOTHERMAL ? Rev(D.T_wall[f], 2) : Rev(D.T_wall[f]);
         P.face_solid[f] = D.face_solid[f];
     }
     for (int k = 0; k < NSP; ++k) {
@@ -103,8 +193,8 @@ static StepParams<Rev> rev_params(const StepParams<double>& D)
     }
     P.fuel = D.fuel;
     P.oxid = D.oxid;
-    P.A_lat = Rev(D.A_lat);
-    P.Ta = Rev(D.Ta);
+    P.A_lat = Rev(D.A_lat, 0);
+    P.Ta = Rev(D.Ta, 1);
     P.Q_cp = Rev(D.Q_cp);
     P.A_lat_d = D.A_lat_d;
     P.Ta_d = D.Ta_d;
@@ -115,11 +205,11 @@ static StepParams<Rev> rev_params(const StepParams<double>& D)
     P.alpha = Rev(D.alpha);
     P.alpha12 = Rev(D.alpha12);
     P.lam_yield = Rev(D.lam_yield);
-    P.u_in = Rev(D.u_in);
+    P.u_in = Rev(D.u_in, 3);
     P.T_in = Rev(D.T_in);
     P.invW_in = Rev(D.invW_in);
     P.rho_in = Rev(D.rho_in);
-    P.T_solid = Rev(D.T_solid);
+    P.T_solid = D.solid_isothermal ? Rev(D.T_solid, 2) : Rev(D.T_solid);
     P.solid_isothermal = D.solid_isothermal;
     P.poiseuille = D.poiseuille;
     P.epsY = Rev(D.epsY);
@@ -133,46 +223,62 @@ static StepParams<Rev> rev_params(const StepParams<double>& D)
     return P;
 }
 
-size_t adjoint_node_bytes() { return 2 * sizeof(double) + 2 * sizeof(int16_t) + sizeof(double); }
+size_t adjoint_node_bytes() { return 2 * sizeof(double) + sizeof(int32_t); }
 size_t rev_store_bytes() { return sizeof(RevStore); }
 
-cudaError_t launch_adjoint_step(int dim, const StepParams<double>& Pd, int planes, const void* state, bool fp32,
-                                const uint8_t* solid, const double* lam_next, double* lam, double* dtheta,
-                                const AdjointWork& w, cudaStream_t stream)
+cudaError_t launch_adjoint_record(int dim, const StepParams<double>& Pd, int planes, const void* states,
+                                  size_t state_bytes, int slots, bool fp32, const uint8_t* solid, long long c0,
+                                  long long n, const AdjointWork& w, cudaStream_t stream)
 {
-    if (dim != 2) return cudaErrorInvalidValue;
+    if (dim != 2 || slots < 1 || slots > w.slots) return cudaErrorInvalidValue;
     const long long nel = (long long)planes * Pd.N;
     RevStore* rin = (RevStore*)w.rin;
-    RevStore* rout = (RevStore*)w.rout;
+    cudaError_t e;
     const unsigned nb = (unsigned)((nel + 255) / 256);
-    if (fp32)
-        to_rev_kernel<float><<<nb, 256, 0, stream>>>(nel, (const float*)state, rin);
-    else
-        to_rev_kernel<double><<<nb, 256, 0, stream>>>(nel, (const double*)state, rin);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    for (int j = 0; j < slots; ++j) {
+        const char* st = (const char*)states + (size_t)j * state_bytes;
+        if (fp32)
+            to_rev_kernel<float><<<nb, 256, 0, stream>>>(nel, (const float*)st, rin + (long long)j * nel);
+        else
+            to_rev_kernel<double><<<nb, 256, 0, stream>>>(nel, (const double*)st, rin + (long long)j * nel);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     RevTape tp;
     tp.a0 = w.a0;
     tp.a1 = w.a1;
-    tp.p0 = w.p0;
-    tp.p1 = w.p1;
-    tp.adj = w.adj;
+    tp.par = w.par;
     tp.in_base = rin;
     tp.maxn = w.maxn;
     tp.overflow = w.flags;
     if ((e = cudaMemcpyToSymbolAsync(rev_tape, &tp, sizeof tp, 0, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
         return e;
     const StepParams<Rev> P = rev_params(Pd);
-    for (long long c0 = 0; c0 < Pd.ncell; c0 += w.chunk) {
-        const long long n = Pd.ncell - c0 < w.chunk ? Pd.ncell - c0 : w.chunk;
-        // the tape is sized for w.chunk threads: launch that many (idle ones
-        // return at once) so that the interleaved layout has a fixed stride
-        const unsigned blocks = (unsigned)((w.chunk + REV_BLOCK - 1) / REV_BLOCK);
-        adjoint_kernel<2><<<blocks, REV_BLOCK, REV_BLOCK * sizeof(int), stream>>>(
-            P, rin, rout, solid, c0, n, planes, lam_next, lam, dtheta, w.flags + 1);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    // the tape is sized for w.slots * w.chunk threads: launch that many per
+    // slot (idle ones return at once) so that the interleaved layout has a
+    // fixed stride
+    const unsigned blocks = (unsigned)((w.slots * w.chunk + REV_BLOCK - 1) / REV_BLOCK);
+    adjoint_record_kernel<2><<<blocks, REV_BLOCK, REV_BLOCK * sizeof(int), stream>>>(
+        P, rin, (RevStore*)w.rout, solid, c0, n, w.chunk, nel, w.count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_sweep(const StepParams<double>& Pd, int planes, int slot, const uint8_t* solid,
+                                 long long c0, long long n, const double* lam_next, double* lam, double* dtheta,
+                                 const AdjointWork& w, cudaStream_t stream)
+{
+    if (slot < 0 || slot >= w.slots) return cudaErrorInvalidValue;
+    if ((unsigned long long)w.maxn * w.slots * w.chunk >= (1ull << 32)) return cudaErrorInvalidValue;  // 32-bit offsets
+    const long long nel = (long long)planes * Pd.N;
+    constexpr size_t smem = REV_BLOCK * REV_WIN * sizeof(double);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(adjoint_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
+        return e;
+    const unsigned blocks = (unsigned)(w.chunk / REV_BLOCK);
+    adjoint_sweep_kernel<<<blocks, REV_BLOCK, smem, stream>>>(
+        (const RevStore*)w.rout + slot * nel, solid, c0, n, Pd.ncell, Pd.N, planes, slot,
+        (long long)w.slots * w.chunk, slot * nel, w.count, lam_next, lam, dtheta, w.adj, w.flags + 1);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

@@ -1074,16 +1074,29 @@ int lbfd_adjoint_backward(lbfd_handle* h, double seed, double* grad)
     const size_t lbytes = h->planes * (size_t)h->stride * sizeof(double);  // an adjoint state, FP64
     const long long nel = (long long)h->planes * h->stride;
     const int planes = (int)h->planes;
-    // tape: at most 6 GB, in chunks of cells
+    // tapes: at most 12 GB.  Several steps per record launch when one
+    // step's tape fits several times (more threads in flight than cells),
+    // else one step in chunks of cells.
     lbfd::AdjointWork w;
     memset(&w, 0, sizeof w);
     w.maxn = 4096;
+    const size_t budget = (size_t)12 << 30;
     const size_t node = lbfd::adjoint_node_bytes();
-    long long chunk = (long long)((size_t)6 << 30) / ((long long)w.maxn * (long long)node);
-    chunk = chunk / 64 * 64;
     const long long need = (h->ncell + 63) / 64 * 64;
-    w.chunk = chunk < need ? chunk : need;
-    const size_t tape = (size_t)w.maxn * w.chunk;
+    const size_t far = (size_t)w.maxn * sizeof(double);  // adj, per thread
+    const size_t per_slot = (size_t)need * ((size_t)w.maxn * node + sizeof(int)) + 2 * nel * lbfd::rev_store_bytes();
+    if ((size_t)need * far + per_slot <= budget) {
+        w.chunk = need;
+        const size_t fit = (budget - (size_t)need * far) / per_slot;
+        w.slots = (int)(fit < (size_t)K ? fit : (size_t)K);
+        if (w.slots > 8) w.slots = 8;
+    } else {
+        long long chunk = (long long)((budget - 2 * nel * lbfd::rev_store_bytes()) /
+                                      ((size_t)w.maxn * node + sizeof(int) + far));
+        w.chunk = chunk / 64 * 64;
+        w.slots = 1;
+    }
+    const size_t tape = (size_t)w.maxn * w.chunk * w.slots;
     char* seg = nullptr;
     double *lam0 = nullptr, *lam1 = nullptr, *dth = nullptr;
     std::vector<void*> owned;
@@ -1100,13 +1113,13 @@ int lbfd_adjoint_backward(lbfd_handle* h, double seed, double* grad)
     if ((e = alloc((void**)&seg, sbytes * K)) != cudaSuccess || (e = alloc((void**)&lam0, lbytes)) != cudaSuccess ||
         (e = alloc((void**)&lam1, lbytes)) != cudaSuccess ||
         (e = alloc((void**)&dth, lbfd::NTAN * sizeof(double))) != cudaSuccess ||
-        (e = alloc(&w.rin, nel * lbfd::rev_store_bytes())) != cudaSuccess ||
-        (e = alloc(&w.rout, nel * lbfd::rev_store_bytes())) != cudaSuccess ||
+        (e = alloc(&w.rin, w.slots * nel * lbfd::rev_store_bytes())) != cudaSuccess ||
+        (e = alloc(&w.rout, w.slots * nel * lbfd::rev_store_bytes())) != cudaSuccess ||
         (e = alloc((void**)&w.a0, tape * sizeof(double))) != cudaSuccess ||
         (e = alloc((void**)&w.a1, tape * sizeof(double))) != cudaSuccess ||
-        (e = alloc((void**)&w.adj, tape * sizeof(double))) != cudaSuccess ||
-        (e = alloc((void**)&w.p0, tape * sizeof(int16_t))) != cudaSuccess ||
-        (e = alloc((void**)&w.p1, tape * sizeof(int16_t))) != cudaSuccess ||
+        (e = alloc((void**)&w.par, tape * sizeof(int32_t))) != cudaSuccess ||
+        (e = alloc((void**)&w.count, w.slots * w.chunk * sizeof(int))) != cudaSuccess ||
+        (e = alloc((void**)&w.adj, (size_t)w.maxn * w.chunk * sizeof(double))) != cudaSuccess ||
         (e = alloc((void**)&w.flags, 2 * sizeof(int))) != cudaSuccess) {
         release();
         cuda_fail(e, "cudaMalloc(adjoint)");
@@ -1155,11 +1168,27 @@ int lbfd_adjoint_backward(lbfd_handle* h, double seed, double* grad)
             AK(lbfd::launch_step(h->dim, h->precision, h->variant, h->Pd, h->Pf,
                                  view_of(h, seg + (size_t)(j - 1) * sbytes), view_of(h, seg + (size_t)j * sbytes),
                                  h->solid, b, h->side, s));
-        for (int j = len - 1; j >= 0; --j) {
-            AK(cudaMemsetAsync(lam0, 0, lbytes, s));
-            AK(lbfd::launch_adjoint_step(h->dim, h->Pd, planes, seg + (size_t)j * sbytes, fp32, h->solid, lam1, lam0,
-                                         dth, w, s));
-            std::swap(lam0, lam1);
+        for (int j1 = len - 1; j1 >= 0; j1 -= w.slots) {
+            const int j0 = j1 - w.slots + 1 > 0 ? j1 - w.slots + 1 : 0;
+            if (w.chunk >= h->ncell) {  // the steps j0..j1 recorded at once, then swept one by one
+                AK(lbfd::launch_adjoint_record(h->dim, h->Pd, planes, seg + (size_t)j0 * sbytes, sbytes, j1 - j0 + 1,
+                                               fp32, h->solid, 0, h->ncell, w, s));
+                for (int j = j1; j >= j0; --j) {
+                    AK(cudaMemsetAsync(lam0, 0, lbytes, s));
+                    AK(lbfd::launch_adjoint_sweep(h->Pd, planes, j - j0, h->solid, 0, h->ncell, lam1, lam0, dth, w,
+                                                  s));
+                    std::swap(lam0, lam1);
+                }
+            } else {  // one step (j0 == j1), recorded and swept in chunks of cells
+                AK(cudaMemsetAsync(lam0, 0, lbytes, s));
+                for (long long c0 = 0; c0 < h->ncell; c0 += w.chunk) {
+                    const long long n = h->ncell - c0 < w.chunk ? h->ncell - c0 : w.chunk;
+                    AK(lbfd::launch_adjoint_record(h->dim, h->Pd, planes, seg + (size_t)j1 * sbytes, sbytes, 1, fp32,
+                                                   h->solid, c0, n, w, s));
+                    AK(lbfd::launch_adjoint_sweep(h->Pd, planes, 0, h->solid, c0, n, lam1, lam0, dth, w, s));
+                }
+                std::swap(lam0, lam1);
+            }
         }
     }
     int flags[2];

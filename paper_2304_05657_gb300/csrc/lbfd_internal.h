@@ -130,27 +130,35 @@ cudaError_t launch_objective(const StepParams<Tan>& P, StateView st, const uint8
 cudaError_t launch_objective(const StepParams<Tanf>& P, StateView st, const uint8_t* solid, int objective,
                              const double* wgt, double* red, cudaStream_t stream);
 
-// Discrete adjoint of one FP64 step (lbfd_adjoint.cu): scratch of the
-// reverse-mode tape, node k of thread t at k * chunk + t.
+// Discrete adjoint of FP64 steps (lbfd_adjoint.cu): scratch of the
+// reverse-mode tapes.  A record launch takes the steps of `slots` states at
+// once (thread t = slot * chunk + u: cell c0 + u), node k of thread t at
+// k * slots * chunk + t; a sweep takes one slot.
 struct AdjointWork {
-    void* rin;   // the input state as tape input (planes * N elements)
-    void* rout;  // the recorded outputs
+    void* rin;   // the input states as tape input (slots * planes * N elements)
+    void* rout;  // the recorded outputs (as many)
     double* a0;
     double* a1;
-    int16_t* p0;
-    int16_t* p1;
-    double* adj;
+    int32_t* par;
+    int* count;       // [slots * chunk] nodes each thread recorded
+    double* adj;      // [maxn][chunk] adjoints of the far nodes during a sweep
     int maxn;         // nodes per thread
-    long long chunk;  // threads (cells) per launch, a multiple of 64
+    int slots;        // steps recorded per launch
+    long long chunk;  // threads (cells) per slot, a multiple of 64
     int* flags;       // [0] tape overflow, [1] most nodes a thread used
 };
-size_t adjoint_node_bytes();
+size_t adjoint_node_bytes();  // tape bytes per node and slot
 size_t rev_store_bytes();
-// lam (zeroed by the caller) += (dF/dx)^T lam_next, dtheta += (dF/dtheta)^T
-// lam_next for the step F taken from `state` (planes of N doubles)
-cudaError_t launch_adjoint_step(int dim, const StepParams<double>& Pd, int planes, const void* state, bool fp32,
-                                const uint8_t* solid, const double* lam_next, double* lam, double* dtheta,
-                                const AdjointWork& w, cudaStream_t stream);
+// record the steps from `slots` states (slot j at states + j * state_bytes,
+// storage precision) for the cells [c0, c0 + n)
+cudaError_t launch_adjoint_record(int dim, const StepParams<double>& Pd, int planes, const void* states,
+                                  size_t state_bytes, int slots, bool fp32, const uint8_t* solid, long long c0,
+                                  long long n, const AdjointWork& w, cudaStream_t stream);
+// sweep the tapes of slot `slot` for the cells [c0, c0 + n): lam (zeroed by
+// the caller) += (dF/dx)^T lam_next, dtheta += (dF/dtheta)^T lam_next
+cudaError_t launch_adjoint_sweep(const StepParams<double>& Pd, int planes, int slot, const uint8_t* solid,
+                                 long long c0, long long n, const double* lam_next, double* lam, double* dtheta,
+                                 const AdjointWork& w, cudaStream_t stream);
 // quenching-distance objective J = (S1/S0)^(-1/4), S0 = sum_fluid h,
 // S1 = sum_fluid h w (h the heat release of a cell, w = d^-4 its wall
 // weight): red[0..1] = S0, S1 of state st; and the adjoint seed
