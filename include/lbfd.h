@@ -341,13 +341,15 @@ int lbfd_gradient(lbfd_handle* h, int objective, double* value, double* grad);
  * lbfd_adjoint_gradient: lbfd_adjoint_run with this checkpoint interval
  *   for the one call.
  * Device memory of a backward call: checkpoint_every + 2 state copies and
- *   two FP64 adjoint states, plus tapes of at most 12 GB (20 B x 4096 nodes
- *   per cell and recorded step, up to 8 steps recorded per launch when they
- *   fit, else one step with its cells in chunks, and 8 B x 4096 nodes per
- *   cell for the sweep), freed before returning.  All synchronise.
+ *   two FP64 adjoint states, plus tapes of at most 12 GB: 20 B x 2048 nodes
+ *   per cell and recorded step, in two buffers of up to 4 steps each (one
+ *   recorded while the other is swept) when they fit, else one step with
+ *   its cells in chunks; and 8 B x 2048 nodes per cell for the sweep.  A
+ *   step that needs more nodes is taken again with 4096.  Freed before
+ *   returning.  All synchronise.
  * Errors: LBFD_EINVAL (arguments, backward without a record), LBFD_ENOTSUP
  * (other precision, 3-D, curved walls, or a cell whose step needs more than
- * the tape's 4096 nodes), LBFD_ENOMEM. */
+ * 4096 nodes), LBFD_ENOMEM. */
 int lbfd_adjoint_setup(lbfd_handle* h, int checkpoint_every);
 int lbfd_adjoint_record(lbfd_handle* h, int steps, int objective, double* value);
 int lbfd_adjoint_backward(lbfd_handle* h, double seed, double* grad);

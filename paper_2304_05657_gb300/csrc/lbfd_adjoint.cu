@@ -77,7 +77,8 @@ __global__ void __launch_bounds__(REV_BLOCK)
                          long long n, long long ncell, long long N, int planes, long long slot, long long NT,
                          long long ebase, const int* __restrict__ count, const double* __restrict__ lam_next,
                          double* __restrict__ lam, double* __restrict__ dtheta, double* __restrict__ adj_buf,
-                         int* __restrict__ max_nodes)
+                         const double* __restrict__ tape_a0, const double* __restrict__ tape_a1,
+                         const int32_t* __restrict__ tape_par, int* __restrict__ max_nodes)
 {
     extern __shared__ double win_dyn[];
     const long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -102,9 +103,9 @@ __global__ void __launch_bounds__(REV_BLOCK)
         if (node >= nn - REV_WIN) win[((unsigned)node & WM) * REV_BLOCK] += lam_next[e];
         else adj[(unsigned)node * chunk] += lam_next[e];
     }
-    const double* a0 = rev_tape.a0 + t;
-    const double* a1 = rev_tape.a1 + t;
-    const int32_t* par = rev_tape.par + t;
+    const double* a0 = tape_a0 + t;
+    const double* a1 = tape_a1 + t;
+    const int32_t* par = tape_par + t;
     double th0 = 0.0, th1 = 0.0, th2 = 0.0, th3 = 0.0;
     // queue slot j holds, while node k = k0 - j is swept, its tape entry and
     // the adj value of node k + REV_LAG - REV_WIN
@@ -277,7 +278,8 @@ cudaError_t launch_adjoint_sweep(const StepParams<double>& Pd, int planes, int s
     const unsigned blocks = (unsigned)(w.chunk / REV_BLOCK);
     adjoint_sweep_kernel<<<blocks, REV_BLOCK, smem, stream>>>(
         (const RevStore*)w.rout + slot * nel, solid, c0, n, Pd.ncell, Pd.N, planes, slot,
-        (long long)w.slots * w.chunk, slot * nel, w.count, lam_next, lam, dtheta, w.adj, w.flags + 1);
+        (long long)w.slots * w.chunk, slot * nel, w.count, lam_next, lam, dtheta, w.adj, w.a0, w.a1, w.par,
+        w.flags + 1);
     return cudaGetLastError();
 }
 

@@ -1062,11 +1062,13 @@ int lbfd_adjoint_record(lbfd_handle* h, int steps, int objective, double* value)
     return LBFD_OK;
 }
 
-int lbfd_adjoint_backward(lbfd_handle* h, double seed, double* grad)
+// One backward sweep with tapes of maxn nodes per thread; *overflow is set
+// when a cell's step needed more.  The tapes of groups of steps are recorded
+// on a second stream into two alternating buffers while the steps of the
+// previous group are swept on the handle's stream (the record is bound by
+// FP64 arithmetic, the sweep by latency: together they share the SMs).
+static int adjoint_backward_pass(lbfd_handle* h, double seed, int maxn, double* grad, bool* overflow)
 {
-    NvtxRange nvtx_("lbfd_adjoint_backward");
-    if (!h || !grad) return LBFD_EINVAL;
-    if (!h->adj_ck || h->adj_steps < 1) return LBFD_EINVAL;  // nothing recorded
     const int steps = h->adj_steps, nseg = h->adj_nseg;
     const int K = h->adj_K < steps ? h->adj_K : steps;
     const bool fp32 = h->precision == LBFD_MIXED;
@@ -1074,31 +1076,39 @@ int lbfd_adjoint_backward(lbfd_handle* h, double seed, double* grad)
     const size_t lbytes = h->planes * (size_t)h->stride * sizeof(double);  // an adjoint state, FP64
     const long long nel = (long long)h->planes * h->stride;
     const int planes = (int)h->planes;
-    // tapes: at most 12 GB.  Several steps per record launch when one
-    // step's tape fits several times (more threads in flight than cells),
-    // else one step in chunks of cells.
-    lbfd::AdjointWork w;
-    memset(&w, 0, sizeof w);
-    w.maxn = 4096;
+    // tapes: at most 12 GB.  When a step's tapes fit several times, two
+    // buffers of several steps each (recorded per launch); else one step
+    // recorded and swept in chunks of cells.
+    lbfd::AdjointWork w[2];
+    memset(w, 0, sizeof w);
     const size_t budget = (size_t)12 << 30;
     const size_t node = lbfd::adjoint_node_bytes();
     const long long need = (h->ncell + 63) / 64 * 64;
-    const size_t far = (size_t)w.maxn * sizeof(double);  // adj, per thread
-    const size_t per_slot = (size_t)need * ((size_t)w.maxn * node + sizeof(int)) + 2 * nel * lbfd::rev_store_bytes();
-    if ((size_t)need * far + per_slot <= budget) {
-        w.chunk = need;
-        const size_t fit = (budget - (size_t)need * far) / per_slot;
-        w.slots = (int)(fit < (size_t)K ? fit : (size_t)K);
-        if (w.slots > 8) w.slots = 8;
+    const size_t far = (size_t)maxn * sizeof(double);  // adj, per thread
+    const size_t per_slot = (size_t)need * ((size_t)maxn * node + sizeof(int)) + 2 * nel * lbfd::rev_store_bytes();
+    int nbuf = 1;
+    w[0].maxn = maxn;
+    if ((size_t)need * far + 2 * per_slot <= budget) {
+        w[0].chunk = need;
+        const size_t fit = (budget - (size_t)need * far) / (2 * per_slot);
+        w[0].slots = (int)(fit < (size_t)K ? fit : (size_t)K);
+        if (w[0].slots > 4) w[0].slots = 4;
+        nbuf = K > w[0].slots ? 2 : 1;
     } else {
         long long chunk = (long long)((budget - 2 * nel * lbfd::rev_store_bytes()) /
-                                      ((size_t)w.maxn * node + sizeof(int) + far));
-        w.chunk = chunk / 64 * 64;
-        w.slots = 1;
+                                      ((size_t)maxn * node + sizeof(int) + far));
+        w[0].chunk = chunk / 64 * 64;
+        w[0].slots = 1;
     }
-    const size_t tape = (size_t)w.maxn * w.chunk * w.slots;
+    w[1].maxn = maxn;
+    w[1].chunk = w[0].chunk;
+    w[1].slots = w[0].slots;
+    const size_t tape = (size_t)maxn * w[0].chunk * w[0].slots;
+    const bool pipelined = w[0].chunk >= h->ncell;
     char* seg = nullptr;
     double *lam0 = nullptr, *lam1 = nullptr, *dth = nullptr;
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t ev[5] = {};  // records done (2), sweeps done (2), segment ready
     std::vector<void*> owned;
     auto alloc = [&](void** p, size_t bytes) {
         cudaError_t e = cudaMalloc(p, bytes);
@@ -1106,25 +1116,36 @@ int lbfd_adjoint_backward(lbfd_handle* h, double seed, double* grad)
         return e;
     };
     auto release = [&]() {
+        if (s2) cudaStreamSynchronize(s2);
+        cudaStreamSynchronize(h->stream);
         for (void* p : owned) cudaFree(p);
-        adjoint_release(h);
+        for (cudaEvent_t x : ev)
+            if (x) cudaEventDestroy(x);
+        if (s2) cudaStreamDestroy(s2);
     };
-    cudaError_t e;
+    cudaError_t e = cudaSuccess;
     if ((e = alloc((void**)&seg, sbytes * K)) != cudaSuccess || (e = alloc((void**)&lam0, lbytes)) != cudaSuccess ||
         (e = alloc((void**)&lam1, lbytes)) != cudaSuccess ||
         (e = alloc((void**)&dth, lbfd::NTAN * sizeof(double))) != cudaSuccess ||
-        (e = alloc(&w.rin, w.slots * nel * lbfd::rev_store_bytes())) != cudaSuccess ||
-        (e = alloc(&w.rout, w.slots * nel * lbfd::rev_store_bytes())) != cudaSuccess ||
-        (e = alloc((void**)&w.a0, tape * sizeof(double))) != cudaSuccess ||
-        (e = alloc((void**)&w.a1, tape * sizeof(double))) != cudaSuccess ||
-        (e = alloc((void**)&w.par, tape * sizeof(int32_t))) != cudaSuccess ||
-        (e = alloc((void**)&w.count, w.slots * w.chunk * sizeof(int))) != cudaSuccess ||
-        (e = alloc((void**)&w.adj, (size_t)w.maxn * w.chunk * sizeof(double))) != cudaSuccess ||
-        (e = alloc((void**)&w.flags, 2 * sizeof(int))) != cudaSuccess) {
+        (e = alloc((void**)&w[0].adj, (size_t)maxn * w[0].chunk * sizeof(double))) != cudaSuccess ||
+        (e = alloc((void**)&w[0].flags, 2 * sizeof(int))) != cudaSuccess) {
         release();
         cuda_fail(e, "cudaMalloc(adjoint)");
         return LBFD_ENOMEM;
     }
+    w[1].adj = w[0].adj;
+    w[1].flags = w[0].flags;
+    for (int i = 0; i < nbuf; ++i)
+        if ((e = alloc(&w[i].rin, w[i].slots * nel * lbfd::rev_store_bytes())) != cudaSuccess ||
+            (e = alloc(&w[i].rout, w[i].slots * nel * lbfd::rev_store_bytes())) != cudaSuccess ||
+            (e = alloc((void**)&w[i].a0, tape * sizeof(double))) != cudaSuccess ||
+            (e = alloc((void**)&w[i].a1, tape * sizeof(double))) != cudaSuccess ||
+            (e = alloc((void**)&w[i].par, tape * sizeof(int32_t))) != cudaSuccess ||
+            (e = alloc((void**)&w[i].count, w[i].slots * w[i].chunk * sizeof(int))) != cudaSuccess) {
+            release();
+            cuda_fail(e, "cudaMalloc(adjoint)");
+            return LBFD_ENOMEM;
+        }
     cudaStream_t s = h->stream;
 #define AK(call)                         \
     do {                                 \
@@ -1134,7 +1155,12 @@ int lbfd_adjoint_backward(lbfd_handle* h, double seed, double* grad)
             return cuda_fail(e_, #call); \
         }                                \
     } while (0)
-    AK(cudaMemsetAsync(w.flags, 0, 2 * sizeof(int), s));
+    if (nbuf == 2) {
+        AK(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+        for (cudaEvent_t& x : ev) AK(cudaEventCreateWithFlags(&x, cudaEventDisableTiming));
+    }
+    cudaStream_t rs = nbuf == 2 ? s2 : s;  // the stream of the records
+    AK(cudaMemsetAsync(w[0].flags, 0, 2 * sizeof(int), s));
     AK(cudaMemsetAsync(dth, 0, lbfd::NTAN * sizeof(double), s));
     // the adjoint of J with respect to the final state (FP64), times seed
     AK(cudaMemsetAsync(lam1, 0, lbytes, s));
@@ -1159,6 +1185,7 @@ int lbfd_adjoint_backward(lbfd_handle* h, double seed, double* grad)
     // backward pass: each segment recomputed from its checkpoint with the
     // forward kernels (FP32 in the mixed form), every step's adjoint in FP64
     const lbfd::BoundaryLists b = lists(h);
+    const int G = w[0].slots;
     for (int g = nseg - 1; g >= 0; --g) {
         const int len = steps - g * K < K ? steps - g * K : K;
         for (int j = 0; j < len; ++j)  // every slot starts as the checkpoint (solid cells never change)
@@ -1168,38 +1195,89 @@ int lbfd_adjoint_backward(lbfd_handle* h, double seed, double* grad)
             AK(lbfd::launch_step(h->dim, h->precision, h->variant, h->Pd, h->Pf,
                                  view_of(h, seg + (size_t)(j - 1) * sbytes), view_of(h, seg + (size_t)j * sbytes),
                                  h->solid, b, h->side, s));
-        for (int j1 = len - 1; j1 >= 0; j1 -= w.slots) {
-            const int j0 = j1 - w.slots + 1 > 0 ? j1 - w.slots + 1 : 0;
-            if (w.chunk >= h->ncell) {  // the steps j0..j1 recorded at once, then swept one by one
-                AK(lbfd::launch_adjoint_record(h->dim, h->Pd, planes, seg + (size_t)j0 * sbytes, sbytes, j1 - j0 + 1,
-                                               fp32, h->solid, 0, h->ncell, w, s));
-                for (int j = j1; j >= j0; --j) {
-                    AK(cudaMemsetAsync(lam0, 0, lbytes, s));
-                    AK(lbfd::launch_adjoint_sweep(h->Pd, planes, j - j0, h->solid, 0, h->ncell, lam1, lam0, dth, w,
-                                                  s));
-                    std::swap(lam0, lam1);
-                }
-            } else {  // one step (j0 == j1), recorded and swept in chunks of cells
+        if (!pipelined) {  // one step at a time (j0 == j1), recorded and swept in chunks of cells
+            for (int j = len - 1; j >= 0; --j) {
                 AK(cudaMemsetAsync(lam0, 0, lbytes, s));
-                for (long long c0 = 0; c0 < h->ncell; c0 += w.chunk) {
-                    const long long n = h->ncell - c0 < w.chunk ? h->ncell - c0 : w.chunk;
-                    AK(lbfd::launch_adjoint_record(h->dim, h->Pd, planes, seg + (size_t)j1 * sbytes, sbytes, 1, fp32,
-                                                   h->solid, c0, n, w, s));
-                    AK(lbfd::launch_adjoint_sweep(h->Pd, planes, 0, h->solid, c0, n, lam1, lam0, dth, w, s));
+                for (long long c0 = 0; c0 < h->ncell; c0 += w[0].chunk) {
+                    const long long n = h->ncell - c0 < w[0].chunk ? h->ncell - c0 : w[0].chunk;
+                    AK(lbfd::launch_adjoint_record(h->dim, h->Pd, planes, seg + (size_t)j * sbytes, sbytes, 1, fp32,
+                                                   h->solid, c0, n, w[0], s));
+                    AK(lbfd::launch_adjoint_sweep(h->Pd, planes, 0, h->solid, c0, n, lam1, lam0, dth, w[0], s));
                 }
                 std::swap(lam0, lam1);
             }
+            continue;
+        }
+        // groups of G steps from the end of the segment: group i holds the
+        // steps j1(i) - G + 1 .. j1(i) (clipped at 0) and uses buffer i % 2
+        const int ngroups = (len + G - 1) / G;
+        auto first = [&](int i) { return len - 1 - i * G - (G - 1) > 0 ? len - 1 - i * G - (G - 1) : 0; };
+        auto record = [&](int i) -> cudaError_t {
+            const int j1 = len - 1 - i * G, j0 = first(i);
+            return lbfd::launch_adjoint_record(h->dim, h->Pd, planes, seg + (size_t)j0 * sbytes, sbytes, j1 - j0 + 1,
+                                               fp32, h->solid, 0, h->ncell, w[i % nbuf], rs);
+        };
+        if (nbuf == 2) {  // the segment's states are ready for the records
+            AK(cudaEventRecord(ev[4], s));
+            AK(cudaStreamWaitEvent(s2, ev[4], 0));
+        }
+        AK(record(0));
+        if (nbuf == 2) AK(cudaEventRecord(ev[0], s2));
+        for (int i = 0; i < ngroups; ++i) {
+            const int bi = i % nbuf;
+            if (nbuf == 2) {
+                AK(cudaStreamWaitEvent(s, ev[bi], 0));  // group i recorded
+                if (i + 1 < ngroups) {
+                    // group i + 1 into the other buffer once its last sweeps (group i - 1) are done
+                    if (i >= 1) AK(cudaStreamWaitEvent(s2, ev[2 + (i + 1) % 2], 0));
+                    AK(record(i + 1));
+                    AK(cudaEventRecord(ev[(i + 1) % 2], s2));
+                }
+            } else if (i >= 1) {
+                AK(record(i));
+            }
+            const int j1 = len - 1 - i * G, j0 = first(i);
+            for (int j = j1; j >= j0; --j) {
+                AK(cudaMemsetAsync(lam0, 0, lbytes, s));
+                AK(lbfd::launch_adjoint_sweep(h->Pd, planes, j - j0, h->solid, 0, h->ncell, lam1, lam0, dth, w[bi], s));
+                std::swap(lam0, lam1);
+            }
+            if (nbuf == 2) AK(cudaEventRecord(ev[2 + bi], s));
         }
     }
     int flags[2];
     double gr[lbfd::NTAN];
-    AK(cudaMemcpyAsync(flags, w.flags, sizeof flags, cudaMemcpyDeviceToHost, s));
+    AK(cudaMemcpyAsync(flags, w[0].flags, sizeof flags, cudaMemcpyDeviceToHost, s));
     AK(cudaMemcpyAsync(gr, dth, sizeof gr, cudaMemcpyDeviceToHost, s));
     AK(cudaStreamSynchronize(s));
 #undef AK
     release();
-    if (flags[0]) return LBFD_ENOTSUP;  // a cell's step needs more tape than provided
+    *overflow = flags[0] != 0;
     for (int k = 0; k < lbfd::NTAN; ++k) grad[k] = gr[k];
+    return LBFD_OK;
+}
+
+int lbfd_adjoint_backward(lbfd_handle* h, double seed, double* grad)
+{
+    NvtxRange nvtx_("lbfd_adjoint_backward");
+    if (!h || !grad) return LBFD_EINVAL;
+    if (!h->adj_ck || h->adj_steps < 1) return LBFD_EINVAL;  // nothing recorded
+    // tapes of 2048 nodes per cell and step hold every step of the 2-D
+    // general form with room to spare; a step that needs more is taken again
+    // with the 16-bit node limit's share of 4096
+    double g[lbfd::NTAN];
+    bool overflow = false;
+    for (int maxn : {2048, 4096}) {
+        const int st = adjoint_backward_pass(h, seed, maxn, g, &overflow);
+        if (st != LBFD_OK) {
+            adjoint_release(h);
+            return st;
+        }
+        if (!overflow) break;
+    }
+    adjoint_release(h);
+    if (overflow) return LBFD_ENOTSUP;  // a cell's step needs more tape than provided
+    for (int k = 0; k < lbfd::NTAN; ++k) grad[k] = g[k];
     return LBFD_OK;
 }
 
