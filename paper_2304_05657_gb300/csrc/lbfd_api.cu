@@ -46,6 +46,11 @@ struct lbfd_handle {
     long long* bndw;      // 3-D: the others (next to in-domain solids only)
     long long nbndw;
     unsigned long long* bndw_code;  // 3-D: their neighbourhood codes
+    long long* bndfc;     // 3-D: the cells near faces that take the coded form (staircase walls)
+    long long nbndfc;
+    unsigned long long* bndfc_code;
+    long long* bndfg;     // 3-D: the other cells near faces (general form)
+    long long nbndfg;
     uint8_t* interior;    // per cell, 1 = updated by the interior tile kernels
     void* aux;            // 3-D: Lambda and grad rho planes of the split variants
     int* wtiles;          // tiles holding the other boundary cells (2-D)
@@ -256,6 +261,9 @@ void free_handle(lbfd_handle* h)
     if (h->bndf) cudaFree(h->bndf);
     if (h->bndw) cudaFree(h->bndw);
     if (h->bndw_code) cudaFree(h->bndw_code);
+    if (h->bndfc) cudaFree(h->bndfc);
+    if (h->bndfc_code) cudaFree(h->bndfc_code);
+    if (h->bndfg) cudaFree(h->bndfg);
     if (h->interior) cudaFree(h->interior);
     if (h->aux) cudaFree(h->aux);
     if (h->wtiles) cudaFree(h->wtiles);
@@ -315,12 +323,22 @@ lbfd::BoundaryLists lists(const lbfd_handle* h)
     b.wall = nullptr;
     b.nwall = 0;
     b.wall_code = nullptr;
+    b.face_coded = nullptr;
+    b.nface_coded = 0;
+    b.face_code = nullptr;
     if (h->dim == 3) {  // the general form takes curved walls in both lists
         b.face = h->bndf;
         b.nface = h->nbndf;
         b.wall = h->bndw;
         b.nwall = h->nbndw;
         b.wall_code = h->bndw_code;
+        if (!curved) {  // staircase walls: most cells near faces take their codes
+            b.face = h->bndfg;
+            b.nface = h->nbndfg;
+            b.face_coded = h->bndfc;
+            b.nface_coded = h->nbndfc;
+            b.face_code = h->bndfc_code;
+        }
     }
     b.interior = h->interior;
     b.aux = h->aux;
@@ -500,6 +518,27 @@ int lbfd_create(const lbfd_grid* grid, const uint8_t* solid_mask, const lbfd_mec
             (e = cudaMalloc(&h->aux, (size_t)4 * h->stride * h->esz)) != cudaSuccess) {
             free_handle(h);
             return cuda_fail(e, "split-step buffers");
+        }
+        {  // the cells near faces: coded where the coded form applies
+            std::vector<long long> fc, fg;
+            std::vector<unsigned long long> fcodes;
+            lbfd::face_codes(h->grid.nx, h->grid.ny, h->grid.nz, h->Pd.bc, m.data(), lists_host[1], fc, fcodes, fg);
+            h->nbndfc = (long long)fc.size();
+            h->nbndfg = (long long)fg.size();
+            if ((!fc.empty() &&
+                 ((e = cudaMalloc(&h->bndfc, fc.size() * sizeof(long long))) != cudaSuccess ||
+                  (e = cudaMemcpy(h->bndfc, fc.data(), fc.size() * sizeof(long long), cudaMemcpyHostToDevice)) !=
+                      cudaSuccess ||
+                  (e = cudaMalloc(&h->bndfc_code, fcodes.size() * sizeof(unsigned long long))) != cudaSuccess ||
+                  (e = cudaMemcpy(h->bndfc_code, fcodes.data(), fcodes.size() * sizeof(unsigned long long),
+                                  cudaMemcpyHostToDevice)) != cudaSuccess)) ||
+                (!fg.empty() &&
+                 ((e = cudaMalloc(&h->bndfg, fg.size() * sizeof(long long))) != cudaSuccess ||
+                  (e = cudaMemcpy(h->bndfg, fg.data(), fg.size() * sizeof(long long), cudaMemcpyHostToDevice)) !=
+                      cudaSuccess))) {
+                free_handle(h);
+                return cuda_fail(e, "face lists");
+            }
         }
         if (!wl.empty()) {
             std::vector<unsigned long long> codes;
@@ -693,7 +732,8 @@ int lbfd_launches_per_step(const lbfd_handle* h)
     if (h->variant > 0 && !is_tangent(h->precision)) {
         if (h->dim == 3) {
             const bool wall_list = b.nwall > 0 && (h->variant < 6 || h->Pd.curved);
-            n += (b.nface > 0 ? 1 : 0) + (wall_list ? 1 : 0) + (h->variant == 4 || h->variant == 5 ? 1 : 0);
+            n += (b.nface > 0 ? 1 : 0) + (b.nface_coded > 0 ? 1 : 0) + (wall_list ? 1 : 0) +
+                 (h->variant == 4 || h->variant == 5 ? 1 : 0);
         } else {
             const bool wv = h->variant >= 5 && b.nwall_tiles > 0;
             n += ((wv ? b.nface : b.nall) > 0 ? 1 : 0) + (wv ? 1 : 0);

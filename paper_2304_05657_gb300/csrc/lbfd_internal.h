@@ -67,6 +67,9 @@ struct BoundaryLists {
     const long long* wall;  // 3-D: all \ face, cells whose stencils reach no non-periodic face
     long long nwall;
     const unsigned long long* wall_code;  // 3-D: their neighbourhood codes (cell_step_coded)
+    const long long* face_coded;  // 3-D: cells near inlet/outlet faces taken by cell_step_coded<FACES>
+    long long nface_coded;        // (then `face` holds the other cells near faces)
+    const unsigned long long* face_code;
     const uint8_t* interior;  // per cell, 1 for the cells the interior tile kernels update
     void* aux;                // 3-D: 4 planes of the compute type for the split variants
 };
@@ -91,6 +94,12 @@ cudaError_t launch_step3d_tiled(int precision, int variant, const StepParams<dou
 // layout in cell_step_coded).
 void wall_codes(int nx, int ny, int nz, const int* bc, const uint8_t* solid, const std::vector<long long>& cells,
                 std::vector<unsigned long long>& out);
+// The cells near domain faces that cell_step_coded<FACES> takes (faces of
+// one axis, all of them inlet or outlet faces, no corner of the general
+// form's rules in reach; staircase walls) with their codes, and the others
+// (general form).  Both in the order of `cells`.
+void face_codes(int nx, int ny, int nz, const int* bc, const uint8_t* solid, const std::vector<long long>& cells,
+                std::vector<long long>& coded, std::vector<unsigned long long>& codes, std::vector<long long>& rest);
 
 // Fluid cells that are not interior for the tile kernels (host, at create);
 // faces_only (2-D): only cells whose stencil leaves the domain.

@@ -215,6 +215,93 @@ void wall_codes(int nx, int ny, int nz, const int* bc, const uint8_t* solid, con
     }
 }
 
+void face_codes(int nx, int ny, int nz, const int* bc, const uint8_t* solid, const std::vector<long long>& cells,
+                std::vector<long long>& coded, std::vector<unsigned long long>& codes, std::vector<long long>& rest)
+{
+    const int n[3] = {nx, ny, nz};
+    coded.clear();
+    codes.clear();
+    rest.clear();
+    // point q: 0 fluid, 1 solid, 2 beyond a non-periodic face (periodic axes wrapped)
+    auto kind = [&](int q[3], int* face) {
+        *face = -1;
+        for (int a = 0; a < 3; ++a) {
+            if (q[a] >= 0 && q[a] < n[a]) continue;
+            const int f = 2 * a + (q[a] < 0 ? 0 : 1);
+            if (bc[f] != BC_PERIODIC) {
+                *face = f;
+                return 2;
+            }
+            q[a] = ((q[a] % n[a]) + n[a]) % n[a];
+        }
+        return solid[(long long)q[0] + (long long)nx * ((long long)q[1] + (long long)ny * q[2])] ? 1 : 0;
+    };
+    auto open_face = [&](int f) { return bc[f] == BC_INLET || bc[f] == BC_OUTLET || bc[f] == BC_OUTLET_PRESSURE; };
+    for (const long long c : cells) {
+        const int p[3] = {(int)(c % nx), (int)((c / nx) % ny), (int)(c / ((long long)nx * ny))};
+        bool ok = true;
+        int axis = -1;  // the one axis whose faces are in reach
+        for (int a = 0; a < 3 && ok; ++a)
+            for (int side = -1; side <= 1; side += 2) {
+                const int f = 2 * a + (side < 0 ? 0 : 1);
+                const bool reach = side < 0 ? p[a] - 2 < 0 : p[a] + 2 >= n[a];
+                if (!reach || bc[f] == BC_PERIODIC) continue;
+                if (!open_face(f) || (axis >= 0 && axis != a)) ok = false;
+                axis = a;
+            }
+        unsigned long long code = 0;
+        for (int i = 0; i < 27 && ok; ++i) {
+            const int ci[3] = {cx_of(i), cy_of(i), cz_of(i)};
+            int q[3] = {p[0] - ci[0], p[1] - ci[1], p[2] - ci[2]}, f = -1;
+            const int k = kind(q, &f);
+            if (k == 1) code |= 1ull << i;  // bounce-back from a solid source
+            if (k != 2) continue;
+            // beyond a face: the general form bounces back where the boundary
+            // column is solid, and takes the convective outlet's inner value
+            // from the cell itself where the inner cell is solid
+            int qc[3] = {p[0] - ci[0], p[1] - ci[1], p[2] - ci[2]};
+            for (int a = 0; a < 3; ++a) qc[a] = qc[a] < 0 ? 0 : (qc[a] >= n[a] ? n[a] - 1 : qc[a]);
+            if (solid[(long long)qc[0] + (long long)nx * ((long long)qc[1] + (long long)ny * qc[2])]) ok = false;
+            if (bc[f] == BC_OUTLET) {
+                const int a = f / 2, ns = (f % 2 == 1) ? 1 : -1;
+                int qi[3] = {p[0], p[1], p[2]};
+                qi[a] -= ns;
+                int fi = -1;
+                if (qi[a] < 0 || qi[a] >= n[a] || kind(qi, &fi) != 0) ok = false;
+            }
+        }
+        for (int a = 0; a < 3 && ok; ++a) {
+            unsigned bits6 = 0, faces2 = 0;
+            for (int side = -1; side <= 1; side += 2) {
+                unsigned w = 0, face = 0;
+                for (int j = 1; j <= 2 && !w; ++j) {
+                    int q[3] = {p[0], p[1], p[2]}, f = -1;
+                    q[a] += side * j;
+                    const int k = kind(q, &f);
+                    if (k != 0) {
+                        w = (unsigned)j;
+                        face = k == 2 ? 1u : 0u;
+                    }
+                }
+                int qo[3] = {p[0], p[1], p[2]}, fo = -1;
+                qo[a] -= side;
+                const unsigned opp = w != 0 && kind(qo, &fo) != 0 ? 1u : 0u;
+                const unsigned b3 = w | (opp << 2);
+                bits6 |= side < 0 ? b3 : b3 << 3;
+                faces2 |= face << (side < 0 ? 0 : 1);
+            }
+            code |= (unsigned long long)bits6 << (32 + 6 * a);
+            code |= (unsigned long long)faces2 << (50 + 2 * a);
+        }
+        if (ok) {
+            coded.push_back(c);
+            codes.push_back(code);
+        } else {
+            rest.push_back(c);
+        }
+    }
+}
+
 void boundary_cells(int dim, int nx, int ny, int nz, const int* bc, const uint8_t* solid, std::vector<long long>& out,
                     bool faces_only, const int* face_solid)
 {

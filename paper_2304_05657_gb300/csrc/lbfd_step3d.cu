@@ -5,10 +5,11 @@
 namespace lbfd {
 
 // The interior cells go to the tile kernel; on the side stream (same input
-// state, disjoint writes) the general form takes the cells near domain
-// faces (b.face), and the cells next to in-domain solids (b.wall) go
-// through their coded neighbourhoods (or, with curved walls, the general
-// form with the face rules compiled out).
+// state, disjoint writes) the cells near inlet and outlet faces go through
+// their coded neighbourhoods (b.face_coded) and the general form takes the
+// other cells near domain faces (b.face), and the cells next to in-domain
+// solids (b.wall) go through their coded neighbourhoods (or, with curved
+// walls, the general form with the face rules compiled out).
 // the tile kernel instance: MINB > 0 caps its registers for MINB blocks per SM
 template <typename S, typename R, int TX, int TY, int ZC, int MINB>
 static auto tile3_kernel()
@@ -36,7 +37,7 @@ static cudaError_t launch_t3(const StepParams<R>& P, StateView in, StateView out
     if (bin.interior == nullptr || (SPLIT && bin.aux == nullptr)) return cudaErrorInvalidValue;
     BoundaryLists b = bin;
     if (WALLS && !P.curved) b.nwall = 0;
-    const bool fork = (b.nface > 0 || b.nwall > 0) && side.stream != nullptr;
+    const bool fork = (b.nface > 0 || b.nface_coded > 0 || b.nwall > 0) && side.stream != nullptr;
     if (fork) {
         if ((e = cudaEventRecord(side.fork, stream)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(side.stream, side.fork, 0)) != cudaSuccess) return e;
@@ -47,6 +48,13 @@ static cudaError_t launch_t3(const StepParams<R>& P, StateView in, StateView out
         const unsigned nb = (unsigned)((b.nface + 127) / 128);
         e = launch_prio(step_kernel_boundary<3, S, R, true>, dim3(nb), dim3(128), 0, bs, prio, P, (const S*)in.g,
                         (S*)out.g, (const S*)in.T, (S*)out.T, (const S*)in.Y, (S*)out.Y, solid, b.face, b.nface);
+        if (e != cudaSuccess) return e;
+    }
+    if (b.nface_coded > 0) {  // cells near inlet/outlet faces with their codes
+        const unsigned nb = (unsigned)((b.nface_coded + 127) / 128);
+        e = launch_prio(step_kernel_wallcode<3, S, R, true>, dim3(nb), dim3(128), 0, bs, prio, P, (const S*)in.g,
+                        (S*)out.g, (const S*)in.T, (S*)out.T, (const S*)in.Y, (S*)out.Y, b.face_coded, b.face_code,
+                        b.nface_coded);
         if (e != cudaSuccess) return e;
     }
     if (b.nwall > 0) {

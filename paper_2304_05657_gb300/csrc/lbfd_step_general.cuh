@@ -445,21 +445,31 @@ __device__ __forceinline__ void cell_step_general(const StepParams<R>& P, const 
 
 // ---------------------------------------------------------------------------
 // The same update for a cell next to in-domain solids whose stencils reach
-// no non-periodic face (staircase walls), with its neighbourhood given by a
-// code computed at create instead of mask reads:
+// no non-periodic face (staircase walls), or (FACES) for a cell near inlet
+// and outlet faces of one axis, with its neighbourhood given by a code
+// computed at create instead of mask reads:
 //   bits 0..26   population i is pulled from a solid cell (bounce-back)
 //   bits 32..49  per axis a (6 bits at 32 + 6a), per side (low 3 bits: -,
-//                high 3 bits: +): the distance 1 or 2 of the first solid cell
-//                along the line (0: none within 2) and, in the third bit,
-//                whether the neighbour on the other side is solid
-// so that all loads of the cell can be issued at once.
+//                high 3 bits: +): the distance 1 or 2 of the first point
+//                along the line that is not a fluid cell (0: none within 2)
+//                and, in the third bit, whether the neighbour on the other
+//                side is not a fluid cell either
+//   bits 50..55  (FACES) per axis (2 bits at 50 + 2a, -: low, +: high): that
+//                first point lies beyond the domain face (inlet: Dirichlet
+//                T_in, Y_in ghosts; outlets: zero gradient), not in a solid
+// so that all loads of the cell can be issued at once.  A population whose
+// source lies beyond an inlet or outlet face takes the rules of Eq. 31, 32
+// or the constant-pressure outlet; the code builder leaves out the cells
+// where the general form would bounce such a population back or take the
+// convective outlet's inner value from the cell itself.
 // ---------------------------------------------------------------------------
 template <int DIM, typename R>
 __device__ __forceinline__ void coded_line(const StepParams<R>& P, const int p[3], long long c, int a, unsigned code,
-                                           LineDesc<R>& L)
+                                           unsigned faces, LineDesc<R>& L)
 {
-    // the line's cells (periodic wrap: only periodic faces are in reach),
-    // without indexing an array by the run-time axis
+    // the line's cells (periodic wrap: points beyond a non-periodic face
+    // are ghosts, replaced below), without indexing an array by the
+    // run-time axis
     const int pa = a == 0 ? p[0] : (a == 1 ? p[1] : p[2]);
     const int n = a == 0 ? P.nx : (a == 1 ? P.ny : P.nz);
     const long long stride = a == 0 ? 1LL : (a == 1 ? (long long)P.nx : (long long)P.nx * P.ny);
@@ -475,25 +485,29 @@ __device__ __forceinline__ void coded_line(const StepParams<R>& P, const int p[3
         L.TB[j] = R(0);
     }
     L.near = code != 0;
-    const int mode = P.solid_isothermal ? G_DIRICHLET_T : G_NEUMANN;
+    const int solid_mode = P.solid_isothermal ? G_DIRICHLET_T : G_NEUMANN;
 #pragma unroll
     for (int side = -1; side <= 1; side += 2) {
         const unsigned bits = side < 0 ? (code & 7u) : (code >> 3);
         const int w = (int)(bits & 3u);
         if (!w) continue;
         const bool opp_solid = (bits >> 2) & 1u;
+        const bool face = (faces >> (side < 0 ? 0 : 1)) & 1u;
+        const int ftype = P.bc[2 * a + (side < 0 ? 0 : 1)];
+        const int mode = !face ? solid_mode : (ftype == BC_INLET ? G_INLET : G_NEUMANN);
+        const R TB = !face ? P.T_solid : (ftype == BC_INLET ? P.T_in : R(0));
 #pragma unroll
         for (int j = 1; j <= 2; ++j) {
             if (j < w) continue;
             const int m = 2 * w - 1 - j;  // mirror offset on this side (Eq. 34)
             L.src[2 + side * j] = m >= 0 ? L.src[2 + side * m] : (opp_solid ? c : raw[2 - side]);
             L.mode[2 + side * j] = mode;
-            L.TB[2 + side * j] = P.T_solid;
+            L.TB[2 + side * j] = TB;
         }
     }
 }
 
-template <int DIM, typename S, typename R>
+template <int DIM, typename S, typename R, bool FACES = false>
 __device__ __forceinline__ void cell_step_coded(const StepParams<R>& P, const int p[3], long long c,
                                                 unsigned long long code, const S* LBFD_RESTRICT g_in,
                                                 S* LBFD_RESTRICT g_out, const S* LBFD_RESTRICT T_in,
@@ -520,12 +534,82 @@ __device__ __forceinline__ void cell_step_coded(const StepParams<R>& P, const in
             ozm = p[2] == 0 ? (P.nz - 1) * plane : -plane;
             ozp = p[2] == P.nz - 1 ? (1 - P.nz) * plane : plane;
         }
+        // FACES: the cell's own velocity for the outlet rules, when one of
+        // its populations comes from beyond an outlet face
+        R uc[3] = {R(0), R(0), R(0)}, mc[3] = {R(0), R(0), R(0)};
+        if constexpr (FACES) {
+            bool own = false;
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) {
+                const int n = a == 0 ? P.nx : (a == 1 ? P.ny : P.nz);
+                const int pa = a == 0 ? p[0] : (a == 1 ? p[1] : p[2]);
+                const int lo = P.bc[2 * a], hi = P.bc[2 * a + 1];
+                own |= pa == 0 && (lo == BC_OUTLET || lo == BC_OUTLET_PRESSURE);
+                own |= pa == n - 1 && (hi == BC_OUTLET || hi == BC_OUTLET_PRESSURE);
+            }
+            if (own) {
+                R gc[Q];
+#pragma unroll
+                for (int j = 0; j < Q; ++j) gc[j] = R(g_in[(long long)j * N + c]);
+                const R inv = fdiv(R(3), rho0);
+#pragma unroll
+                for (int a = 0; a < DIM; ++a) {
+                    R m = R(0);
+#pragma unroll
+                    for (int j = 0; j < Q; ++j) {
+                        const int cj = ccomp<DIM>(j, a);
+                        if (cj != 0) m += R(cj) * gc[j];
+                    }
+                    mc[a] = m;
+                    uc[a] = m * inv;
+                }
+            }
+        }
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const int cx = ccomp<DIM>(i, 0), cy = ccomp<DIM>(i, 1), cz = ccomp<DIM>(i, 2);
             const long long s = c + (cx > 0 ? oxm : (cx < 0 ? oxp : 0)) + (cy > 0 ? oym : (cy < 0 ? oyp : 0)) +
                                 (cz > 0 ? ozm : (cz < 0 ? ozp : 0));
             const bool bb = (code >> i) & 1ull;
+            if constexpr (FACES) {
+                // the face the source x - c_i lies beyond (at most one)
+                int f = -1;
+#pragma unroll
+                for (int a = 0; a < DIM; ++a) {
+                    const int ca = ccomp<DIM>(i, a);
+                    const int n = a == 0 ? P.nx : (a == 1 ? P.ny : P.nz);
+                    const int sa = (a == 0 ? p[0] : (a == 1 ? p[1] : p[2])) - ca;
+                    if (ca > 0 && sa < 0 && P.bc[2 * a] != BC_PERIODIC) f = 2 * a;
+                    if (ca < 0 && sa >= n && P.bc[2 * a + 1] != BC_PERIODIC) f = 2 * a + 1;
+                }
+                if (f >= 0) {
+                    const int ib = opposite<DIM>(i);
+                    const R gib = R(g_in[(long long)ib * N + c]);
+                    const int a = f / 2, t = P.bc[f];
+                    const R ci = R(f / 2 == 0 ? cx : (f / 2 == 1 ? cy : cz));
+                    if (t == BC_INLET) {  // Eq. 31 applied to g, u_in along the inward normal
+                        const R un = (f % 2 == 0) ? P.u_in : -P.u_in;
+                        g[i] = gib + R(2) * weight<DIM, R>(i) * P.rho_in * ci * un;
+                    } else if (t == BC_OUTLET_PRESSURE) {  // constant P_h = 0: anti-bounce-back
+                        R cu = R(0), uu = R(0);
+#pragma unroll
+                        for (int b = 0; b < DIM; ++b) {
+                            cu += R(ccomp<DIM>(i, b)) * uc[b];
+                            uu += uc[b] * uc[b];
+                        }
+                        const R geq_even = weight<DIM, R>(i) * rho0 * (R(1.5) * cu * cu - R(0.5) * uu);
+                        g[i] = R(2) * geq_even - gib;
+                    } else {  // Eq. 32 in lattice units, outward normal along a
+                        const int ns = (f % 2 == 1) ? 1 : -1;
+                        const R mom = R(ns) * (a == 0 ? mc[0] : (a == 1 ? mc[1] : mc[2]));
+                        const R un = fdiv(R(3) * mom, rho0);
+                        const long long st = a == 0 ? 1LL : (a == 1 ? (long long)P.nx : plane);
+                        const R inner = R(g_in[(long long)i * N + c - ns * st]);
+                        g[i] = (P.cs - un) * inner + (R(1) - P.cs + un) * R(g_in[(long long)i * N + c]);
+                    }
+                    continue;
+                }
+            }
             g[i] = R(g_in[bb ? (long long)opposite<DIM>(i) * N + c : (long long)i * N + s]);
         }
     }
@@ -551,7 +635,8 @@ __device__ __forceinline__ void cell_step_coded(const StepParams<R>& P, const in
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
         LineDesc<R> L;
-        coded_line<DIM, R>(P, p, c, a, (unsigned)(code >> (32 + 6 * a)) & 63u, L);
+        coded_line<DIM, R>(P, p, c, a, (unsigned)(code >> (32 + 6 * a)) & 63u,
+                           FACES ? (unsigned)(code >> (50 + 2 * a)) & 3u : 0u, L);
         R Tl[5], Yl[NSP][5], invWl[5], rhol[5];
 #pragma unroll
         for (int j = 0; j < 5; ++j) {  // every point's loads at once
