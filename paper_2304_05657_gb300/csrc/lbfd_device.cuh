@@ -268,6 +268,42 @@ __device__ __forceinline__ void central_forward(R* f, const R* u)
     }
 }
 
+// The central moments of orders 0-2 only (the others are left partly
+// transformed): the collision with omega_hi = 1 needs no more, since it
+// sets every cumulant of order >= 3 to its equilibrium.  The same
+// expressions as central_forward for the moments it forms.
+template <typename R>
+__device__ __forceinline__ void cm3_forward01(R& f0, R& f1, R f2, R u)
+{
+    R r0 = f0 + f1 + f2;
+    R r1 = f2 - f0;
+    f0 = r0;
+    f1 = r1 - u * r0;
+}
+template <int DIM, typename R>
+__device__ __forceinline__ void central_forward_lo(R* f, const R* u)
+{
+    constexpr int NZ = DIM == 3 ? 3 : 1;
+#pragma unroll
+    for (int c = 0; c < NZ; ++c)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) cm3_forward(f[3 * b + 9 * c], f[1 + 3 * b + 9 * c], f[2 + 3 * b + 9 * c], u[0]);
+#pragma unroll
+    for (int c = 0; c < NZ; ++c) {  // y lines of x order p: y orders up to 2 - p
+        cm3_forward(f[9 * c], f[3 + 9 * c], f[6 + 9 * c], u[1]);
+        cm3_forward01(f[1 + 9 * c], f[4 + 9 * c], f[7 + 9 * c], u[1]);
+        f[2 + 9 * c] = f[2 + 9 * c] + f[5 + 9 * c] + f[8 + 9 * c];
+    }
+    if (DIM == 3) {  // z lines of x-y order s: z orders up to 2 - s
+        cm3_forward(f[0], f[9], f[18], u[2]);
+        cm3_forward01(f[1], f[10], f[19], u[2]);
+        cm3_forward01(f[3], f[12], f[21], u[2]);
+        f[2] = f[2] + f[11] + f[20];
+        f[4] = f[4] + f[13] + f[22];
+        f[6] = f[6] + f[15] + f[24];
+    }
+}
+
 template <int DIM, typename R>
 __device__ __forceinline__ void central_inverse(R* m, const R* u)
 {
@@ -422,7 +458,10 @@ __device__ __forceinline__ void eq_cumulants(R* fe, R e, const R* u)
 // orders 0-1 carried, second order split into trace (omega_b) and
 // deviatoric/off-diagonal (omega_s), orders >= 3 at omega_hi.
 // ---------------------------------------------------------------------------
-template <int DIM, typename R, typename PR>
+// HI1: omega_hi == 1 (the caller checks), so the pre-collision cumulants of
+// order >= 3 are not formed: the relaxation sets them to equilibrium, as
+// fe + (1 - omega_hi) (g - fe) does for omega_hi = 1.
+template <int DIM, typename R, typename PR, bool HI1 = false>
 __device__ __forceinline__ void collide(const StepParams<PR>& P, R* g, R rho, const R* u, const R* grad_rho,
                                         R Lam)
 {
@@ -452,8 +491,12 @@ __device__ __forceinline__ void collide(const StepParams<PR>& P, R* g, R rho, co
         xi[i] = cs2 * (feq_r - wi) * cg + wi * rcs2 * Lam;  // Eq. 9
         g[i] = (g[i] + R(0.5) * xi[i]) * inv_rcs2;  // Eq. 19
     }
-    central_forward<DIM>(g, u);
-    to_cumulants<DIM>(g);
+    if constexpr (HI1) {
+        central_forward_lo<DIM>(g, u);  // orders 0-2: cumulants = central moments
+    } else {
+        central_forward<DIM>(g, u);
+        to_cumulants<DIM>(g);
+    }
     // the target: cumulants of g^eq / (rho cs2) = w (P_h/(rho cs2) - 1) + f^eq/rho (Eq. 12)
     eq_cumulants<DIM>(fe, P_h * inv_rcs2 - R(1), u);
     // relaxation
@@ -461,7 +504,7 @@ __device__ __forceinline__ void collide(const StepParams<PR>& P, R* g, R rho, co
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
         const int o = moment_order(j);
-        if (o >= 3) g[j] = fe[j] + (R(1) - wh) * (g[j] - fe[j]);
+        if (o >= 3) g[j] = HI1 ? fe[j] : fe[j] + (R(1) - wh) * (g[j] - fe[j]);
     }
     if (DIM == 2) {
         const int ixx = LBFD_M(2, 0, 0), iyy = LBFD_M(0, 2, 0), ixy = LBFD_M(1, 1, 0);

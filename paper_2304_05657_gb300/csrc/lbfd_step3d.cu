@@ -11,11 +11,11 @@ namespace lbfd {
 // solids (b.wall) go through their coded neighbourhoods (or, with curved
 // walls, the general form with the face rules compiled out).
 // the tile kernel instance: MINB > 0 caps its registers for MINB blocks per SM
-template <typename S, typename R, int TX, int TY, int ZC, int MINB>
+template <typename S, typename R, int TX, int TY, int ZC, int MINB, bool HI1 = false>
 static auto tile3_kernel()
 {
     if constexpr (MINB > 0) return step_kernel_tiled3d_capped<S, R, TX, TY, ZC, MINB>;
-    else return step_kernel_tiled3d<S, R, TX, TY, ZC>;
+    else return step_kernel_tiled3d<S, R, TX, TY, ZC, HI1>;
 }
 
 // SPLIT: the tile kernel does a1-a7 and a per-cell kernel a8-a10 (two
@@ -27,9 +27,15 @@ static cudaError_t launch_t3(const StepParams<R>& P, StateView in, StateView out
                              const BoundaryLists& bin, const SideStream& side, cudaStream_t stream)
 {
     constexpr size_t smem = tile3_smem_bytes<R, TX, TY>();
-    auto kern = tile3_kernel<S, R, TX, TY, ZC, MINB>();
+    // FP32 with omega_hi = 1 (the usual setting): the tile and coded kernels
+    // that skip the pre-collision cumulants of order >= 3
+    constexpr bool F32 = sizeof(R) == 4;
+    const bool hi1 = F32 && P.omega_hi == R(1);
+    auto kern = hi1 ? tile3_kernel<S, R, TX, TY, ZC, MINB, F32>() : tile3_kernel<S, R, TX, TY, ZC, MINB>();
     auto fkern = step_kernel_fd3d<S, R, TX, TY, ZC>;
     auto wkern = step_kernel_tiled3d_walls<S, R, TX, TY, ZC>;
+    auto fcode = hi1 ? step_kernel_wallcode<3, S, R, true, F32> : step_kernel_wallcode<3, S, R, true>;
+    auto wcode = hi1 ? step_kernel_wallcode<3, S, R, false, F32> : step_kernel_wallcode<3, S, R, false>;
     cudaError_t e = SPLIT   ? cudaFuncSetAttribute(fkern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
                     : WALLS ? cudaFuncSetAttribute(wkern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
                             : cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -52,7 +58,7 @@ static cudaError_t launch_t3(const StepParams<R>& P, StateView in, StateView out
     }
     if (b.nface_coded > 0) {  // cells near inlet/outlet faces with their codes
         const unsigned nb = (unsigned)((b.nface_coded + 127) / 128);
-        e = launch_prio(step_kernel_wallcode<3, S, R, true>, dim3(nb), dim3(128), 0, bs, prio, P, (const S*)in.g,
+        e = launch_prio(fcode, dim3(nb), dim3(128), 0, bs, prio, P, (const S*)in.g,
                         (S*)out.g, (const S*)in.T, (S*)out.T, (const S*)in.Y, (S*)out.Y, b.face_coded, b.face_code,
                         b.nface_coded);
         if (e != cudaSuccess) return e;
@@ -60,7 +66,7 @@ static cudaError_t launch_t3(const StepParams<R>& P, StateView in, StateView out
     if (b.nwall > 0) {
         const unsigned nb = (unsigned)((b.nwall + 127) / 128);
         if (!P.curved && b.wall_code != nullptr)  // staircase walls: the coded neighbourhoods
-            e = launch_prio(step_kernel_wallcode<3, S, R>, dim3(nb), dim3(128), 0, bs, prio, P, (const S*)in.g,
+            e = launch_prio(wcode, dim3(nb), dim3(128), 0, bs, prio, P, (const S*)in.g,
                             (S*)out.g, (const S*)in.T, (S*)out.T, (const S*)in.Y, (S*)out.Y, b.wall, b.wall_code,
                             b.nwall);
         else

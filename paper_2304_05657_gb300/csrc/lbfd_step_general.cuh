@@ -507,7 +507,7 @@ __device__ __forceinline__ void coded_line(const StepParams<R>& P, const int p[3
     }
 }
 
-template <int DIM, typename S, typename R, bool FACES = false>
+template <int DIM, typename S, typename R, bool FACES = false, bool HI1 = false>
 __device__ __forceinline__ void cell_step_coded(const StepParams<R>& P, const int p[3], long long c,
                                                 unsigned long long code, const S* LBFD_RESTRICT g_in,
                                                 S* LBFD_RESTRICT g_out, const S* LBFD_RESTRICT T_in,
@@ -659,7 +659,7 @@ __device__ __forceinline__ void cell_step_coded(const StepParams<R>& P, const in
         lam_Y += P.inv_Wk[k] * DY;
     }
     const R Lam = fdiv(DT, T0) + fdiv(lam_Y, invW0);
-    collide<DIM, R>(P, g, rho0, u, acc.grad_rho, Lam);
+    collide<DIM, R, R, HI1>(P, g, rho0, u, acc.grad_rho, Lam);
 #pragma unroll
     for (int i = 0; i < Q; ++i) g_out[(long long)i * N + c] = S(g[i]);
 }

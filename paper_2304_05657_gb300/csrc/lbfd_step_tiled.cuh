@@ -459,7 +459,7 @@ __global__ void __launch_bounds__(TX * TY)
 // The cells of a coded list: next to in-domain solids (staircase walls, no
 // non-periodic face in reach), or (FACES) near inlet and outlet faces:
 // cell_step_coded
-template <int DIM, typename S, typename R, bool FACES = false>
+template <int DIM, typename S, typename R, bool FACES = false, bool HI1 = false>
 __global__ void __launch_bounds__(128) step_kernel_wallcode(StepParams<R> P, const S* LBFD_RESTRICT g_in,
                                                             S* LBFD_RESTRICT g_out, const S* LBFD_RESTRICT T_in,
                                                             S* LBFD_RESTRICT T_out, const S* LBFD_RESTRICT Y_in,
@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(128) step_kernel_wallcode(StepParams<R> P, con
     const long long r = c / P.nx;
     p[1] = (int)(r % P.ny);
     p[2] = (int)(r / P.ny);
-    cell_step_coded<DIM, S, R, FACES>(P, p, c, codes[t], g_in, g_out, T_in, T_out, Y_in, Y_out);
+    cell_step_coded<DIM, S, R, FACES, HI1>(P, p, c, codes[t], g_in, g_out, T_in, T_out, Y_in, Y_out);
 }
 
 // The cells the tiled kernel leaves out: general form over a cell list

@@ -181,7 +181,7 @@ __device__ __forceinline__ void stage_plane(const StepParams<R>& P, const TileSm
 
 // SPLIT: steps a1-a7 only; Lambda and grad rho of every interior cell go
 // to aux (four planes) for step_kernel_collide3d, which does a8-a10
-template <typename S, typename R, int TX, int TY, int ZC, bool SPLIT = false, bool WALLS = false>
+template <typename S, typename R, int TX, int TY, int ZC, bool SPLIT = false, bool WALLS = false, bool HI1 = false>
 __device__ __forceinline__ void tiled3d_body(const StepParams<R>& P, const S* LBFD_RESTRICT g_in,
                                              S* LBFD_RESTRICT g_out, const S* LBFD_RESTRICT T_in,
                                              S* LBFD_RESTRICT T_out, const S* LBFD_RESTRICT Y_in,
@@ -306,7 +306,7 @@ __device__ __forceinline__ void tiled3d_body(const StepParams<R>& P, const S* LB
 #pragma unroll
                 for (int a = 0; a < 3; ++a) aux[(long long)(1 + a) * N + c] = acc.grad_rho[a];
             } else {
-                collide<3, R>(P, g, rho0, u, acc.grad_rho, Lam);
+                collide<3, R, R, HI1>(P, g, rho0, u, acc.grad_rho, Lam);
 #pragma unroll
                 for (int i = 0; i < 27; ++i) g_out[(long long)i * N + c] = S(g[i]);
             }
@@ -315,14 +315,14 @@ __device__ __forceinline__ void tiled3d_body(const StepParams<R>& P, const S* LB
     }
 }
 
-template <typename S, typename R, int TX, int TY, int ZC>
+template <typename S, typename R, int TX, int TY, int ZC, bool HI1 = false>
 __global__ void __launch_bounds__(TX * TY) step_kernel_tiled3d(StepParams<R> P, const S* LBFD_RESTRICT g_in,
                                                                S* LBFD_RESTRICT g_out, const S* LBFD_RESTRICT T_in,
                                                                S* LBFD_RESTRICT T_out, const S* LBFD_RESTRICT Y_in,
                                                                S* LBFD_RESTRICT Y_out,
                                                                const uint8_t* LBFD_RESTRICT interior)
 {
-    tiled3d_body<S, R, TX, TY, ZC>(P, g_in, g_out, T_in, T_out, Y_in, Y_out, interior);
+    tiled3d_body<S, R, TX, TY, ZC, false, false, HI1>(P, g_in, g_out, T_in, T_out, Y_in, Y_out, interior);
 }
 
 // interior cells and, from the same staging, the cells next to in-domain

@@ -383,8 +383,12 @@ def test_d3q27_split_variants_equal_fused(lbfd_lib):
     """The split 3-D variants (FD tile kernel, then a collision kernel fed
     Lambda and grad rho through a scratch buffer) do the fused variants'
     arithmetic in the same order; only the compiler's choice of fused
-    multiply-adds may differ between the two programs, so the states agree
-    to a few ulp: 1e-12 relative L2 in FP64, 1e-6 in FP32."""
+    multiply-adds may differ between the two programs, so the FP64 states
+    agree to a few ulp: 1e-12 relative L2.  In FP32 with omega_hi = 1 the
+    fused kernels form only the central moments of orders 0-2 while the
+    collision kernel of the split ones forms all of them (the results are
+    the same up to rounding): 1e-5, the FP32 population bar of the other
+    tests (measured 5e-6)."""
     cfg, solid, T, Y = inputs.sphere_packing(nx=40, ny=14, nz=13, x_range=(8, 30), r_range=(2.0, 3.5),
                                              porosity=0.85, seed=12, ignite_width=5)
     g, T, Y = inputs.perturbed_state(cfg, solid, T, Y, seed=13)
@@ -397,7 +401,7 @@ def test_d3q27_split_variants_equal_fused(lbfd_lib):
                 s.set_state(T, Y, g)
                 s.step(6)
                 st.append(s.get_state())
-            tol = 1e-12 if prec == "fp64" else 1e-6
+            tol = 1e-12 if prec == "fp64" else 1e-5
             compare_states(st[1], st[0], tol, f"{prec} split {split} vs fused {fused}")
 
 
@@ -466,3 +470,32 @@ def test_d3q27_face_codes_match_oracle(lbfd_lib, oracle_mod, outlet):
         sm.set_state(T, Y, g)
         sm.step(8)
         assert rel_l2(sm.read_field(lbfd_lib.FIELD_T), orc[0]) <= 1e-6
+
+
+@pytest.mark.parametrize("omega_hi", [1.0, 1.3])
+def test_d3q27_mixed_higher_order_rate(lbfd_lib, oracle_mod, omega_hi):
+    """The FP32 3-D tile and coded kernels with omega_hi = 1 form only the
+    central moments of orders 0-2 (the relaxation sets every higher cumulant
+    to its equilibrium); with any other rate they form all of them.  Both
+    against the oracle after 10 steps: T and Y to 1e-6, each population
+    plane to 1e-5 (relative L2, as for the other FP32 variants)."""
+    cfg, solid, T, Y = inputs.sphere_packing(nx=40, ny=14, nz=13, x_range=(8, 30), r_range=(2.0, 3.5),
+                                             porosity=0.85, seed=12, ignite_width=5)
+    cfg["omega_hi"] = omega_hi
+    g, T, Y = inputs.perturbed_state(cfg, solid, T, Y, seed=14)
+    o = oracle_mod.Sim(cfg, solid)
+    o.set_state(T, Y, g)
+    o.step(10)
+    To, Yo, go = o.get_state()
+    s = lbfd_lib.Solver(dict(cfg, precision="mixed"), solid)
+    for v in (1, 2):
+        s.variant = v
+        s.set_state(T, Y, g)
+        s.step(10)
+        Tg, Yg, gg = s.get_state()
+        assert rel_l2(Tg, To) <= 1e-6, v
+        for k in range(Yo.shape[0]):
+            if np.linalg.norm(Yo[k]) > 0:
+                assert rel_l2(Yg[k], Yo[k]) <= 1e-6, (v, k)
+        for i in range(go.shape[0]):
+            assert rel_l2(gg[i], go[i]) <= 1e-5, (v, i)
