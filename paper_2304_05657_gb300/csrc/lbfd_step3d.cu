@@ -14,7 +14,7 @@ namespace lbfd {
 template <typename S, typename R, int TX, int TY, int ZC, int MINB, bool HI1 = false>
 static auto tile3_kernel()
 {
-    if constexpr (MINB > 0) return step_kernel_tiled3d_capped<S, R, TX, TY, ZC, MINB>;
+    if constexpr (MINB > 0) return step_kernel_tiled3d_capped<S, R, TX, TY, ZC, MINB, HI1>;
     else return step_kernel_tiled3d<S, R, TX, TY, ZC, HI1>;
 }
 

@@ -341,13 +341,13 @@ __global__ void __launch_bounds__(TX * TY) step_kernel_tiled3d_walls(StepParams<
 }
 
 // the same with the registers capped so that MINB blocks fit on an SM
-template <typename S, typename R, int TX, int TY, int ZC, int MINB>
+template <typename S, typename R, int TX, int TY, int ZC, int MINB, bool HI1 = false>
 __global__ void __launch_bounds__(TX * TY, MINB)
     step_kernel_tiled3d_capped(StepParams<R> P, const S* LBFD_RESTRICT g_in, S* LBFD_RESTRICT g_out,
                                const S* LBFD_RESTRICT T_in, S* LBFD_RESTRICT T_out, const S* LBFD_RESTRICT Y_in,
                                S* LBFD_RESTRICT Y_out, const uint8_t* LBFD_RESTRICT interior)
 {
-    tiled3d_body<S, R, TX, TY, ZC>(P, g_in, g_out, T_in, T_out, Y_in, Y_out, interior);
+    tiled3d_body<S, R, TX, TY, ZC, false, false, HI1>(P, g_in, g_out, T_in, T_out, Y_in, Y_out, interior);
 }
 
 // a1-a7 of the interior cells (the FD half of a split step); FP32 held to
