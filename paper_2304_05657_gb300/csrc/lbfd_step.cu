@@ -259,8 +259,13 @@ void face_codes(int nx, int ny, int nz, const int* bc, const uint8_t* solid, con
             // beyond a face: the general form bounces back where the boundary
             // column is solid, and takes the convective outlet's inner value
             // from the cell itself where the inner cell is solid
+            // (the column: periodic axes wrapped, the others clamped)
             int qc[3] = {p[0] - ci[0], p[1] - ci[1], p[2] - ci[2]};
-            for (int a = 0; a < 3; ++a) qc[a] = qc[a] < 0 ? 0 : (qc[a] >= n[a] ? n[a] - 1 : qc[a]);
+            for (int a = 0; a < 3; ++a) {
+                if (qc[a] >= 0 && qc[a] < n[a]) continue;
+                if (bc[2 * a + (qc[a] < 0 ? 0 : 1)] == BC_PERIODIC) qc[a] = ((qc[a] % n[a]) + n[a]) % n[a];
+                else qc[a] = qc[a] < 0 ? 0 : n[a] - 1;
+            }
             if (solid[(long long)qc[0] + (long long)nx * ((long long)qc[1] + (long long)ny * qc[2])]) ok = false;
             if (bc[f] == BC_OUTLET) {
                 const int a = f / 2, ns = (f % 2 == 1) ? 1 : -1;

@@ -448,11 +448,14 @@ def test_d3q27_face_codes_match_oracle(lbfd_lib, oracle_mod, outlet):
     every 3-D tile variant: FP64 against the oracle to 1e-10, mixed T to
     1e-6.  Solid cells next to both faces leave some cells to the general
     form (an Eq. 32 inner cell that is solid) and give others bounce-back
-    bits beside the face rules."""
+    bits beside the face rules.  Solid cells in the face planes at the
+    periodic y/z seams make the boundary column of a face-crossing population
+    a wrapped cell (the general form bounces such a population back)."""
     cfg, solid, T, Y = inputs.sphere_packing(nx=36, ny=12, nz=11, x_range=(8, 28), r_range=(2.0, 3.0),
                                              porosity=0.85, seed=21, ignite_width=4)
     cfg["bc"][1] = outlet
     solid[4, 5, 1] = solid[6, 3, 34] = solid[7, 8, 33] = True
+    solid[0, 11, 0] = solid[10, 0, 35] = solid[5, 11, 0] = True
     g, T, Y = inputs.perturbed_state(cfg, solid, T, Y, seed=22)
     o = oracle_mod.Sim(cfg, solid)
     o.set_state(T, Y, g)
