@@ -502,3 +502,37 @@ def test_d3q27_mixed_higher_order_rate(lbfd_lib, oracle_mod, omega_hi):
                 assert rel_l2(Yg[k], Yo[k]) <= 1e-6, (v, k)
         for i in range(go.shape[0]):
             assert rel_l2(gg[i], go[i]) <= 1e-5, (v, i)
+
+
+def test_d3q27_packing_cut_by_the_faces(lbfd_lib, oracle_mod):
+    """Spheres that reach the inlet and outlet planes (the packing fills the
+    whole length, periodic in y and z), as in the crops of the large packing
+    that the benchmark compares with the oracle: every 3-D variant in FP64
+    against the oracle to 1e-10, and the FP32 tile variants 1, 2 with every
+    population plane to 1e-5 and T to 1e-6 (relative L2)."""
+    cfg, _, T, Y = inputs.sphere_packing(nx=30, ny=14, nz=13, x_range=(0, 30), r_range=(2.0, 4.0),
+                                         porosity=0.8, seed=31, ignite_width=4)
+    # the middle of a longer packing: spheres cut by both planes
+    solid = inputs.sphere_packing(nx=60, ny=14, nz=13, x_range=(0, 60), r_range=(2.0, 4.0), porosity=0.8,
+                                  seed=34)[1][:, :, 15:45].copy()
+    assert solid[:, :, 0].sum() > 20 and solid[:, :, -1].sum() > 10
+    g, T, Y = inputs.perturbed_state(cfg, solid, T, Y, seed=32)
+    o = oracle_mod.Sim(cfg, solid)
+    o.set_state(T, Y, g)
+    o.step(8)
+    orc = o.get_state()
+    s = lbfd_lib.Solver(cfg, solid)
+    for v in range(s.num_variants):
+        s.variant = v
+        s.set_state(T, Y, g)
+        s.step(8)
+        compare_states(s.get_state(), orc, 1e-10, f"faces cut, variant {v}")
+    sm = lbfd_lib.Solver(dict(cfg, precision="mixed"), solid)
+    for v in (1, 2):
+        sm.variant = v
+        sm.set_state(T, Y, g)
+        sm.step(8)
+        Tg, Yg, gg = sm.get_state()
+        assert rel_l2(Tg, orc[0]) <= 1e-6, v
+        for i in range(gg.shape[0]):
+            assert rel_l2(gg[i], orc[2][i]) <= 1e-5, (v, i)
