@@ -1364,8 +1364,11 @@ int lbfd_get_state_raw(lbfd_handle* h, void* dst, size_t bytes)
 {
     if (!h || !dst || bytes != lbfd_state_bytes(h)) return LBFD_EINVAL;
     const size_t w = (size_t)h->ncell * h->esz;
-    CK(cudaMemcpy2DAsync(dst, w, h->buf[h->cur], (size_t)h->stride * h->esz, w, h->planes, cudaMemcpyDeviceToHost,
-                         h->stream));
+    if (h->stride == h->ncell)  // unpadded planes: one contiguous copy
+        CK(cudaMemcpyAsync(dst, h->buf[h->cur], w * h->planes, cudaMemcpyDeviceToHost, h->stream));
+    else
+        CK(cudaMemcpy2DAsync(dst, w, h->buf[h->cur], (size_t)h->stride * h->esz, w, h->planes,
+                             cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return LBFD_OK;
 }
@@ -1374,8 +1377,11 @@ int lbfd_set_state_raw(lbfd_handle* h, const void* src, size_t bytes)
 {
     if (!h || !src || bytes != lbfd_state_bytes(h)) return LBFD_EINVAL;
     const size_t w = (size_t)h->ncell * h->esz;
-    CK(cudaMemcpy2DAsync(h->buf[h->cur], (size_t)h->stride * h->esz, src, w, w, h->planes, cudaMemcpyHostToDevice,
-                         h->stream));
+    if (h->stride == h->ncell)
+        CK(cudaMemcpyAsync(h->buf[h->cur], src, w * h->planes, cudaMemcpyHostToDevice, h->stream));
+    else
+        CK(cudaMemcpy2DAsync(h->buf[h->cur], (size_t)h->stride * h->esz, src, w, w, h->planes,
+                             cudaMemcpyHostToDevice, h->stream));
     // the other buffer too: the step never rewrites solid cells
     const size_t all = h->planes * (size_t)h->stride * h->esz;
     CK(cudaMemcpyAsync(h->buf[h->cur ^ 1], h->buf[h->cur], all, cudaMemcpyDeviceToDevice, h->stream));
