@@ -325,7 +325,8 @@ int lbfd_gradient(lbfd_handle* h, int objective, double* value, double* grad);
  * branches taken on the values.  The forward pass keeps a copy of the state
  * every `checkpoint_every` steps; the backward pass recomputes each segment
  * from its copy with the forward kernels (FP32 ones for LBFD_MIXED) and
- * evaluates every step's adjoint in FP64 at that trajectory, accumulating
+ * evaluates every step's adjoint at that trajectory, the step recorded in
+ * FP64 (in FP32 for LBFD_MIXED: FP32 values and partials), accumulating
  * lambda and the gradient in FP64.
  *
  * lbfd_adjoint_setup: the checkpoint interval of later calls (default 200).
@@ -341,8 +342,8 @@ int lbfd_gradient(lbfd_handle* h, int objective, double* value, double* grad);
  * lbfd_adjoint_gradient: lbfd_adjoint_run with this checkpoint interval
  *   for the one call.
  * Device memory of a backward call: checkpoint_every + 2 state copies and
- *   two FP64 adjoint states, plus tapes of at most 12 GB: 20 B x 2048 nodes
- *   per cell and recorded step, in two buffers of up to 4 steps each (one
+ *   two FP64 adjoint states, plus tapes of at most 12 GB: 20 B (12 B for
+ *   LBFD_MIXED) x 2048 nodes per cell and recorded step, in two buffers of up to 4 steps each (one
  *   recorded while the other is swept) when they fit, else one step with
  *   its cells in chunks; and 8 B x 2048 nodes per cell for the sweep.  A
  *   step that needs more nodes is taken again with 4096.  Freed before

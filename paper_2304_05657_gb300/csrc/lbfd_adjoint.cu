@@ -16,22 +16,22 @@ constexpr int REV_BLOCK = 64;
 // adjoints run this many sweeps ahead
 constexpr int REV_WIN = 32, REV_LAG = 8;
 
-// the state (FP64, or the FP32 state of the mixed form widened to FP64) as
-// tape input (values only)
-template <typename S>
+// the state as tape input (values only): FP64, or the FP32 state of the
+// mixed form (V = float records its step in FP32)
+template <typename S, typename V>
 __global__ void __launch_bounds__(256) to_rev_kernel(long long n, const S* __restrict__ in,
-                                                     RevStore* __restrict__ out)
+                                                     RevStoreT<V>* __restrict__ out)
 {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < n) out[e] = RevStore(Rev((double)in[e]));
+    if (e < n) out[e] = RevStoreT<V>(RevT<V>((double)in[e]));
 }
 
 // Record: thread t of the launch takes cell c0 + u, u = t % chunk, of the
 // step from the state of slot t / chunk (several steps' tapes are recorded
 // in one launch), and leaves its node count in count[t].
-template <int DIM>
+template <int DIM, typename V>
 __global__ void __launch_bounds__(REV_BLOCK, 8)
-    adjoint_record_kernel(StepParams<Rev> P, const RevStore* __restrict__ rin, RevStore* __restrict__ rout,
+    adjoint_record_kernel(StepParams<RevT<V>> P, const RevStoreT<V>* __restrict__ rin, RevStoreT<V>* __restrict__ rout,
                           const uint8_t* __restrict__ solid, long long c0, long long n, long long chunk,
                           long long nel, int* __restrict__ count)
 {
@@ -43,19 +43,19 @@ __global__ void __launch_bounds__(REV_BLOCK, 8)
         // theta = (ln A, Ta, T_wall, u_in) are the tape's first four nodes
         // (parameter leaves), and P names them as the nodes of A dt, Ta, the
         // isothermal wall and solid temperatures and u_in (rev_params)
-        rev_push(0.0, REV_THETA, P.A_lat.v, REV_NONE);  // d(A dt)/d(ln A) = A dt
-        rev_push(1.0, REV_THETA, 1.0, REV_NONE);
-        rev_push(2.0, REV_THETA, 1.0, REV_NONE);
-        rev_push(3.0, REV_THETA, 1.0, REV_NONE);
+        rev_push<V>(V(0), REV_THETA, P.A_lat.v, REV_NONE);  // d(A dt)/d(ln A) = A dt
+        rev_push<V>(V(1), REV_THETA, V(1), REV_NONE);
+        rev_push<V>(V(2), REV_THETA, V(1), REV_NONE);
+        rev_push<V>(V(3), REV_THETA, V(1), REV_NONE);
         const long long N = P.N;
-        const RevStore* in = rin + slot * nel;
-        RevStore* out = rout + slot * nel;
+        const RevStoreT<V>* in = rin + slot * nel;
+        RevStoreT<V>* out = rout + slot * nel;
         int p[3];
         p[0] = (int)(c % P.nx);
         const long long r = c / P.nx;
         p[1] = (int)(r % P.ny);
         p[2] = (int)(r / P.ny);
-        cell_step_general<DIM, RevStore, Rev>(P, p, c, in, out, in + (long long)Q * N, out + (long long)Q * N,
+        cell_step_general<DIM, RevStoreT<V>, RevT<V>>(P, p, c, in, out, in + (long long)Q * N, out + (long long)Q * N,
                                               in + (long long)(Q + 1) * N, out + (long long)(Q + 1) * N, solid);
     }
     count[t] = rev_count_dyn[threadIdx.x];
@@ -71,13 +71,15 @@ __global__ void __launch_bounds__(REV_BLOCK, 8)
 // passes to node k - REV_WIN, whose value in adj is final then: it is loaded
 // at once and added REV_LAG sweeps later.  The tape entries of node
 // k - REV_LAG are loaded when node k is swept, so no sweep waits on a load;
-// theta contributions accumulate in registers.
+// theta contributions accumulate in registers.  The partials (V) enter FP64
+// products: the adjoints are FP64 whatever V is.
+template <typename V>
 __global__ void __launch_bounds__(REV_BLOCK)
-    adjoint_sweep_kernel(const RevStore* __restrict__ out, const uint8_t* __restrict__ solid, long long c0,
+    adjoint_sweep_kernel(const RevStoreT<V>* __restrict__ out, const uint8_t* __restrict__ solid, long long c0,
                          long long n, long long ncell, long long N, int planes, long long slot, long long NT,
                          long long ebase, const int* __restrict__ count, const double* __restrict__ lam_next,
                          double* __restrict__ lam, double* __restrict__ dtheta, double* __restrict__ adj_buf,
-                         const double* __restrict__ tape_a0, const double* __restrict__ tape_a1,
+                         const V* __restrict__ tape_a0, const V* __restrict__ tape_a1,
                          const int32_t* __restrict__ tape_par, int* __restrict__ max_nodes)
 {
     extern __shared__ double win_dyn[];
@@ -103,18 +105,20 @@ __global__ void __launch_bounds__(REV_BLOCK)
         if (node >= nn - REV_WIN) win[((unsigned)node & WM) * REV_BLOCK] += lam_next[e];
         else adj[(unsigned)node * chunk] += lam_next[e];
     }
-    const double* a0 = tape_a0 + t;
-    const double* a1 = tape_a1 + t;
+    const V* a0 = tape_a0 + t;
+    const V* a1 = tape_a1 + t;
     const int32_t* par = tape_par + t;
     double th0 = 0.0, th1 = 0.0, th2 = 0.0, th3 = 0.0;
     // queue slot j holds, while node k = k0 - j is swept, its tape entry and
     // the adj value of node k + REV_LAG - REV_WIN
-    double lag[REV_LAG], qa0[REV_LAG], qa1[REV_LAG];
+    double lag[REV_LAG];
+    V qa0[REV_LAG], qa1[REV_LAG];
     int32_t qp[REV_LAG];
 #pragma unroll
     for (int j = 0; j < REV_LAG; ++j) {
         const int k = nn - 1 - j;
-        lag[j] = qa0[j] = qa1[j] = 0.0;
+        lag[j] = 0.0;
+        qa0[j] = qa1[j] = V(0);
         qp[j] = -1;  // both parents REV_NONE
         if (k >= 0) {
             const unsigned at = (unsigned)k * (unsigned)NT;
@@ -138,7 +142,8 @@ __global__ void __launch_bounds__(REV_BLOCK)
             *ws = 0.0;  // from now on the slot of node k - REV_WIN
             lag[j] = k >= REV_WIN ? adj[(unsigned)(k - REV_WIN) * chunk] : 0.0;
             const int q0 = (int16_t)(qp[j] & 0xffff), q1 = qp[j] >> 16;
-            const double x0 = qa0[j], x1 = qa1[j];
+            const V v0 = qa0[j];
+            const double x0 = (double)v0, x1 = (double)qa1[j];
             if (k >= REV_LAG) {
                 const unsigned at = (unsigned)(k - REV_LAG) * (unsigned)NT;
                 qp[j] = par[at];
@@ -149,7 +154,7 @@ __global__ void __launch_bounds__(REV_BLOCK)
             if (q0 >= 0) {
                 add(q0, k, a * x0);
             } else if (q0 == REV_STATE) {
-                atomicAdd(&lam[__double_as_longlong(x0) - ebase], a);
+                atomicAdd(&lam[rev_index_of(v0) - ebase], a);
             } else if (q0 == REV_THETA) {
                 const double d = a * x1;
                 const int m = (int)x0;
@@ -170,9 +175,11 @@ __global__ void __launch_bounds__(REV_BLOCK)
 // the parameters as reverse-mode constants, except those that depend on
 // theta: they name the parameter leaves that each thread pushes first (node
 // 0: A dt, 1: Ta, 2: the isothermal wall and solid temperatures, 3: u_in)
-static StepParams<Rev> rev_params(const StepParams<double>& D)
+template <typename V>
+static StepParams<RevT<V>> rev_params(const StepParams<double>& D)
 {
-    StepParams<Rev> P;
+    using Rv = RevT<V>;
+    StepParams<Rv> P;
     memset(&P, 0, sizeof P);  // zero bytes are constants (node 0)
     P.dim = D.dim;
     P.nx = D.nx;
@@ -182,40 +189,40 @@ static StepParams<Rev> rev_params(const StepParams<double>& D)
     P.N = D.N;
     for (int f = 0; f < 6; ++f) {
         P.bc[f] = D.bc[f];
-        P.T_wall[f] = D.bc[f] == BC_WALL_ISOTHERMAL ? Rev(D.T_wall[f], 2) : Rev(D.T_wall[f]);
+        P.T_wall[f] = D.bc[f] == BC_WALL_ISOTHERMAL ? Rv(D.T_wall[f], 2) : Rv(D.T_wall[f]);
         P.face_solid[f] = D.face_solid[f];
     }
     for (int k = 0; k < NSP; ++k) {
-        P.inv_Wk[k] = Rev(D.inv_Wk[k]);
-        P.yield[k] = Rev(D.yield[k]);
-        P.a_diff[k] = Rev(D.a_diff[k]);
-        P.a12[k] = Rev(D.a12[k]);
-        P.Y_in[k] = Rev(D.Y_in[k]);
+        P.inv_Wk[k] = Rv(D.inv_Wk[k]);
+        P.yield[k] = Rv(D.yield[k]);
+        P.a_diff[k] = Rv(D.a_diff[k]);
+        P.a12[k] = Rv(D.a12[k]);
+        P.Y_in[k] = Rv(D.Y_in[k]);
     }
     P.fuel = D.fuel;
     P.oxid = D.oxid;
-    P.A_lat = Rev(D.A_lat, 0);
-    P.Ta = Rev(D.Ta, 1);
-    P.Q_cp = Rev(D.Q_cp);
+    P.A_lat = Rv(D.A_lat, 0);
+    P.Ta = Rv(D.Ta, 1);
+    P.Q_cp = Rv(D.Q_cp);
     P.A_lat_d = D.A_lat_d;
     P.Ta_d = D.Ta_d;
-    P.T_fp64 = Rev(D.T_fp64);
-    P.omega_s = Rev(D.omega_s);
-    P.omega_b = Rev(D.omega_b);
-    P.omega_hi = Rev(D.omega_hi);
-    P.alpha = Rev(D.alpha);
-    P.alpha12 = Rev(D.alpha12);
-    P.lam_yield = Rev(D.lam_yield);
-    P.u_in = Rev(D.u_in, 3);
-    P.T_in = Rev(D.T_in);
-    P.invW_in = Rev(D.invW_in);
-    P.rho_in = Rev(D.rho_in);
-    P.T_solid = D.solid_isothermal ? Rev(D.T_solid, 2) : Rev(D.T_solid);
+    P.T_fp64 = Rv(D.T_fp64);
+    P.omega_s = Rv(D.omega_s);
+    P.omega_b = Rv(D.omega_b);
+    P.omega_hi = Rv(D.omega_hi);
+    P.alpha = Rv(D.alpha);
+    P.alpha12 = Rv(D.alpha12);
+    P.lam_yield = Rv(D.lam_yield);
+    P.u_in = Rv(D.u_in, 3);
+    P.T_in = Rv(D.T_in);
+    P.invW_in = Rv(D.invW_in);
+    P.rho_in = Rv(D.rho_in);
+    P.T_solid = D.solid_isothermal ? Rv(D.T_solid, 2) : Rv(D.T_solid);
     P.solid_isothermal = D.solid_isothermal;
     P.poiseuille = D.poiseuille;
-    P.epsY = Rev(D.epsY);
-    P.epsT = Rev(D.epsT);
-    P.cs = Rev(D.cs);
+    P.epsY = Rv(D.epsY);
+    P.epsT = Rv(D.epsT);
+    P.cs = Rv(D.cs);
     P.curved = 0;
     P.link_row = nullptr;
     P.link_q = nullptr;
@@ -224,24 +231,24 @@ static StepParams<Rev> rev_params(const StepParams<double>& D)
     return P;
 }
 
-size_t adjoint_node_bytes() { return 2 * sizeof(double) + sizeof(int32_t); }
-size_t rev_store_bytes() { return sizeof(RevStore); }
+size_t adjoint_node_bytes(bool fp32) { return 2 * (fp32 ? sizeof(float) : sizeof(double)) + sizeof(int32_t); }
+size_t rev_store_bytes(bool fp32) { return fp32 ? sizeof(RevStoreT<float>) : sizeof(RevStoreT<double>); }
 
-cudaError_t launch_adjoint_record(int dim, const StepParams<double>& Pd, int planes, const void* states,
-                                  size_t state_bytes, int slots, bool fp32, const uint8_t* solid, long long c0,
-                                  long long n, const AdjointWork& w, cudaStream_t stream)
+template <typename V>
+static cudaError_t record_steps(const StepParams<double>& Pd, int planes, const void* states, size_t state_bytes,
+                                int slots, bool fp32, const uint8_t* solid, long long c0, long long n,
+                                const AdjointWork& w, cudaStream_t stream)
 {
-    if (dim != 2 || slots < 1 || slots > w.slots) return cudaErrorInvalidValue;
     const long long nel = (long long)planes * Pd.N;
-    RevStore* rin = (RevStore*)w.rin;
+    RevStoreT<V>* rin = (RevStoreT<V>*)w.rin;
     cudaError_t e;
     const unsigned nb = (unsigned)((nel + 255) / 256);
     for (int j = 0; j < slots; ++j) {
         const char* st = (const char*)states + (size_t)j * state_bytes;
         if (fp32)
-            to_rev_kernel<float><<<nb, 256, 0, stream>>>(nel, (const float*)st, rin + (long long)j * nel);
+            to_rev_kernel<float, V><<<nb, 256, 0, stream>>>(nel, (const float*)st, rin + (long long)j * nel);
         else
-            to_rev_kernel<double><<<nb, 256, 0, stream>>>(nel, (const double*)st, rin + (long long)j * nel);
+            to_rev_kernel<double, V><<<nb, 256, 0, stream>>>(nel, (const double*)st, rin + (long long)j * nel);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     RevTape tp;
@@ -253,34 +260,54 @@ cudaError_t launch_adjoint_record(int dim, const StepParams<double>& Pd, int pla
     tp.overflow = w.flags;
     if ((e = cudaMemcpyToSymbolAsync(rev_tape, &tp, sizeof tp, 0, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
         return e;
-    const StepParams<Rev> P = rev_params(Pd);
+    const StepParams<RevT<V>> P = rev_params<V>(Pd);
     // the tape is sized for w.slots * w.chunk threads: launch that many per
     // slot (idle ones return at once) so that the interleaved layout has a
     // fixed stride
     const unsigned blocks = (unsigned)((w.slots * w.chunk + REV_BLOCK - 1) / REV_BLOCK);
-    adjoint_record_kernel<2><<<blocks, REV_BLOCK, REV_BLOCK * sizeof(int), stream>>>(
-        P, rin, (RevStore*)w.rout, solid, c0, n, w.chunk, nel, w.count);
+    adjoint_record_kernel<2, V><<<blocks, REV_BLOCK, REV_BLOCK * sizeof(int), stream>>>(
+        P, rin, (RevStoreT<V>*)w.rout, solid, c0, n, w.chunk, nel, w.count);
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_sweep(const StepParams<double>& Pd, int planes, int slot, const uint8_t* solid,
+cudaError_t launch_adjoint_record(int dim, const StepParams<double>& Pd, int planes, const void* states,
+                                  size_t state_bytes, int slots, bool fp32, const uint8_t* solid, long long c0,
+                                  long long n, const AdjointWork& w, cudaStream_t stream)
+{
+    if (dim != 2 || slots < 1 || slots > w.slots) return cudaErrorInvalidValue;
+    // the FP32 tape names state elements in 31 bits
+    if (fp32 && (long long)w.slots * planes * Pd.N >= (1ll << 31)) return cudaErrorInvalidValue;
+    if (fp32) return record_steps<float>(Pd, planes, states, state_bytes, slots, fp32, solid, c0, n, w, stream);
+    return record_steps<double>(Pd, planes, states, state_bytes, slots, fp32, solid, c0, n, w, stream);
+}
+
+template <typename V>
+static cudaError_t sweep_step(const StepParams<double>& Pd, int planes, int slot, const uint8_t* solid, long long c0,
+                              long long n, const double* lam_next, double* lam, double* dtheta, const AdjointWork& w,
+                              cudaStream_t stream)
+{
+    const long long nel = (long long)planes * Pd.N;
+    constexpr size_t smem = REV_BLOCK * REV_WIN * sizeof(double);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(adjoint_sweep_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)) != cudaSuccess)
+        return e;
+    const unsigned blocks = (unsigned)(w.chunk / REV_BLOCK);
+    adjoint_sweep_kernel<V><<<blocks, REV_BLOCK, smem, stream>>>(
+        (const RevStoreT<V>*)w.rout + slot * nel, solid, c0, n, Pd.ncell, Pd.N, planes, slot,
+        (long long)w.slots * w.chunk, slot * nel, w.count, lam_next, lam, dtheta, w.adj, (const V*)w.a0,
+        (const V*)w.a1, w.par, w.flags + 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_sweep(const StepParams<double>& Pd, int planes, int slot, bool fp32, const uint8_t* solid,
                                  long long c0, long long n, const double* lam_next, double* lam, double* dtheta,
                                  const AdjointWork& w, cudaStream_t stream)
 {
     if (slot < 0 || slot >= w.slots) return cudaErrorInvalidValue;
     if ((unsigned long long)w.maxn * w.slots * w.chunk >= (1ull << 32)) return cudaErrorInvalidValue;  // 32-bit offsets
-    const long long nel = (long long)planes * Pd.N;
-    constexpr size_t smem = REV_BLOCK * REV_WIN * sizeof(double);
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(adjoint_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-        cudaSuccess)
-        return e;
-    const unsigned blocks = (unsigned)(w.chunk / REV_BLOCK);
-    adjoint_sweep_kernel<<<blocks, REV_BLOCK, smem, stream>>>(
-        (const RevStore*)w.rout + slot * nel, solid, c0, n, Pd.ncell, Pd.N, planes, slot,
-        (long long)w.slots * w.chunk, slot * nel, w.count, lam_next, lam, dtheta, w.adj, w.a0, w.a1, w.par,
-        w.flags + 1);
-    return cudaGetLastError();
+    if (fp32) return sweep_step<float>(Pd, planes, slot, solid, c0, n, lam_next, lam, dtheta, w, stream);
+    return sweep_step<double>(Pd, planes, slot, solid, c0, n, lam_next, lam, dtheta, w, stream);
 }
 
 // ---------------------------------------------------------------------------

@@ -1122,10 +1122,10 @@ static int adjoint_backward_pass(lbfd_handle* h, double seed, int maxn, double* 
     lbfd::AdjointWork w[2];
     memset(w, 0, sizeof w);
     const size_t budget = (size_t)12 << 30;
-    const size_t node = lbfd::adjoint_node_bytes();
+    const size_t node = lbfd::adjoint_node_bytes(fp32);
     const long long need = (h->ncell + 63) / 64 * 64;
     const size_t far = (size_t)maxn * sizeof(double);  // adj, per thread
-    const size_t per_slot = (size_t)need * ((size_t)maxn * node + sizeof(int)) + 2 * nel * lbfd::rev_store_bytes();
+    const size_t per_slot = (size_t)need * ((size_t)maxn * node + sizeof(int)) + 2 * nel * lbfd::rev_store_bytes(fp32);
     int nbuf = 1;
     w[0].maxn = maxn;
     if ((size_t)need * far + 2 * per_slot <= budget) {
@@ -1135,7 +1135,7 @@ static int adjoint_backward_pass(lbfd_handle* h, double seed, int maxn, double* 
         if (w[0].slots > 4) w[0].slots = 4;
         nbuf = K > w[0].slots ? 2 : 1;
     } else {
-        long long chunk = (long long)((budget - 2 * nel * lbfd::rev_store_bytes()) /
+        long long chunk = (long long)((budget - 2 * nel * lbfd::rev_store_bytes(fp32)) /
                                       ((size_t)maxn * node + sizeof(int) + far));
         w[0].chunk = chunk / 64 * 64;
         w[0].slots = 1;
@@ -1145,6 +1145,7 @@ static int adjoint_backward_pass(lbfd_handle* h, double seed, int maxn, double* 
     w[1].slots = w[0].slots;
     const size_t tape = (size_t)maxn * w[0].chunk * w[0].slots;
     const bool pipelined = w[0].chunk >= h->ncell;
+    const size_t vsz = fp32 ? sizeof(float) : sizeof(double);  // a recorded partial
     char* seg = nullptr;
     double *lam0 = nullptr, *lam1 = nullptr, *dth = nullptr;
     cudaStream_t s2 = nullptr;
@@ -1176,10 +1177,9 @@ static int adjoint_backward_pass(lbfd_handle* h, double seed, int maxn, double* 
     w[1].adj = w[0].adj;
     w[1].flags = w[0].flags;
     for (int i = 0; i < nbuf; ++i)
-        if ((e = alloc(&w[i].rin, w[i].slots * nel * lbfd::rev_store_bytes())) != cudaSuccess ||
-            (e = alloc(&w[i].rout, w[i].slots * nel * lbfd::rev_store_bytes())) != cudaSuccess ||
-            (e = alloc((void**)&w[i].a0, tape * sizeof(double))) != cudaSuccess ||
-            (e = alloc((void**)&w[i].a1, tape * sizeof(double))) != cudaSuccess ||
+        if ((e = alloc(&w[i].rin, w[i].slots * nel * lbfd::rev_store_bytes(fp32))) != cudaSuccess ||
+            (e = alloc(&w[i].rout, w[i].slots * nel * lbfd::rev_store_bytes(fp32))) != cudaSuccess ||
+            (e = alloc(&w[i].a0, tape * vsz)) != cudaSuccess || (e = alloc(&w[i].a1, tape * vsz)) != cudaSuccess ||
             (e = alloc((void**)&w[i].par, tape * sizeof(int32_t))) != cudaSuccess ||
             (e = alloc((void**)&w[i].count, w[i].slots * w[i].chunk * sizeof(int))) != cudaSuccess) {
             release();
@@ -1242,7 +1242,7 @@ static int adjoint_backward_pass(lbfd_handle* h, double seed, int maxn, double* 
                     const long long n = h->ncell - c0 < w[0].chunk ? h->ncell - c0 : w[0].chunk;
                     AK(lbfd::launch_adjoint_record(h->dim, h->Pd, planes, seg + (size_t)j * sbytes, sbytes, 1, fp32,
                                                    h->solid, c0, n, w[0], s));
-                    AK(lbfd::launch_adjoint_sweep(h->Pd, planes, 0, h->solid, c0, n, lam1, lam0, dth, w[0], s));
+                    AK(lbfd::launch_adjoint_sweep(h->Pd, planes, 0, fp32, h->solid, c0, n, lam1, lam0, dth, w[0], s));
                 }
                 std::swap(lam0, lam1);
             }
@@ -1279,7 +1279,8 @@ static int adjoint_backward_pass(lbfd_handle* h, double seed, int maxn, double* 
             const int j1 = len - 1 - i * G, j0 = first(i);
             for (int j = j1; j >= j0; --j) {
                 AK(cudaMemsetAsync(lam0, 0, lbytes, s));
-                AK(lbfd::launch_adjoint_sweep(h->Pd, planes, j - j0, h->solid, 0, h->ncell, lam1, lam0, dth, w[bi], s));
+                AK(lbfd::launch_adjoint_sweep(h->Pd, planes, j - j0, fp32, h->solid, 0, h->ncell, lam1, lam0, dth, w[bi],
+                                              s));
                 std::swap(lam0, lam1);
             }
             if (nbuf == 2) AK(cudaEventRecord(ev[2 + bi], s));

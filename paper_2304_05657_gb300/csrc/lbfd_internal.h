@@ -146,8 +146,8 @@ cudaError_t launch_objective(const StepParams<Tanf>& P, StateView st, const uint
 struct AdjointWork {
     void* rin;   // the input states as tape input (slots * planes * N elements)
     void* rout;  // the recorded outputs (as many)
-    double* a0;
-    double* a1;
+    void* a0;         // partials: double, or float for the FP32 forward pass
+    void* a1;
     int32_t* par;
     int* count;       // [slots * chunk] nodes each thread recorded
     double* adj;      // [maxn][chunk] adjoints of the far nodes during a sweep
@@ -156,16 +156,18 @@ struct AdjointWork {
     long long chunk;  // threads (cells) per slot, a multiple of 64
     int* flags;       // [0] tape overflow, [1] most nodes a thread used
 };
-size_t adjoint_node_bytes();  // tape bytes per node and slot
-size_t rev_store_bytes();
+size_t adjoint_node_bytes(bool fp32);  // tape bytes per node and slot
+size_t rev_store_bytes(bool fp32);
 // record the steps from `slots` states (slot j at states + j * state_bytes,
-// storage precision) for the cells [c0, c0 + n)
+// storage precision) for the cells [c0, c0 + n); fp32: the FP32 state of
+// the mixed form, its steps recorded in FP32 (the sweep's adjoints stay
+// FP64)
 cudaError_t launch_adjoint_record(int dim, const StepParams<double>& Pd, int planes, const void* states,
                                   size_t state_bytes, int slots, bool fp32, const uint8_t* solid, long long c0,
                                   long long n, const AdjointWork& w, cudaStream_t stream);
 // sweep the tapes of slot `slot` for the cells [c0, c0 + n): lam (zeroed by
 // the caller) += (dF/dx)^T lam_next, dtheta += (dF/dtheta)^T lam_next
-cudaError_t launch_adjoint_sweep(const StepParams<double>& Pd, int planes, int slot, const uint8_t* solid,
+cudaError_t launch_adjoint_sweep(const StepParams<double>& Pd, int planes, int slot, bool fp32, const uint8_t* solid,
                                  long long c0, long long n, const double* lam_next, double* lam, double* dtheta,
                                  const AdjointWork& w, cudaStream_t stream);
 // quenching-distance objective J = (S1/S0)^(-1/4), S0 = sum_fluid h,
