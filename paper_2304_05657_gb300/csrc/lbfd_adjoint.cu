@@ -4,6 +4,8 @@
 // u_in).  One thread per fluid cell records the general-form step of its
 // cell on a tape (lbfd_rev.cuh), several steps per launch, and one thread per
 // cell sweeps a step's tape backwards.
+#include <type_traits>
+
 #include "lbfd_internal.h"
 #include "lbfd_step_general.cuh"
 #include "lbfd_rev.cuh"
@@ -131,39 +133,50 @@ __global__ void __launch_bounds__(REV_BLOCK)
         if (q >= k - REV_WIN) win[((unsigned)q & WM) * REV_BLOCK] += x;
         else atomicAdd(&adj[(unsigned)q * chunk], x);
     };
-    for (int k0 = nn - 1; k0 >= 0; k0 -= REV_LAG) {
+    // one sweep step; CHECK: near the start of the tape, where the window,
+    // the far values and the prefetch reach below node 0 (the groups of
+    // REV_LAG nodes from the end that lie wholly above REV_WIN need none)
+    auto sweep = [&](auto check, int k, int j) {
+        constexpr bool CHECK = decltype(check)::value;
+        if (!CHECK || k + REV_LAG - REV_WIN >= 0) win[((unsigned)(k + REV_LAG) & WM) * REV_BLOCK] += lag[j];
+        double* ws = win + ((unsigned)k & WM) * REV_BLOCK;
+        const double a = *ws;
+        *ws = 0.0;  // from now on the slot of node k - REV_WIN
+        lag[j] = !CHECK || k >= REV_WIN ? adj[(unsigned)(k - REV_WIN) * chunk] : 0.0;
+        const int q0 = (int16_t)(qp[j] & 0xffff), q1 = qp[j] >> 16;
+        const V v0 = qa0[j];
+        const double x0 = (double)v0, x1 = (double)qa1[j];
+        if (!CHECK || k >= REV_LAG) {
+            const unsigned at = (unsigned)(k - REV_LAG) * (unsigned)NT;
+            qp[j] = par[at];
+            qa0[j] = a0[at];
+            qa1[j] = a1[at];
+        }
+        if (a == 0.0) return;
+        if (q0 >= 0) {
+            add(q0, k, a * x0);
+        } else if (q0 == REV_STATE) {
+            atomicAdd(&lam[rev_index_of(v0) - ebase], a);
+        } else if (q0 == REV_THETA) {
+            const double d = a * x1;
+            const int m = (int)x0;
+            th0 += m == 0 ? d : 0.0;
+            th1 += m == 1 ? d : 0.0;
+            th2 += m == 2 ? d : 0.0;
+            th3 += m == 3 ? d : 0.0;
+        }
+        if (q1 >= 0) add(q1, k, a * x1);
+    };
+    int k0 = nn - 1;
+    for (; k0 - (REV_LAG - 1) >= REV_WIN; k0 -= REV_LAG) {
+#pragma unroll
+        for (int j = 0; j < REV_LAG; ++j) sweep(std::false_type{}, k0 - j, j);
+    }
+    for (; k0 >= 0; k0 -= REV_LAG) {
 #pragma unroll
         for (int j = 0; j < REV_LAG; ++j) {
-            const int k = k0 - j;
-            if (k < 0) break;
-            if (k + REV_LAG - REV_WIN >= 0) win[((unsigned)(k + REV_LAG) & WM) * REV_BLOCK] += lag[j];
-            double* ws = win + ((unsigned)k & WM) * REV_BLOCK;
-            const double a = *ws;
-            *ws = 0.0;  // from now on the slot of node k - REV_WIN
-            lag[j] = k >= REV_WIN ? adj[(unsigned)(k - REV_WIN) * chunk] : 0.0;
-            const int q0 = (int16_t)(qp[j] & 0xffff), q1 = qp[j] >> 16;
-            const V v0 = qa0[j];
-            const double x0 = (double)v0, x1 = (double)qa1[j];
-            if (k >= REV_LAG) {
-                const unsigned at = (unsigned)(k - REV_LAG) * (unsigned)NT;
-                qp[j] = par[at];
-                qa0[j] = a0[at];
-                qa1[j] = a1[at];
-            }
-            if (a == 0.0) continue;
-            if (q0 >= 0) {
-                add(q0, k, a * x0);
-            } else if (q0 == REV_STATE) {
-                atomicAdd(&lam[rev_index_of(v0) - ebase], a);
-            } else if (q0 == REV_THETA) {
-                const double d = a * x1;
-                const int m = (int)x0;
-                th0 += m == 0 ? d : 0.0;
-                th1 += m == 1 ? d : 0.0;
-                th2 += m == 2 ? d : 0.0;
-                th3 += m == 3 ? d : 0.0;
-            }
-            if (q1 >= 0) add(q1, k, a * x1);
+            if (k0 - j < 0) break;
+            sweep(std::true_type{}, k0 - j, j);
         }
     }
     if (th0 != 0.0) atomicAdd(&dtheta[0], th0);
