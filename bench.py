@@ -400,7 +400,8 @@ def gradient_rate(args):
     out["adjoint_grad_steps_per_s"] = S / (time.perf_counter() - t0)
     s.close()
     out["adjoint_vs_fp64_step_time"] = out["fp64_steps_per_s"] / out["adjoint_grad_steps_per_s"]
-    # the same with the FP32 forward pass (mixed kernels), adjoint in FP64
+    # the same with the FP32 forward pass (mixed kernels; its steps recorded
+    # in FP32), the adjoints accumulated in FP64
     s = lbfd.Solver(dict(cfg, precision="mixed"), solid, stream=stream)
     s.init_fields(T, Y)
     s.autotune(reps=5)
