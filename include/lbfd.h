@@ -350,7 +350,9 @@ int lbfd_gradient(lbfd_handle* h, int objective, double* value, double* grad);
  *   returning.  All synchronise.
  * Errors: LBFD_EINVAL (arguments, backward without a record), LBFD_ENOTSUP
  * (other precision, 3-D, curved walls, or a cell whose step needs more than
- * 4096 nodes), LBFD_ENOMEM. */
+ * 4096 nodes), LBFD_ENOMEM, LBFD_ECUDA (also for LBFD_MIXED when four
+ * recorded states hold 2^31 elements or more: the FP32 tape names state
+ * elements in 31 bits). */
 int lbfd_adjoint_setup(lbfd_handle* h, int checkpoint_every);
 int lbfd_adjoint_record(lbfd_handle* h, int steps, int objective, double* value);
 int lbfd_adjoint_backward(lbfd_handle* h, double seed, double* grad);
