@@ -231,12 +231,17 @@ int lbfd_set_wait_limit(lbfd_handle* h, long long ns);
  * planes) and a per-cell collision kernel (a8-a10), and 6..7 are 1..2 with
  * the cells next to in-domain solids updated in the tile kernel too (ghost
  * points by the mirror rule from the staged mask, bounce-back pulls).  The
- * cells the tiles leave out go through the general form over lists
- * computed at create (in 3-D, one list for cells near domain faces and one,
- * with the face rules compiled out, for cells next to in-domain solids,
- * which variants 6..7 launch only with curved walls).  All variants compute the same step up
- * to rounding order.  Default: 1 (0 for LBFD_TANGENT, which has the
- * general form only). */
+ * cells the tiles leave out are listed at create.  In 2-D they go through
+ * the general form.  In 3-D with staircase walls, a 64-bit neighbourhood
+ * code per listed cell drives a compact form of the step: one list for the
+ * cells next to in-domain solids (variants 1..5), one for the cells near
+ * inlet and outlet faces of one axis.  The general form takes the other
+ * cells near domain faces, and every listed cell when the walls are curved.
+ * In FP32 with omega_hi = 1 the 3-D tile and coded kernels form only the
+ * central moments of orders 0-2 (the relaxation sets the higher cumulants
+ * to equilibrium).  All variants compute the same step up to rounding
+ * order.  Default: 1 (0 for LBFD_TANGENT, which has the general form
+ * only). */
 int lbfd_num_variants(const lbfd_handle* h);
 int lbfd_get_variant(const lbfd_handle* h);
 int lbfd_set_variant(lbfd_handle* h, int variant);
