@@ -1,7 +1,7 @@
-// Host-side check of the 3-D face-code builder: for a few small geometries,
-// the cells near domain faces (boundary_cells, faces only) split by
-// face_codes into the coded ones (with their codes) and the rest, printed
-// one JSON object per case.  Built and run by tests/test_face_codes_host.py
+// Host-side check of the 3-D code builders: for a few small geometries, the
+// cells near domain faces (boundary_cells, faces only) split by face_codes
+// into the coded ones (with their codes) and the rest, and the wall codes of
+// the cells around one solid cell, printed one JSON object per case.  Built and run by tests/test_face_codes_host.py
 // on the CPU; no GPU call is made.
 #include <cstdio>
 #include <vector>
@@ -33,6 +33,22 @@ static void run(const char* name, int nx, int ny, int nz, const int* bc, const s
     printf("]}\n");
 }
 
+// the neighbourhood codes of the cells next to one solid cell in a periodic
+// domain (wall_codes; listed in index order)
+static void run_walls(const char* name, int nx, int ny, int nz, int sx, int sy, int sz)
+{
+    const int bc[6] = {0, 0, 0, 0, 0, 0};
+    std::vector<uint8_t> solid((size_t)nx * ny * nz, 0);
+    solid[(size_t)sx + (size_t)nx * (sy + (size_t)ny * sz)] = 1;
+    std::vector<long long> all, face, cells;
+    lbfd::boundary_cells(3, nx, ny, nz, bc, solid.data(), all, false, nullptr);
+    std::vector<unsigned long long> codes;
+    lbfd::wall_codes(nx, ny, nz, bc, solid.data(), all, codes);
+    printf("{\"case\": \"%s\", \"nx\": %d, \"ny\": %d, \"nz\": %d, \"coded\": [", name, nx, ny, nz);
+    for (size_t t = 0; t < all.size(); ++t) printf("%s[%lld, %llu]", t ? ", " : "", all[t], codes[t]);
+    printf("], \"rest\": []}\n");
+}
+
 int main()
 {
     const int open_x[6] = {3, 5, 0, 0, 0, 0};        // inlet, constant-pressure outlet, periodic y and z
@@ -43,5 +59,6 @@ int main()
     run("inner_pressure", 12, 6, 5, open_x, {10, 2, 2});
     run("inner_eq32", 12, 6, 5, eq32_x, {10, 2, 2});
     run("walls_y", 12, 8, 5, walls_y, {});
+    run_walls("one_solid", 9, 9, 9, 4, 4, 4);
     return 0;
 }

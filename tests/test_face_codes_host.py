@@ -87,3 +87,33 @@ def test_wall_faces_stay_with_the_general_form(cases):
     coded = sorted(xyz(d, c) for c, _ in d["coded"])
     assert coded == sorted((x, y, z) for x in (0, 1, 10, 11) for y in range(2, 6) for z in range(5))
     assert len(d["rest"]) == 12 * 4 * 5  # every cell within two of a y wall
+
+
+def test_wall_codes_around_one_solid_cell(cases):
+    """Every cell within reach of a single solid cell at (4, 4, 4) of a
+    periodic 9^3 domain: bounce-back bits for the populations pulled from it
+    (the cell at x - c_i is the solid) and, on each axis line through the
+    solid, the distance of the ghost on the solid's side."""
+    d = cases["one_solid"]
+    codes = {xyz(d, c): code for c, code in d["coded"]}
+    # the listed cells: the 26 neighbours and the 6 axis cells at distance 2
+    assert len(codes) == 26 + 6
+    s = (4, 4, 4)
+    for (x, y, z), code in codes.items():
+        dx, dy, dz = x - s[0], y - s[1], z - s[2]
+        bits = code & ((1 << 27) - 1)
+        if max(abs(dx), abs(dy), abs(dz)) == 1:
+            # population c = (dx, dy, dz) comes from the solid
+            i = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)
+            assert bits == 1 << i, ((x, y, z), hex(bits))
+        else:
+            assert bits == 0
+        for a, dist in enumerate((dx, dy, dz)):
+            line = (code >> (32 + 6 * a)) & 0x3F
+            others = [v for b, v in enumerate((dx, dy, dz)) if b != a]
+            if others == [0, 0] and dist != 0:
+                side_bits = abs(dist) << 3 if dist < 0 else abs(dist)  # dist < 0: the solid is on the + side
+                assert line == side_bits, ((x, y, z), a, line)
+            else:
+                assert line == 0, ((x, y, z), a, line)
+        assert (code >> 50) == 0
